@@ -1,0 +1,309 @@
+"""ParaQAOA hot-path benchmark (one JSON line on rank 0).
+
+Workload (the paper-scale configuration): Erdos-Renyi G(400, 0.1) and
+G(400, 0.5), integer weights uniform in {1..10}, seed 0; the balanced
+partition gives 21 parts of 20 vertices (2^20 complex64 amplitudes each).
+One step solves both graphs end to end: p = 1 grid (16 x 16), 32 Adam steps
+at p = 1, INTERP to p = 2, 32 Adam steps at p = 2, a final simulation that
+keeps the states, top-16 per part and a beam-256 merge. The metric counts
+every amplitude-layer the step simulates (2^n * p per evaluated instance).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own copy of the workload (graph seeds
+offset by rank): weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "QAOA amplitude-layer updates/s (%HBM roofline); 16k-vertex time-to-cut"
+UNIT = "amp-layer/s"
+NV, M, K, BEAM, P_FINAL, GRID, STEPS_ADAM = 400, 21, 16, 256, 2, 16, 32
+DENSITIES = (0.1, 0.5)
+WMAX = 10
+
+
+def workload(rank: int):
+    return [synth.erdos_renyi(NV, pe, seed=rank, wmax=WMAX) for pe in DENSITIES]
+
+
+def amp_layers_per_graph(n: int = 20) -> int:
+    """Amplitude-layers one solve of one graph simulates."""
+    d = 1 << n
+    grid = GRID * GRID * M * d * 1
+    adam1 = STEPS_ADAM * 4 * 1 * M * d * 1 + M * d * 1   # shifted evals + final eval
+    adam2 = STEPS_ADAM * 4 * 2 * M * d * 2 + M * d * 2
+    final = M * d * P_FINAL
+    return grid + adam1 + adam2 + final
+
+
+def config_dict():
+    return {"workload": "G(400,0.1)+G(400,0.5), w in {1..10}, seed 0; 21 parts x 20 qubits (2^20 complex64); "
+                        "p=1 16x16 grid + 32 Adam -> INTERP -> p=2 32 Adam; top-16; beam-256 merge",
+            "graphs": 2, "parts_per_graph": M, "qubits": 20, "p": P_FINAL, "K": K, "beam": BEAM,
+            "adam_steps": STEPS_ADAM, "grid": f"{GRID}x{GRID}",
+            "l2": "working set > L2: every batch streams >= 1.3 GB of state"}
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(kernel_src: str):
+    """ncu DRAM bytes per launch recorded for the current kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", "layer_pass_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return rec.get("dram_bytes_per_launch_full") if rec.get("source_sha256") == h else None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float = 15.0):
+    """The oracle, as it stands, on this host's cores: <C> evaluations of
+    20-qubit parts at p = 2 (the Adam batches of the workload), until about
+    `seconds` of CPU work."""
+    import oracle
+    g = synth.erdos_renyi(NV, 0.1, 0, wmax=WMAX)
+    subs = oracle.subgraphs(g, M)
+    batch = oracle.Batch(subs)
+    gam, bet = synth.random_angles(M, 2, 5)
+    done, t0 = 0, time.perf_counter()
+    chunk = max(1, oracle.num_threads())
+    while time.perf_counter() - t0 < seconds:
+        idx = (np.arange(chunk) + done) % M
+        oracle.expect_batch(batch, idx.astype(np.int32), gam[idx], bet[idx])
+        done += chunk
+    dt = time.perf_counter() - t0
+    amps = done * (1 << 20) * 2
+    return {"value": amps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} oracle <C> evaluations of 20-qubit parts at p=2 (complex128), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(seconds=max(5.0, 20.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(seconds=2.0)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(seconds=max(3.0, 60.0 / max(1, args.steps)))["value"])
+    v = statistics.median(vals) if vals else cb["value"]
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_layer_case(args):
+    """168 instances (21 parts x 8 angle sets) of 20 qubits at p = 2, <C> only:
+    one Adam-step batch of the workload; prints per-launch layer-pass timing."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    g = synth.erdos_renyi(NV, 0.1, 0, wmax=WMAX)
+    ctx = capi.paraqaoa_create(0)
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, M)
+    ids = np.repeat(np.arange(M, dtype=np.int32), 8)
+    gam, bet = synth.random_angles(len(ids), 2, 3)
+    capi.paraqaoa_part_upload(ctx, part)
+    for it in range(args.iters):
+        if it == args.iters - 1:
+            capi.paraqaoa_profile_enable(ctx, True)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+        capi.paraqaoa_expect(ctx, len(ids))
+    n_l, ms, by = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
+    peak, kind = read_peaks()
+    print(json.dumps({"case": "layer_pass", "instances": int(len(ids)), "qubits": 20, "p": 2,
+                      "launches": n_l, "ms": ms, "algorithmic_bytes": by,
+                      "achieved_gbs": by / (ms / 1e3) / 1e9, "peak_gbs": peak,
+                      "frac": by / (ms / 1e3) / 1e9 / peak}), flush=True)
+    capi.paraqaoa_part_free(part)
+    capi.paraqaoa_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="solve", choices=["solve", "layer_pass"],
+                    help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
+                         "a small case for profiling the layer-pass kernel")
+    ap.add_argument("--iters", type=int, default=3)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.case == "layer_pass":
+        return run_layer_case(args)
+
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()  # before the first GPU call of the timed work
+    stream = torch.cuda.Stream()
+    solver = pkg.Solver(device=local)
+    capi.paraqaoa_set_stream(solver.ctx, stream.cuda_stream)
+    graphs = workload(rank)
+    Gs = [capi.Graph.of(g) for g in graphs]
+    cfg = pkg.SolveConfig(M=M, K=K, p=P_FINAL, grid_points=GRID, adam_steps=STEPS_ADAM, beam=BEAM)
+
+    def step():
+        return [solver.solve(G, cfg) for G in Gs]
+
+    for _ in range(max(3, args.warmup)):
+        res = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    capi.paraqaoa_profile_enable(solver.ctx, True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = {k: capi.paraqaoa_profile_read(solver.ctx, k) for k in range(5)}
+    capi.paraqaoa_profile_enable(solver.ctx, False)
+    # end to end through the public API with host buffers: partition, upload,
+    # every host<->device copy and the merge readback inside the timed region
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for G in Gs:
+            part = capi.paraqaoa_partition(G, M)
+            capi.paraqaoa_part_upload(solver.ctx, part, True)
+            capi.paraqaoa_part_free(part)
+        step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    amps_step = amp_layers_per_graph() * len(graphs)
+    value = amps_step * args.steps * world / (ms / 1e3)
+    e2e_value = amps_step * args.steps * world / e2e_s
+    launches, lp_ms, lp_bytes = prof[capi.KCLASS_LAYER_PASS]
+    peak, peak_kind = read_peaks()
+    achieved = (lp_bytes / (lp_ms / 1e3)) / 1e9 if lp_ms > 0 else 0.0
+    traffic = traffic_for(os.path.join(ROOT, "paper_2603_26232_gb300", "csrc", "sim_kernels.cu"))
+    total_launches = sum(v[0] for v in prof.values())
+    h2d = sum(int(G.row_ptr.nbytes + G.col.nbytes + G.w.nbytes) for G in Gs)
+    d2h = len(Gs) * (M * K * 8 + NV + M * 8 * 3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 state, f64 <C>",
+            "data": "synthetic (seeded Erdos-Renyi graphs)", "config": config_dict(),
+            "time_to_cut_s": (ms / 1e3) / args.steps / len(graphs),
+            "cuts": [int(r.cut) for r in res],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None, "traffic": traffic,
+                         "kernel": "k_layer_pass (HBM-streaming layer pass)",
+                         "launches": launches, "avg_launch_ms": lp_ms / max(launches, 1),
+                         "algorithmic_bytes_per_launch": lp_bytes / max(launches, 1),
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "layer_pass_share": lp_ms / ms if ms else None,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(total_launches),
+            "clocks": clk,
+            "cpu_baseline": cb,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

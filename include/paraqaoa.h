@@ -1,0 +1,198 @@
+/*
+ * paraqaoa.h -- C ABI of the GB300 (sm_103a) ParaQAOA hot path.
+ *
+ * The library runs the data-parallel part of ParaQAOA (arXiv 2603.26232):
+ * partition a Max-Cut graph into a chain of subgraphs (Sec. 3.2, Alg. 1),
+ * simulate one QAOA circuit per subgraph on the GPU (Sec. 2.2, Sec. 3.3),
+ * reduce <C> and pick the top-K bitstrings (Sec. 3.3.2), and merge the
+ * candidates into a cut of the whole graph (Sec. 3.4, Alg. 2).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: PARAQAOA_OK (0) or a negative PARAQAOA_E_* code;
+ *    paraqaoa_strerror() names it. A failed call leaves its outputs
+ *    unspecified and the context usable, except after PARAQAOA_E_CUDA
+ *    (a CUDA runtime error), after which the context should be destroyed.
+ *  - Pointers named *_host (and every pointer not said otherwise) are host
+ *    memory owned by the caller; the library copies what it needs before the
+ *    call returns and never keeps them. Pointers named *_dev are device
+ *    memory of the context's GPU, also owned by the caller.
+ *  - The library owns paraqaoa_ctx, paraqaoa_part and all device state they
+ *    create; free them with paraqaoa_destroy / paraqaoa_part_free.
+ *  - Bit order: bit j of a bitstring z is local vertex j of its subgraph, i.e.
+ *    global vertex first_i + j. z_j = 1 puts the vertex in S. (The paper
+ *    prints bitstrings vertex by vertex, so its "110" is z = 0b011.)
+ *  - Angles: U_C(gamma) = exp(-i gamma C), U_M(beta) = exp(-i beta sum_j X_j),
+ *    layer l = 0..p-1 applies U_C(gamma[l]) then U_M(beta[l]) (Sec. 2.2).
+ *  - Threading: one context per host thread. Work is queued on the context's
+ *    stream; calls that return results to the host synchronise it.
+ *  - Weights are positive int32; a subgraph's total weight must be
+ *    <= PARAQAOA_MAX_SUBGRAPH_WEIGHT for simulation (its cut values index an
+ *    on-chip phase table).
+ */
+#ifndef PARAQAOA_H
+#define PARAQAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PARAQAOA_OK 0
+#define PARAQAOA_E_INVAL (-1)            /* bad argument, size or ordering of calls */
+#define PARAQAOA_E_TOO_MANY_QUBITS (-2)  /* a subgraph has more than PARAQAOA_MAX_QUBITS vertices */
+#define PARAQAOA_E_ADMISSION (-3)        /* the batch's device memory exceeds the context budget */
+#define PARAQAOA_E_NOMEM (-4)            /* host or device allocation failed */
+#define PARAQAOA_E_SEARCH_TOO_LARGE (-5) /* exhaustive merge requested over too many leaves */
+#define PARAQAOA_E_CUDA (-6)             /* CUDA runtime error */
+#define PARAQAOA_E_TIMEOUT (-7)          /* a bounded device-side wait gave up */
+#define PARAQAOA_E_NO_RESULT (-8)        /* results requested before a matching simulate call */
+
+#define PARAQAOA_MAX_QUBITS 30
+#define PARAQAOA_MAX_SUBGRAPH_WEIGHT 4095
+#define PARAQAOA_MAX_TOPK 32
+#define PARAQAOA_MAX_P 16
+
+/* Partition modes (Sec. 3.2, Alg. 1). */
+#define PARAQAOA_PART_BALANCED 0     /* |V|-1 steps split evenly, larger first; |V_i cap V_i+1| = 1 */
+#define PARAQAOA_PART_ALG1_LITERAL 1 /* s = floor(|V|/M) - 1 as printed in Alg. 1; last part takes the rest */
+#define PARAQAOA_PART_SIZES 2        /* explicit sizes[M], sum(sizes) - (M-1) = |V| */
+
+/* simulate_batch flags */
+#define PARAQAOA_SIM_EXPECT 0x1u     /* reduce <C> for every instance (paraqaoa_expect) */
+#define PARAQAOA_SIM_KEEP_STATE 0x2u /* keep the final states (paraqaoa_topk, paraqaoa_state) */
+
+/* topk flags */
+#define PARAQAOA_TOPK_CANONICAL 0x0u /* rank only z with bit n-1 = 0 (P(z) = P(not z)) */
+#define PARAQAOA_TOPK_RAW 0x1u       /* rank every z */
+
+/* Symmetric CSR: both directions of every edge stored, no self-loops, w > 0,
+ * row_ptr[n] = nnz. All arrays are host memory owned by the caller. */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  const int32_t *w;
+} paraqaoa_csr;
+
+typedef struct paraqaoa_ctx paraqaoa_ctx;
+typedef struct paraqaoa_part paraqaoa_part;
+
+/* Create a context on CUDA device `device`. hbm_budget (bytes) caps the
+ * device memory one simulate batch may use; 0 means 80% of the device's free
+ * memory at creation. */
+int paraqaoa_create(paraqaoa_ctx **out, int device, size_t hbm_budget);
+void paraqaoa_destroy(paraqaoa_ctx *ctx);
+
+/* Run subsequent work of ctx on `stream` (a cudaStream_t of ctx's device, or
+ * NULL for the context's own stream). The caller keeps ownership. */
+int paraqaoa_set_stream(paraqaoa_ctx *ctx, void *stream);
+
+/* Sec. 3.2, Alg. 1 (Connectivity-Preserving Partitioning + GetSubgraph):
+ * split vertices 0..n-1 into M index ranges, neighbours sharing one vertex,
+ * and keep for each part the induced edges E_i; the remaining edges are
+ * E_inter (Sec. 3.4.1). `sizes` is read only in PARAQAOA_PART_SIZES mode.
+ * Host-only; O(|V| + |E|). */
+int paraqaoa_partition(const paraqaoa_csr *g, int32_t M, int32_t mode, const int32_t *sizes,
+                       paraqaoa_part **out);
+void paraqaoa_part_free(paraqaoa_part *part);
+
+/* Describe a partition: M, and per part its first global vertex, size,
+ * edge count and total weight (each array M entries, any may be NULL). */
+int paraqaoa_part_info(const paraqaoa_part *part, int32_t *M, int32_t *first, int32_t *size,
+                       int64_t *edges, int64_t *weight);
+
+/* Local edge list (u < v, sorted) of part `id`; arrays sized by part_info. */
+int paraqaoa_part_edges(const paraqaoa_part *part, int32_t id, int32_t *u, int32_t *v, int32_t *w);
+
+/* Copy the partition's subgraph data (adjacency bit-planes, degrees) to the
+ * device. Simulation uploads on first use; calling this first keeps the copy
+ * out of a timed region. Re-uploads if `force` is non-zero. */
+int paraqaoa_part_upload(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t force);
+
+/* Sec. 2.1 cut table of part `id`: out_host[z] = C(z) = sum of w_uv over
+ * edges (u, v) of E_id with z_u != z_v, for z in [0, 2^n). 2^n entries. */
+int paraqaoa_cut_table(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t id, uint16_t *out_host);
+
+/* Sec. 2.2 / Sec. 3.3: simulate `count` QAOA instances. Instance i runs on
+ * part ids[i] with angles gamma[i*p + l], beta[i*p + l] (FP64, host), starting
+ * from |+>^n; the state is complex64. With PARAQAOA_SIM_EXPECT the
+ * expectation <C> is reduced (FP32 terms, FP64 sums); with
+ * PARAQAOA_SIM_KEEP_STATE the final states stay on the device for
+ * paraqaoa_topk / paraqaoa_state. Results replace those of the previous
+ * call. Returns PARAQAOA_E_ADMISSION if the states would exceed the budget. */
+int paraqaoa_simulate_batch(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids,
+                            int32_t count, int32_t p, const double *gamma, const double *beta,
+                            uint32_t flags);
+
+/* <C> of the last simulate call's instances (count must match). Synchronises. */
+int paraqaoa_expect(paraqaoa_ctx *ctx, int32_t count, double *out_host);
+
+/* Sec. 3.3.2: the K most probable bitstrings of each instance of the last
+ * simulate call (made with PARAQAOA_SIM_KEEP_STATE), ranked by probability
+ * (FP32) descending, then z ascending. out_z and out_p hold count*K entries.
+ * 1 <= K <= PARAQAOA_MAX_TOPK. Synchronises. */
+int paraqaoa_topk(paraqaoa_ctx *ctx, int32_t count, int32_t K, uint32_t *out_z, float *out_p,
+                  uint32_t flags);
+
+/* Final complex64 state of instance i of the last KEEP_STATE simulate call,
+ * written interleaved (re, im): 2 * 2^n floats. Synchronises. */
+int paraqaoa_state(paraqaoa_ctx *ctx, int32_t i, float *out_host);
+
+/* Sec. 3.4, Alg. 2: merge candidates cand[i*K + j] (bitstring j of part i,
+ * local bit order) into a cut of the whole graph g. Level i > 0 takes the
+ * candidate or its complement so that the shared vertex keeps its side.
+ *  - beam == 0: exhaustive level-aware depth-first merge (Alg. 2): K^L
+ *    starting paths walked in parallel, each to the last level; the best
+ *    leaf (ties: first in lexicographic candidate order) wins.
+ *    PARAQAOA_E_SEARCH_TOO_LARGE when K^M > 2^40.
+ *  - beam  > 0: beam reading for large M: keep the best `beam` partial
+ *    paths per level, ranked by the cut of the edges whose ends are both
+ *    assigned, ties by lexicographic candidate order. Exact when
+ *    beam >= K^(M-1).
+ * out_side[v] in {0,1} for every vertex (vertex 0 on side 0); *out_cut is
+ * CutVal of that assignment. */
+int paraqaoa_merge(paraqaoa_ctx *ctx, const paraqaoa_csr *g, const paraqaoa_part *part,
+                   const uint32_t *cand, int32_t K, int32_t L, int64_t beam, uint8_t *out_side,
+                   int64_t *out_cut);
+
+/* p = 1 grid search (angle loop, first stage): gamma_a = pi a / points,
+ * beta_b = (pi/2) b / points for a, b in [0, points); every part in ids is
+ * simulated at every grid point; per part the first maximum of <C> in
+ * row-major (a, b) order is returned. out_values (optional, count*points^2)
+ * receives every <C>. */
+int paraqaoa_grid_search(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids,
+                         int32_t count, int32_t points, double *out_gamma, double *out_beta,
+                         double *out_best, double *out_values);
+
+/* Fixed-iteration Adam (angle loop, second stage) on f = -<C>/W with
+ * central-difference gradients of step h; all scalar updates in FP64 on the
+ * device. gamma_io / beta_io (count*p, host) hold the start angles and
+ * receive the final ones; out_value (count) receives <C> there. */
+int paraqaoa_optimize(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids,
+                      int32_t count, int32_t p, int32_t steps, double lr, double h,
+                      double *gamma_io, double *beta_io, double *out_value);
+
+/* Per-kernel device time recorded with CUDA events on the context stream.
+ * enable != 0 starts recording (and clears the counters). */
+int paraqaoa_profile_enable(paraqaoa_ctx *ctx, int32_t enable);
+/* Read one counter set: kernel class `which` (see PARAQAOA_KCLASS_*):
+ * launches, summed device milliseconds and algorithmic bytes moved. */
+int paraqaoa_profile_read(paraqaoa_ctx *ctx, int32_t which, int64_t *launches, double *ms,
+                          double *bytes);
+
+#define PARAQAOA_KCLASS_LAYER_PASS 0 /* HBM-streaming layer passes (n >= 15) */
+#define PARAQAOA_KCLASS_SMEM_SIM 1   /* whole-state-on-chip simulation (n <= 14) */
+#define PARAQAOA_KCLASS_TOPK 2
+#define PARAQAOA_KCLASS_MERGE 3
+#define PARAQAOA_KCLASS_OTHER 4
+#define PARAQAOA_KCLASS_COUNT 5
+
+const char *paraqaoa_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARAQAOA_H */

@@ -1,0 +1,112 @@
+"""GB300-native ParaQAOA hot path (arXiv 2603.26232).
+
+The CUDA library (libparaqaoa.so, built from csrc/ for sm_103a) does the
+work; this package only binds its C ABI (``_capi``, same names as the header
+include/paraqaoa.h) and strings the calls of one ParaQAOA solve together.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _capi
+from ._capi import *  # noqa: F401,F403  (the C-ABI functions and constants)
+from ._capi import Graph, ParaQAOAError
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force)
+
+
+@dataclass
+class SolveConfig:
+    M: int                   # number of parts (Sec. 3.2)
+    K: int = 4               # top-K per part (Sec. 3.3.2)
+    p: int = 1               # QAOA depth
+    grid_points: int = 16    # p = 1 grid
+    adam_steps: int = 0      # Adam steps per depth (0: grid only)
+    lr: float = 0.02
+    h: float = 1e-3
+    L: int = 1               # merge starting level (exhaustive merge)
+    beam: int = 0            # 0: exhaustive merge; > 0: beam width
+    mode: int = _capi.PART_BALANCED
+    sizes: np.ndarray | None = None
+
+
+@dataclass
+class SolveResult:
+    side: np.ndarray
+    cut: int
+    gamma: np.ndarray
+    beta: np.ndarray
+    expect: np.ndarray
+    cand: np.ndarray
+    cand_p: np.ndarray
+    times: dict = field(default_factory=dict)
+
+
+def interp(gamma: np.ndarray, beta: np.ndarray):
+    """INTERP (Zhou et al., PRX 10, 021067, 2020): depth-p angles -> p+1."""
+    p = gamma.shape[-1]
+
+    def one(x):
+        x0 = np.concatenate([np.zeros(x.shape[:-1] + (1,)), x, np.zeros(x.shape[:-1] + (1,))], axis=-1)
+        i = np.arange(1, p + 2)
+        return ((i - 1) / p) * x0[..., i - 1] + ((p - i + 1) / p) * x0[..., i]
+
+    return one(gamma), one(beta)
+
+
+class Solver:
+    """One CUDA context and the full ParaQAOA pipeline on it:
+    partition -> angle search -> final simulation -> top-K -> merge."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.ctx = _capi.paraqaoa_create(device, hbm_budget)
+
+    def close(self):
+        if self.ctx:
+            _capi.paraqaoa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, g, cfg: SolveConfig, sync_times: bool = False) -> SolveResult:
+        G = Graph.of(g)
+        t = {}
+        t0 = time.perf_counter()
+        part = _capi.paraqaoa_partition(G, cfg.M, cfg.mode, cfg.sizes)
+        try:
+            first, size, _, _ = _capi.paraqaoa_part_info(part)
+            ids = np.arange(len(size), dtype=np.int32)
+            _capi.paraqaoa_part_upload(self.ctx, part)
+            t["partition"] = time.perf_counter() - t0
+            gam, bet, best, _ = _capi.paraqaoa_grid_search(self.ctx, part, ids, cfg.grid_points)
+            gam, bet = gam[:, None], bet[:, None]
+            val = best
+            if cfg.adam_steps > 0:
+                gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, 1, gam, bet, cfg.adam_steps,
+                                                        cfg.lr, cfg.h)
+            for depth in range(2, cfg.p + 1):
+                gam, bet = interp(gam, bet)
+                gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, depth, gam, bet,
+                                                        cfg.adam_steps, cfg.lr, cfg.h)
+            t["angles"] = time.perf_counter() - t0 - t["partition"]
+            _capi.paraqaoa_simulate_batch(self.ctx, part, ids, cfg.p, gam, bet,
+                                          _capi.SIM_EXPECT | _capi.SIM_KEEP_STATE)
+            ex = _capi.paraqaoa_expect(self.ctx, len(ids))
+            cand, cand_p = _capi.paraqaoa_topk(self.ctx, len(ids), cfg.K)
+            t["final"] = time.perf_counter() - t0 - t["partition"] - t["angles"]
+            side, cut = _capi.paraqaoa_merge(self.ctx, G, part, cand, cfg.K, cfg.L, cfg.beam)
+            t["merge"] = time.perf_counter() - t0 - t["partition"] - t["angles"] - t["final"]
+            t["total"] = time.perf_counter() - t0
+            return SolveResult(side, cut, gam, bet, ex, cand, cand_p, t)
+        finally:
+            _capi.paraqaoa_part_free(part)

@@ -1,0 +1,250 @@
+"""ctypes binding of libparaqaoa.so: one Python function per C entry point,
+same names, argument marshalling only (numpy arrays in, numpy arrays out).
+
+Every computation runs in the CUDA library. There is no CPU fallback: if
+the shared library is missing or cannot be loaded, importing this module's
+functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libparaqaoa.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "paraqaoa.h")
+
+OK = 0
+E_INVAL, E_TOO_MANY_QUBITS, E_ADMISSION, E_NOMEM = -1, -2, -3, -4
+E_SEARCH_TOO_LARGE, E_CUDA, E_TIMEOUT, E_NO_RESULT = -5, -6, -7, -8
+PART_BALANCED, PART_ALG1_LITERAL, PART_SIZES = 0, 1, 2
+SIM_EXPECT, SIM_KEEP_STATE = 0x1, 0x2
+TOPK_CANONICAL, TOPK_RAW = 0x0, 0x1
+KCLASS_LAYER_PASS, KCLASS_SMEM_SIM, KCLASS_TOPK, KCLASS_MERGE, KCLASS_OTHER = range(5)
+MAX_TOPK = 32
+MAX_SUBGRAPH_WEIGHT = 4095
+
+
+class ParaQAOAError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+_lib = None
+P = ctypes.c_void_p
+_SIGS = {
+    "paraqaoa_create": ([ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+    "paraqaoa_destroy": ([P], None),
+    "paraqaoa_set_stream": ([P, P], ctypes.c_int),
+    "paraqaoa_partition": ([P, ctypes.c_int32, ctypes.c_int32, P, ctypes.POINTER(P)], ctypes.c_int),
+    "paraqaoa_part_free": ([P], None),
+    "paraqaoa_part_info": ([P, P, P, P, P, P], ctypes.c_int),
+    "paraqaoa_part_edges": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "paraqaoa_part_upload": ([P, P, ctypes.c_int32], ctypes.c_int),
+    "paraqaoa_cut_table": ([P, P, ctypes.c_int32, P], ctypes.c_int),
+    "paraqaoa_simulate_batch": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_uint32], ctypes.c_int),
+    "paraqaoa_expect": ([P, ctypes.c_int32, P], ctypes.c_int),
+    "paraqaoa_topk": ([P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_uint32], ctypes.c_int),
+    "paraqaoa_state": ([P, ctypes.c_int32, P], ctypes.c_int),
+    "paraqaoa_merge": ([P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P, P], ctypes.c_int),
+    "paraqaoa_grid_search": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P], ctypes.c_int),
+    "paraqaoa_optimize": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                           ctypes.c_double, P, P, P], ctypes.c_int),
+    "paraqaoa_profile_enable": ([P, ctypes.c_int32], ctypes.c_int),
+    "paraqaoa_profile_read": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "paraqaoa_strerror": ([ctypes.c_int], ctypes.c_char_p),
+}
+
+
+def declared_symbols() -> list[str]:
+    """Every function the public header declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(paraqaoa_[a-z_]+)\s*\(", txt)))
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (build it first with build.py). Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: run `python -m paper_2603_26232_gb300.build` "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _arr(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise ParaQAOAError(rc, what)
+
+
+def strerror(code: int) -> str:
+    return load().paraqaoa_strerror(code).decode()
+
+
+# --------------------------------------------------------------------- objects
+class Graph:
+    """Host CSR arrays kept alive for the C struct that points into them."""
+
+    def __init__(self, n: int, row_ptr, col, w):
+        self.n = int(n)
+        self.row_ptr = _arr(row_ptr, np.int64)
+        self.col = _arr(col, np.int32)
+        self.w = _arr(w, np.int32)
+        self.csr = Csr(self.n, int(self.row_ptr[-1]), _ptr(self.row_ptr), _ptr(self.col), _ptr(self.w))
+
+    @classmethod
+    def of(cls, g):
+        return g if isinstance(g, Graph) else cls(g.n, g.row_ptr, g.col, g.w)
+
+
+def paraqaoa_create(device: int = 0, hbm_budget: int = 0):
+    h = P()
+    _check(load().paraqaoa_create(ctypes.byref(h), int(device), int(hbm_budget)), "paraqaoa_create")
+    return h
+
+
+def paraqaoa_destroy(ctx):
+    load().paraqaoa_destroy(ctx)
+
+
+def paraqaoa_set_stream(ctx, stream_handle: int | None):
+    _check(load().paraqaoa_set_stream(ctx, stream_handle), "paraqaoa_set_stream")
+
+
+def paraqaoa_partition(g: Graph, M: int, mode: int = PART_BALANCED, sizes=None):
+    h = P()
+    sz = None if sizes is None else _arr(sizes, np.int32)
+    _check(load().paraqaoa_partition(ctypes.byref(g.csr), int(M), int(mode), _ptr(sz), ctypes.byref(h)),
+           "paraqaoa_partition")
+    return h
+
+
+def paraqaoa_part_free(part):
+    load().paraqaoa_part_free(part)
+
+
+def paraqaoa_part_info(part):
+    M = np.zeros(1, np.int32)
+    _check(load().paraqaoa_part_info(part, _ptr(M), None, None, None, None), "paraqaoa_part_info")
+    m = int(M[0])
+    first = np.zeros(m, np.int32)
+    size = np.zeros(m, np.int32)
+    edges = np.zeros(m, np.int64)
+    weight = np.zeros(m, np.int64)
+    _check(load().paraqaoa_part_info(part, None, _ptr(first), _ptr(size), _ptr(edges), _ptr(weight)),
+           "paraqaoa_part_info")
+    return first, size, edges, weight
+
+
+def paraqaoa_part_edges(part, pid: int, count: int):
+    u = np.zeros(count, np.int32)
+    v = np.zeros(count, np.int32)
+    w = np.zeros(count, np.int32)
+    _check(load().paraqaoa_part_edges(part, int(pid), _ptr(u), _ptr(v), _ptr(w)), "paraqaoa_part_edges")
+    return u, v, w
+
+
+def paraqaoa_part_upload(ctx, part, force: bool = False):
+    _check(load().paraqaoa_part_upload(ctx, part, 1 if force else 0), "paraqaoa_part_upload")
+
+
+def paraqaoa_cut_table(ctx, part, pid: int, n: int) -> np.ndarray:
+    out = np.zeros(1 << n, np.uint16)
+    _check(load().paraqaoa_cut_table(ctx, part, int(pid), _ptr(out)), "paraqaoa_cut_table")
+    return out
+
+
+def paraqaoa_simulate_batch(ctx, part, ids, p: int, gamma, beta, flags: int = SIM_EXPECT):
+    ids = _arr(ids, np.int32)
+    g = _arr(gamma, np.float64).reshape(len(ids), p)
+    b = _arr(beta, np.float64).reshape(len(ids), p)
+    _check(load().paraqaoa_simulate_batch(ctx, part, _ptr(ids), len(ids), int(p), _ptr(g), _ptr(b),
+                                          int(flags)), "paraqaoa_simulate_batch")
+
+
+def paraqaoa_expect(ctx, count: int) -> np.ndarray:
+    out = np.zeros(count, np.float64)
+    _check(load().paraqaoa_expect(ctx, int(count), _ptr(out)), "paraqaoa_expect")
+    return out
+
+
+def paraqaoa_topk(ctx, count: int, K: int, flags: int = TOPK_CANONICAL):
+    z = np.zeros((count, K), np.uint32)
+    pr = np.zeros((count, K), np.float32)
+    _check(load().paraqaoa_topk(ctx, int(count), int(K), _ptr(z), _ptr(pr), int(flags)), "paraqaoa_topk")
+    return z, pr
+
+
+def paraqaoa_state(ctx, i: int, n: int) -> np.ndarray:
+    out = np.zeros(2 << n, np.float32)
+    _check(load().paraqaoa_state(ctx, int(i), _ptr(out)), "paraqaoa_state")
+    return out.view(np.complex64)
+
+
+def paraqaoa_merge(ctx, g: Graph, part, cand, K: int, L: int = 1, beam: int = 0):
+    cand = _arr(cand, np.uint32)
+    side = np.zeros(g.n, np.uint8)
+    cut = np.zeros(1, np.int64)
+    _check(load().paraqaoa_merge(ctx, ctypes.byref(g.csr), part, _ptr(cand), int(K), int(L), int(beam),
+                                 _ptr(side), _ptr(cut)), "paraqaoa_merge")
+    return side, int(cut[0])
+
+
+def paraqaoa_grid_search(ctx, part, ids, points: int = 16, want_values: bool = False):
+    ids = _arr(ids, np.int32)
+    n = len(ids)
+    g = np.zeros(n, np.float64)
+    b = np.zeros(n, np.float64)
+    best = np.zeros(n, np.float64)
+    vals = np.zeros(n * points * points, np.float64) if want_values else None
+    _check(load().paraqaoa_grid_search(ctx, part, _ptr(ids), n, int(points), _ptr(g), _ptr(b), _ptr(best),
+                                       _ptr(vals)), "paraqaoa_grid_search")
+    return g, b, best, (vals.reshape(n, points * points) if want_values else None)
+
+
+def paraqaoa_optimize(ctx, part, ids, p: int, gamma0, beta0, steps: int = 32, lr: float = 0.02,
+                      h: float = 1e-3):
+    ids = _arr(ids, np.int32)
+    n = len(ids)
+    g = np.array(gamma0, dtype=np.float64).reshape(n, p).copy()
+    b = np.array(beta0, dtype=np.float64).reshape(n, p).copy()
+    val = np.zeros(n, np.float64)
+    _check(load().paraqaoa_optimize(ctx, part, _ptr(ids), n, int(p), int(steps), float(lr), float(h),
+                                    _ptr(g), _ptr(b), _ptr(val)), "paraqaoa_optimize")
+    return g, b, val
+
+
+def paraqaoa_profile_enable(ctx, enable: bool = True):
+    _check(load().paraqaoa_profile_enable(ctx, 1 if enable else 0), "paraqaoa_profile_enable")
+
+
+def paraqaoa_profile_read(ctx, which: int):
+    n = np.zeros(1, np.int64)
+    ms = np.zeros(1, np.float64)
+    by = np.zeros(1, np.float64)
+    _check(load().paraqaoa_profile_read(ctx, int(which), _ptr(n), _ptr(ms), _ptr(by)), "paraqaoa_profile_read")
+    return int(n[0]), float(ms[0]), float(by[0])

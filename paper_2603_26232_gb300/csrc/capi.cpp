@@ -1,0 +1,1042 @@
+// C ABI of the ParaQAOA hot path: context, partition, admission, pass
+// scheduling and the host side of every entry point in include/paraqaoa.h.
+// Every numerical step runs in the CUDA kernels of this directory; this file
+// validates arguments, lays out device memory and enqueues launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "pq_internal.h"
+
+using namespace pq;
+
+namespace {
+
+std::atomic<uint64_t> g_part_serial{1};
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);  // synchronous: no queued kernel still uses it
+    p = nullptr;
+    cap = 0;
+    const size_t want = (bytes + 255) & ~size_t(255);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) cap = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+int cuda_rc(cudaError_t e) {
+  if (e == cudaSuccess) return PARAQAOA_OK;
+  if (e == cudaErrorMemoryAllocation) return PARAQAOA_E_NOMEM;
+  return PARAQAOA_E_CUDA;
+}
+
+#define PQ_CUDA(call)                       \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return cuda_rc(e_); \
+  } while (0)
+
+int bitlen(int64_t x) {
+  int b = 0;
+  while (x > 0) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+}  // namespace
+
+struct paraqaoa_part {
+  uint64_t serial;
+  int32_t nv = 0, M = 0;
+  std::vector<int32_t> first, size;
+  std::vector<int64_t> eoff;  // M+1 into eu/ev/ew
+  std::vector<int32_t> eu, ev, ew;
+  std::vector<int64_t> weight;
+  std::vector<int32_t> P;
+  std::vector<int32_t> plane_off;
+  std::vector<uint32_t> planes;
+};
+
+// A simulate plan: the instances of one batch and where their data lives.
+struct SimPlan {
+  int32_t count = 0, p = 0;
+  uint32_t flags = 0;
+  std::vector<InstDev> inst;
+  std::vector<int32_t> lists;                   // concatenated instance lists
+  std::pair<int32_t, int32_t> tiny{0, 0};       // offset, length into lists
+  std::map<int, std::pair<int32_t, int32_t>> smem, hbm;  // n -> (offset, length)
+  int64_t table_elems = 0, state_elems = 0, partial_elems = 0;
+  int32_t tabcap = 1;  // largest W + 1 of the batch (phase-table entries on chip)
+  bool valid = false;
+};
+
+struct paraqaoa_ctx {
+  int device = 0;
+  size_t budget = 0;
+  cudaStream_t own = nullptr, stream = nullptr;
+  int c_min = 3;  // fewest contiguous low qubits a high-group tile carries
+  // partition on the device
+  uint64_t part_serial = 0;
+  DevBuf d_subs, d_planes;
+  // simulate
+  SimPlan plan;
+  DevBuf d_inst, d_lists, d_gamma, d_beta, d_tables, d_states, d_partials, d_expect;
+  // top-K
+  DevBuf d_chunk_off, d_topk_scratch, d_topk_z, d_topk_p;
+  // merge
+  DevBuf m_first, m_size, m_level, m_cand, m_intra, m_eoff, m_eu, m_ev, m_ew, m_key, m_path;
+  DevBuf m_sides[2], m_score[2], m_rank[2], m_r2s[2], m_keys, m_nb;
+  // angle loop
+  DevBuf o_vals, o_best, o_theta, o_m, o_v, o_w, o_g2, o_b2;
+  // profiling
+  bool prof = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[PARAQAOA_KCLASS_COUNT] = {};
+  double ms[PARAQAOA_KCLASS_COUNT] = {}, bytes[PARAQAOA_KCLASS_COUNT] = {};
+};
+
+namespace {
+
+cudaEvent_t get_event(paraqaoa_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  paraqaoa_ctx* c;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(paraqaoa_ctx* c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+    if (c->prof) {
+      a = get_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof && a) {
+      cudaEvent_t b = get_event(c);
+      cudaEventRecord(b, c->stream);
+      c->pending.push_back({cls, a, b, bytes});
+    }
+  }
+};
+
+void prof_flush(paraqaoa_ctx* c) {
+  if (c->pending.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->pending) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    c->launches[r.cls] += 1;
+    c->ms[r.cls] += t;
+    c->bytes[r.cls] += r.bytes;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->pending.clear();
+}
+
+int validate_csr(const paraqaoa_csr* g) {
+  if (!g || g->n < 1 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && (!g->col || !g->w)))
+    return PARAQAOA_E_INVAL;
+  if (g->row_ptr[0] != 0 || g->row_ptr[g->n] != g->nnz) return PARAQAOA_E_INVAL;
+  int64_t up = 0, down = 0, wbal = 0;
+  for (int32_t u = 0; u < g->n; ++u) {
+    if (g->row_ptr[u + 1] < g->row_ptr[u]) return PARAQAOA_E_INVAL;
+    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
+      const int32_t v = g->col[k];
+      if (v < 0 || v >= g->n || v == u || g->w[k] <= 0) return PARAQAOA_E_INVAL;
+      if (u < v) {
+        ++up;
+        wbal += g->w[k];
+      } else {
+        ++down;
+        wbal -= g->w[k];
+      }
+    }
+  }
+  if (up != down || wbal != 0) return PARAQAOA_E_INVAL;  // not symmetric
+  return PARAQAOA_OK;
+}
+
+// Level (part index) at which each vertex is first assigned.
+std::vector<int32_t> levels_of(const paraqaoa_part* pt) {
+  std::vector<int32_t> lv(pt->nv, 0);
+  for (int32_t i = 0; i < pt->M; ++i)
+    for (int32_t v = (i == 0 ? 0 : 1); v < pt->size[i]; ++v) lv[pt->first[i] + v] = i;
+  return lv;
+}
+
+int upload_part(paraqaoa_ctx* c, const paraqaoa_part* pt, bool force) {
+  if (!force && c->part_serial == pt->serial) return PARAQAOA_OK;
+  std::vector<SubDev> subs(pt->M);
+  for (int32_t i = 0; i < pt->M; ++i) {
+    subs[i].n = pt->size[i];
+    subs[i].P = pt->P[i];
+    subs[i].W = (int32_t)std::min<int64_t>(pt->weight[i], 0x7fffffff);
+    subs[i].first = pt->first[i];
+    subs[i].plane_off = pt->plane_off[i];
+  }
+  PQ_CUDA(c->d_subs.ensure(sizeof(SubDev) * std::max<size_t>(subs.size(), 1)));
+  PQ_CUDA(c->d_planes.ensure(sizeof(uint32_t) * std::max<size_t>(pt->planes.size(), 1)));
+  PQ_CUDA(cudaMemcpyAsync(c->d_subs.p, subs.data(), sizeof(SubDev) * subs.size(),
+                          cudaMemcpyHostToDevice, c->stream));
+  if (!pt->planes.empty())
+    PQ_CUDA(cudaMemcpyAsync(c->d_planes.p, pt->planes.data(), sizeof(uint32_t) * pt->planes.size(),
+                            cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));  // host vectors are temporaries
+  c->part_serial = pt->serial;
+  return PARAQAOA_OK;
+}
+
+// Build the plan of a batch (validation, admission, memory layout).
+int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
+               int32_t p, uint32_t flags) {
+  SimPlan& pl = c->plan;
+  pl = SimPlan();
+  if (count < 1 || p < 1 || p > PARAQAOA_MAX_P || !ids) return PARAQAOA_E_INVAL;
+  pl.count = count;
+  pl.p = p;
+  pl.flags = flags;
+  pl.inst.resize(count);
+  const bool keep = flags & PARAQAOA_SIM_KEEP_STATE;
+  std::vector<int32_t> tiny;
+  std::map<int, std::vector<int32_t>> smem, hbm;
+  for (int32_t i = 0; i < count; ++i) {
+    const int32_t s = ids[i];
+    if (s < 0 || s >= pt->M) return PARAQAOA_E_INVAL;
+    const int n = pt->size[s];
+    if (n > PARAQAOA_MAX_QUBITS) return PARAQAOA_E_TOO_MANY_QUBITS;
+    if (pt->weight[s] > PARAQAOA_MAX_SUBGRAPH_WEIGHT) return PARAQAOA_E_INVAL;
+    InstDev& I = pl.inst[i];
+    std::memset(&I, 0, sizeof(I));
+    I.sub = s;
+    I.n = n;
+    I.P = pt->P[s];
+    I.W = (int32_t)pt->weight[s];
+    I.table_off = pl.table_elems;
+    pl.tabcap = std::max(pl.tabcap, I.W + 1);
+    pl.table_elems += (int64_t)p * (I.W + 1);
+    I.state_off = -1;
+    I.part_off = -1;
+    const bool big = n > kSmemMaxQubits;
+    if (big || keep) {
+      I.state_off = pl.state_elems;
+      pl.state_elems += int64_t(1) << n;
+    }
+    if (big) {
+      I.part_off = pl.partial_elems;
+      pl.partial_elems += int64_t(1) << (n - kTileBits);
+      hbm[n].push_back(i);
+    } else if (n >= 10) {
+      smem[n].push_back(i);
+    } else {
+      tiny.push_back(i);
+    }
+  }
+  pl.tabcap = (pl.tabcap + 15) & ~15;
+  auto add = [&](std::vector<int32_t>& v) {
+    std::pair<int32_t, int32_t> r((int32_t)pl.lists.size(), (int32_t)v.size());
+    pl.lists.insert(pl.lists.end(), v.begin(), v.end());
+    return r;
+  };
+  auto t = add(tiny);
+  pl.tiny = t;
+  for (auto& kv : smem) pl.smem[kv.first] = add(kv.second);
+  for (auto& kv : hbm) pl.hbm[kv.first] = add(kv.second);
+  // admission: every byte this batch puts on the device
+  const double need = (double)pl.state_elems * 8 + (double)pl.table_elems * 8 +
+                      (double)pl.partial_elems * 8 + (double)count * (sizeof(InstDev) + 8 + 16 * p) +
+                      (double)pl.lists.size() * 4;
+  if (need > (double)c->budget) return PARAQAOA_E_ADMISSION;
+  PQ_CUDA(c->d_inst.ensure(sizeof(InstDev) * count));
+  PQ_CUDA(c->d_lists.ensure(sizeof(int32_t) * std::max<size_t>(pl.lists.size(), 1)));
+  PQ_CUDA(c->d_gamma.ensure(sizeof(double) * count * p));
+  PQ_CUDA(c->d_beta.ensure(sizeof(double) * count * p));
+  PQ_CUDA(c->d_tables.ensure(sizeof(float2) * std::max<int64_t>(pl.table_elems, 1)));
+  PQ_CUDA(c->d_states.ensure(sizeof(float2) * std::max<int64_t>(pl.state_elems, 1)));
+  PQ_CUDA(c->d_partials.ensure(sizeof(double) * std::max<int64_t>(pl.partial_elems, 1)));
+  PQ_CUDA(c->d_expect.ensure(sizeof(double) * count));
+  PQ_CUDA(cudaMemcpyAsync(c->d_inst.p, pl.inst.data(), sizeof(InstDev) * count,
+                          cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(c->d_lists.p, pl.lists.data(), sizeof(int32_t) * pl.lists.size(),
+                          cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));  // pl vectors may change before the copy ran
+  pl.valid = true;
+  return PARAQAOA_OK;
+}
+
+// Enqueue the whole simulation of the current plan; angles in c->d_gamma/d_beta.
+int plan_run(paraqaoa_ctx* c) {
+  SimPlan& pl = c->plan;
+  const int32_t p = pl.p;
+  const bool keep = pl.flags & PARAQAOA_SIM_KEEP_STATE;
+  const bool want = pl.flags & PARAQAOA_SIM_EXPECT;
+  InstDev* inst = c->d_inst.as<InstDev>();
+  const int32_t* lists = c->d_lists.as<int32_t>();
+  const SubDev* subs = c->d_subs.as<SubDev>();
+  const uint32_t* planes = c->d_planes.as<uint32_t>();
+  float2* tables = c->d_tables.as<float2>();
+  float2* states = c->d_states.as<float2>();
+  double* partials = c->d_partials.as<double>();
+  double* expect = c->d_expect.as<double>();
+  {
+    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+    PQ_CUDA(launch_prep_layers(inst, pl.count, p, c->d_gamma.as<double>(), c->d_beta.as<double>(),
+                               tables, inst, c->stream));
+  }
+  if (pl.tiny.second > 0) {
+    ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, 0);
+    PQ_CUDA(launch_tiny_sim(inst, lists + pl.tiny.first, pl.tiny.second, p, subs, planes, tables,
+                            states, expect, keep, want, pl.tabcap, c->stream));
+  }
+  for (auto& kv : pl.smem) {
+    ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, keep ? (double)kv.second.second * 8.0 * (1 << kv.first) : 0.0);
+    PQ_CUDA(launch_smem_sim(kv.first, inst, lists + kv.second.first, kv.second.second, p, subs,
+                            planes, tables, states, expect, keep, want, pl.tabcap, c->stream));
+  }
+  for (auto& kv : pl.hbm) {
+    const int n = kv.first;
+    const auto sched = make_schedule(n, p, c->c_min, keep, want);
+    const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
+    for (const PassDesc& pd : sched) {
+      const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
+      ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
+      PQ_CUDA(launch_layer_pass(n, pd, inst, lists + kv.second.first, kv.second.second, subs,
+                                planes, tables, states, partials, pl.tabcap, c->stream));
+    }
+    if (want) {
+      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+      PQ_CUDA(launch_expect_reduce(inst, lists + kv.second.first, kv.second.second,
+                                   1 << (n - kTileBits), partials, expect, c->stream));
+    }
+  }
+  return PARAQAOA_OK;
+}
+
+}  // namespace
+
+namespace pq {
+
+// p layers over G qubit groups: group 0 = qubits [0, 13) (a tile is 2^13
+// consecutive amplitudes), groups 1.. split qubits [13, n) evenly, each tile
+// carrying the lowest 13 - g qubits (>= c_min) so that HBM accesses stay in
+// runs of 2^(13-g) amplitudes. Layer l visits the groups in increasing order
+// for even l and decreasing for odd l, so the last group of layer l is the
+// first of layer l+1 and one pass can finish layer l, apply the phase of
+// l+1 and start its mixer: 1 + p (G - 1) passes in all.
+std::vector<PassDesc> make_schedule(int n, int p, int c_min, bool keep, bool expect) {
+  const int TB = kTileBits;
+  struct Grp {
+    int c, s, mix_lo;
+  };
+  std::vector<Grp> grp;
+  grp.push_back({TB, TB, 0});
+  const int rest = n - TB;
+  const int gmax = TB - std::max(0, std::min(c_min, TB - 1));
+  const int H = (rest + gmax - 1) / gmax;
+  int s = TB;
+  for (int h = 0; h < H; ++h) {
+    const int g = rest / H + (h < rest % H ? 1 : 0);
+    grp.push_back({TB - g, s, TB - g});
+    s += g;
+  }
+  const int G = (int)grp.size();
+  auto mk = [&](int gi) {
+    PassDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.c = grp[gi].c;
+    d.s = grp[gi].s;
+    d.mix_lo = grp[gi].mix_lo;
+    d.layerA = d.layerP = d.layerB = -1;
+    return d;
+  };
+  std::vector<PassDesc> out;
+  PassDesc first = mk(0);
+  first.init = 1;
+  first.layerP = 0;
+  first.layerB = 0;
+  first.store = 1;
+  out.push_back(first);
+  for (int l = 0; l < p; ++l) {
+    std::vector<int> ord(G);
+    for (int i = 0; i < G; ++i) ord[i] = (l % 2 == 0) ? i : G - 1 - i;
+    for (int idx = 1; idx < G; ++idx) {
+      PassDesc d = mk(ord[idx]);
+      d.layerA = l;
+      if (idx < G - 1) {
+        d.store = 1;
+      } else if (l < p - 1) {
+        d.layerP = l + 1;
+        d.layerB = l + 1;
+        d.store = 1;
+      } else {
+        d.store = keep ? 1 : 0;
+        d.expect = expect ? 1 : 0;
+        d.last = 1;
+      }
+      out.push_back(d);
+    }
+  }
+  return out;
+}
+
+}  // namespace pq
+
+extern "C" {
+
+const char* paraqaoa_strerror(int code) {
+  switch (code) {
+    case PARAQAOA_OK: return "ok";
+    case PARAQAOA_E_INVAL: return "invalid argument";
+    case PARAQAOA_E_TOO_MANY_QUBITS: return "subgraph has too many vertices to simulate";
+    case PARAQAOA_E_ADMISSION: return "batch exceeds the context's device-memory budget";
+    case PARAQAOA_E_NOMEM: return "out of memory";
+    case PARAQAOA_E_SEARCH_TOO_LARGE: return "exhaustive merge space too large";
+    case PARAQAOA_E_CUDA: return "CUDA runtime error";
+    case PARAQAOA_E_TIMEOUT: return "device-side wait timed out";
+    case PARAQAOA_E_NO_RESULT: return "no matching simulate results";
+    default: return "unknown error";
+  }
+}
+
+int paraqaoa_create(paraqaoa_ctx** out, int device, size_t hbm_budget) {
+  if (!out) return PARAQAOA_E_INVAL;
+  *out = nullptr;
+  int ndev = 0;
+  PQ_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(device));
+  paraqaoa_ctx* c = new (std::nothrow) paraqaoa_ctx();
+  if (!c) return PARAQAOA_E_NOMEM;
+  c->device = device;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_rc(e);
+  }
+  c->stream = c->own;
+  if (hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    hbm_budget = (size_t)(0.8 * (double)fr);
+  }
+  c->budget = hbm_budget;
+  *out = c;
+  return PARAQAOA_OK;
+}
+
+void paraqaoa_destroy(paraqaoa_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  DevBuf* bufs[] = {&c->d_subs, &c->d_planes, &c->d_inst, &c->d_lists, &c->d_gamma, &c->d_beta,
+                    &c->d_tables, &c->d_states, &c->d_partials, &c->d_expect, &c->d_chunk_off,
+                    &c->d_topk_scratch, &c->d_topk_z, &c->d_topk_p, &c->m_first, &c->m_size,
+                    &c->m_level, &c->m_cand, &c->m_intra, &c->m_eoff, &c->m_eu, &c->m_ev, &c->m_ew,
+                    &c->m_key, &c->m_path, &c->m_sides[0], &c->m_sides[1], &c->m_score[0],
+                    &c->m_score[1], &c->m_rank[0], &c->m_rank[1], &c->m_r2s[0], &c->m_r2s[1],
+                    &c->m_keys, &c->m_nb, &c->o_vals, &c->o_best, &c->o_theta, &c->o_m, &c->o_v,
+                    &c->o_w, &c->o_g2, &c->o_b2};
+  for (DevBuf* b : bufs) b->release();
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+int paraqaoa_set_stream(paraqaoa_ctx* c, void* stream) {
+  if (!c) return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  c->stream = stream ? (cudaStream_t)stream : c->own;
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_partition(const paraqaoa_csr* g, int32_t M, int32_t mode, const int32_t* sizes,
+                       paraqaoa_part** out) {
+  if (!out) return PARAQAOA_E_INVAL;
+  *out = nullptr;
+  int rc = validate_csr(g);
+  if (rc != PARAQAOA_OK) return rc;
+  const int32_t nv = g->n;
+  if (M < 1 || M > nv) return PARAQAOA_E_INVAL;
+  std::vector<int32_t> first(M), size(M);
+  if (mode == PARAQAOA_PART_BALANCED) {
+    if (M > 1 && nv - 1 < M) return PARAQAOA_E_INVAL;
+    if (M == 1) {
+      first[0] = 0;
+      size[0] = nv;
+    } else {
+      const int32_t q = (nv - 1) / M, r = (nv - 1) % M;
+      int32_t o = 0;
+      for (int32_t i = 0; i < M; ++i) {
+        const int32_t t = q + (i < r ? 1 : 0);
+        first[i] = o;
+        size[i] = t + 1;
+        o += t;
+      }
+    }
+  } else if (mode == PARAQAOA_PART_ALG1_LITERAL) {
+    const int32_t s = nv / M - 1;
+    if (M > 1 && s < 1) return PARAQAOA_E_INVAL;
+    for (int32_t i = 0; i < M; ++i) {
+      first[i] = i * s;
+      size[i] = (i == M - 1) ? nv - i * s : s + 1;
+    }
+  } else if (mode == PARAQAOA_PART_SIZES) {
+    if (!sizes) return PARAQAOA_E_INVAL;
+    int64_t tot = 0;
+    for (int32_t i = 0; i < M; ++i) {
+      if (sizes[i] < (M > 1 ? 2 : 1)) return PARAQAOA_E_INVAL;
+      tot += sizes[i];
+    }
+    if (tot - (M - 1) != nv) return PARAQAOA_E_INVAL;
+    int32_t o = 0;
+    for (int32_t i = 0; i < M; ++i) {
+      first[i] = o;
+      size[i] = sizes[i];
+      o += sizes[i] - 1;
+    }
+  } else {
+    return PARAQAOA_E_INVAL;
+  }
+  paraqaoa_part* pt = new (std::nothrow) paraqaoa_part();
+  if (!pt) return PARAQAOA_E_NOMEM;
+  pt->serial = g_part_serial.fetch_add(1);
+  pt->nv = nv;
+  pt->M = M;
+  pt->first = first;
+  pt->size = size;
+  // GetSubgraph for all parts in one pass: an edge (u, v), u < v, lies in a
+  // part iff u is in the part where v is first assigned.
+  std::vector<int32_t> lv = levels_of(pt);
+  std::vector<int64_t> cnt(M, 0);
+  for (int32_t u = 0; u < nv; ++u)
+    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
+      const int32_t v = g->col[k];
+      if (u < v && u >= first[lv[v]]) cnt[lv[v]]++;
+    }
+  pt->eoff.assign(M + 1, 0);
+  for (int32_t i = 0; i < M; ++i) pt->eoff[i + 1] = pt->eoff[i] + cnt[i];
+  pt->eu.resize(pt->eoff[M]);
+  pt->ev.resize(pt->eoff[M]);
+  pt->ew.resize(pt->eoff[M]);
+  std::vector<int64_t> fill(pt->eoff.begin(), pt->eoff.end() - 1);
+  for (int32_t u = 0; u < nv; ++u)
+    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
+      const int32_t v = g->col[k];
+      if (u < v && u >= first[lv[v]]) {
+        const int32_t i = lv[v];
+        const int64_t at = fill[i]++;
+        pt->eu[at] = u - first[i];
+        pt->ev[at] = v - first[i];
+        pt->ew[at] = g->w[k];
+      }
+    }
+  // edges within a part are visited by increasing u, then v: sorted already
+  pt->weight.assign(M, 0);
+  pt->P.assign(M, 1);
+  pt->plane_off.assign(M, 0);
+  size_t planes = 0;
+  for (int32_t i = 0; i < M; ++i) {
+    int32_t wmax = 1;
+    for (int64_t e = pt->eoff[i]; e < pt->eoff[i + 1]; ++e) {
+      pt->weight[i] += pt->ew[e];
+      wmax = std::max(wmax, pt->ew[e]);
+    }
+    pt->P[i] = std::min(bitlen(wmax), kMaxPlanes);
+    pt->plane_off[i] = (int32_t)planes;
+    planes += (size_t)std::min(size[i], 32) * pt->P[i];
+  }
+  pt->planes.assign(planes, 0u);
+  for (int32_t i = 0; i < M; ++i) {
+    if (size[i] > 32) continue;  // bit-planes need n <= 32; such parts cannot be simulated
+    const int P = pt->P[i];
+    uint32_t* pl = pt->planes.data() + pt->plane_off[i];
+    for (int64_t e = pt->eoff[i]; e < pt->eoff[i + 1]; ++e) {
+      const int a = pt->eu[e], b = pt->ev[e], w = pt->ew[e];
+      for (int bit = 0; bit < P; ++bit)
+        if ((w >> bit) & 1) {
+          pl[a * P + bit] |= 1u << b;
+          pl[b * P + bit] |= 1u << a;
+        }
+    }
+  }
+  *out = pt;
+  return PARAQAOA_OK;
+}
+
+void paraqaoa_part_free(paraqaoa_part* pt) { delete pt; }
+
+int paraqaoa_part_info(const paraqaoa_part* pt, int32_t* M, int32_t* first, int32_t* size,
+                       int64_t* edges, int64_t* weight) {
+  if (!pt) return PARAQAOA_E_INVAL;
+  if (M) *M = pt->M;
+  for (int32_t i = 0; i < pt->M; ++i) {
+    if (first) first[i] = pt->first[i];
+    if (size) size[i] = pt->size[i];
+    if (edges) edges[i] = pt->eoff[i + 1] - pt->eoff[i];
+    if (weight) weight[i] = pt->weight[i];
+  }
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_part_edges(const paraqaoa_part* pt, int32_t id, int32_t* u, int32_t* v, int32_t* w) {
+  if (!pt || id < 0 || id >= pt->M) return PARAQAOA_E_INVAL;
+  for (int64_t e = pt->eoff[id], k = 0; e < pt->eoff[id + 1]; ++e, ++k) {
+    if (u) u[k] = pt->eu[e];
+    if (v) v[k] = pt->ev[e];
+    if (w) w[k] = pt->ew[e];
+  }
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_part_upload(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t force) {
+  if (!c || !pt) return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  return upload_part(c, pt, force != 0);
+}
+
+int paraqaoa_cut_table(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t id, uint16_t* out_host) {
+  if (!c || !pt || !out_host || id < 0 || id >= pt->M) return PARAQAOA_E_INVAL;
+  if (pt->size[id] > PARAQAOA_MAX_QUBITS) return PARAQAOA_E_TOO_MANY_QUBITS;
+  if (pt->weight[id] > 65535) return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  int rc = upload_part(c, pt, false);
+  if (rc) return rc;
+  const size_t bytes = sizeof(uint16_t) << pt->size[id];
+  PQ_CUDA(c->d_states.ensure(bytes));  // scratch: the cut table replaces any kept states
+  c->plan.valid = false;
+  {
+    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)bytes);
+    PQ_CUDA(launch_cut_table(c->d_subs.as<SubDev>() + id, pt->size[id], c->d_planes.as<uint32_t>(),
+                             c->d_states.as<uint16_t>(), c->stream));
+  }
+  PQ_CUDA(cudaMemcpyAsync(out_host, c->d_states.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_simulate_batch(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids,
+                            int32_t count, int32_t p, const double* gamma, const double* beta,
+                            uint32_t flags) {
+  if (!c || !pt || !gamma || !beta) return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  int rc = upload_part(c, pt, false);
+  if (rc) return rc;
+  rc = plan_build(c, pt, ids, count, p, flags);
+  if (rc) return rc;
+  PQ_CUDA(cudaMemcpyAsync(c->d_gamma.p, gamma, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(c->d_beta.p, beta, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
+  return plan_run(c);
+}
+
+int paraqaoa_expect(paraqaoa_ctx* c, int32_t count, double* out_host) {
+  if (!c || !out_host) return PARAQAOA_E_INVAL;
+  if (!c->plan.valid || c->plan.count != count || !(c->plan.flags & PARAQAOA_SIM_EXPECT))
+    return PARAQAOA_E_NO_RESULT;
+  PQ_CUDA(cudaSetDevice(c->device));
+  PQ_CUDA(cudaMemcpyAsync(out_host, c->d_expect.p, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_topk(paraqaoa_ctx* c, int32_t count, int32_t K, uint32_t* out_z, float* out_p,
+                  uint32_t flags) {
+  if (!c || !out_z || !out_p || K < 1 || K > PARAQAOA_MAX_TOPK) return PARAQAOA_E_INVAL;
+  if (!c->plan.valid || c->plan.count != count || !(c->plan.flags & PARAQAOA_SIM_KEEP_STATE))
+    return PARAQAOA_E_NO_RESULT;
+  PQ_CUDA(cudaSetDevice(c->device));
+  const int raw = (flags & PARAQAOA_TOPK_RAW) ? 1 : 0;
+  std::vector<int64_t> off(count + 1, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    const int n = c->plan.inst[i].n;
+    const int64_t cnt = raw ? (int64_t(1) << n) : (n == 1 ? 1 : (int64_t(1) << (n - 1)));
+    if (K > cnt) return PARAQAOA_E_INVAL;
+    off[i + 1] = off[i] + topk_chunks_of(n, raw);
+  }
+  PQ_CUDA(c->d_chunk_off.ensure(sizeof(int64_t) * (count + 1)));
+  PQ_CUDA(c->d_topk_scratch.ensure(sizeof(uint64_t) * 32 * std::max<int64_t>(off[count], 1)));
+  PQ_CUDA(c->d_topk_z.ensure(sizeof(uint32_t) * count * K));
+  PQ_CUDA(c->d_topk_p.ensure(sizeof(float) * count * K));
+  PQ_CUDA(cudaMemcpyAsync(c->d_chunk_off.p, off.data(), sizeof(int64_t) * (count + 1),
+                          cudaMemcpyHostToDevice, c->stream));
+  {
+    ProfScope ps(c, PARAQAOA_KCLASS_TOPK, 0);
+    PQ_CUDA(launch_topk_stages(c->d_inst.as<InstDev>(), count, K, raw, c->d_chunk_off.as<int64_t>(),
+                               off[count], c->d_states.as<float2>(), c->d_topk_scratch.as<uint64_t>(),
+                               c->d_topk_z.as<uint32_t>(), c->d_topk_p.as<float>(), c->stream));
+  }
+  PQ_CUDA(cudaMemcpyAsync(out_z, c->d_topk_z.p, sizeof(uint32_t) * count * K, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(out_p, c->d_topk_p.p, sizeof(float) * count * K, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_state(paraqaoa_ctx* c, int32_t i, float* out_host) {
+  if (!c || !out_host) return PARAQAOA_E_INVAL;
+  if (!c->plan.valid || !(c->plan.flags & PARAQAOA_SIM_KEEP_STATE)) return PARAQAOA_E_NO_RESULT;
+  if (i < 0 || i >= c->plan.count) return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  const InstDev& I = c->plan.inst[i];
+  PQ_CUDA(cudaMemcpyAsync(out_host, c->d_states.as<float2>() + I.state_off, sizeof(float2) << I.n,
+                          cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* pt,
+                   const uint32_t* cand, int32_t K, int32_t L, int64_t beam, uint8_t* out_side,
+                   int64_t* out_cut) {
+  if (!c || !pt || !cand || !out_side || !out_cut || K < 1 || K > PARAQAOA_MAX_TOPK || beam < 0)
+    return PARAQAOA_E_INVAL;
+  int rc = validate_csr(g);
+  if (rc) return rc;
+  if (g->n != pt->nv) return PARAQAOA_E_INVAL;
+  const int32_t M = pt->M, nv = pt->nv;
+  for (int32_t i = 0; i < M; ++i) {
+    if (pt->size[i] > 32) return PARAQAOA_E_TOO_MANY_QUBITS;
+    const uint32_t mask = pt->size[i] >= 32 ? 0xffffffffu : ((1u << pt->size[i]) - 1u);
+    for (int32_t j = 0; j < K; ++j)
+      if (cand[(int64_t)i * K + j] & ~mask) return PARAQAOA_E_INVAL;
+  }
+  int64_t total_w = 0;
+  for (int64_t k = 0; k < g->nnz; ++k) total_w += g->w[k];
+  total_w /= 2;
+  PQ_CUDA(cudaSetDevice(c->device));
+  rc = upload_part(c, pt, false);
+  if (rc) return rc;
+  // inter-partition edges bucketed by the level of their larger end
+  std::vector<int32_t> lv = levels_of(pt);
+  std::vector<int64_t> cnt(M + 1, 0);
+  for (int32_t u = 0; u < nv; ++u)
+    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
+      const int32_t v = g->col[k];
+      if (u < v && u < pt->first[lv[v]]) cnt[lv[v] + 1]++;
+    }
+  for (int32_t i = 0; i < M; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int32_t> eu(cnt[M]), ev(cnt[M]), ew(cnt[M]);
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  for (int32_t u = 0; u < nv; ++u)
+    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
+      const int32_t v = g->col[k];
+      if (u < v && u < pt->first[lv[v]]) {
+        const int64_t at = fill[lv[v]]++;
+        eu[at] = u;
+        ev[at] = v - pt->first[lv[v]];
+        ew[at] = g->w[k];
+      }
+    }
+  const int64_t E = std::max<int64_t>(cnt[M], 1);
+  PQ_CUDA(c->m_first.ensure(4 * M));
+  PQ_CUDA(c->m_size.ensure(4 * M));
+  PQ_CUDA(c->m_level.ensure(4 * (size_t)nv));
+  PQ_CUDA(c->m_cand.ensure(4 * (size_t)M * K));
+  PQ_CUDA(c->m_intra.ensure(8 * (size_t)M * K));
+  PQ_CUDA(c->m_eoff.ensure(8 * (size_t)(M + 1)));
+  PQ_CUDA(c->m_eu.ensure(4 * E));
+  PQ_CUDA(c->m_ev.ensure(4 * E));
+  PQ_CUDA(c->m_ew.ensure(4 * E));
+  auto up = [&](DevBuf& b, const void* h, size_t n) {
+    return n ? cudaMemcpyAsync(b.p, h, n, cudaMemcpyHostToDevice, c->stream) : cudaSuccess;
+  };
+  PQ_CUDA(up(c->m_first, pt->first.data(), 4 * M));
+  PQ_CUDA(up(c->m_size, pt->size.data(), 4 * M));
+  PQ_CUDA(up(c->m_level, lv.data(), 4 * (size_t)nv));
+  PQ_CUDA(up(c->m_cand, cand, 4 * (size_t)M * K));
+  PQ_CUDA(up(c->m_eoff, cnt.data(), 8 * (size_t)(M + 1)));
+  PQ_CUDA(up(c->m_eu, eu.data(), 4 * cnt[M]));
+  PQ_CUDA(up(c->m_ev, ev.data(), 4 * cnt[M]));
+  PQ_CUDA(up(c->m_ew, ew.data(), 4 * cnt[M]));
+  MergeDev md;
+  md.M = M;
+  md.K = K;
+  md.nv = nv;
+  md.words = (nv + 31) / 32;
+  md.first = c->m_first.as<int32_t>();
+  md.size = c->m_size.as<int32_t>();
+  md.level_of = c->m_level.as<int32_t>();
+  md.cand = c->m_cand.as<uint32_t>();
+  md.intra = c->m_intra.as<int64_t>();
+  md.eoff = c->m_eoff.as<int64_t>();
+  md.eu = c->m_eu.as<int32_t>();
+  md.ev = c->m_ev.as<int32_t>();
+  md.ew = c->m_ew.as<int32_t>();
+  std::vector<uint32_t> packed(md.words, 0u);
+  {
+    ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
+    PQ_CUDA(launch_cand_intra(c->d_subs.as<SubDev>(), c->d_planes.as<uint32_t>(), md.cand, M, K,
+                              c->m_intra.as<int64_t>(), c->stream));
+  }
+  if (beam == 0) {
+    // exhaustive level-aware DFS (Alg. 2)
+    const double space = std::pow((double)K, (double)M);
+    if (space > 1099511627776.0 || M > kMaxExhaustiveLevels) return PARAQAOA_E_SEARCH_TOO_LARGE;
+    if (total_w >= (int64_t(1) << 31)) return PARAQAOA_E_INVAL;
+    if (L < 1) L = 1;
+    if (L > M) L = M;
+    int64_t nprefix = 1;
+    for (int32_t i = 0; i < L; ++i) nprefix *= K;
+    while (nprefix > (int64_t(1) << 30) && L > 1) {
+      --L;
+      nprefix /= K;
+    }
+    PQ_CUDA(c->m_key.ensure(8));
+    PQ_CUDA(c->m_path.ensure(4 * (size_t)M));
+    PQ_CUDA(cudaMemsetAsync(c->m_key.p, 0, 8, c->stream));
+    unsigned long long key = 0;
+    std::vector<int32_t> path(M);
+    {
+      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
+      PQ_CUDA(launch_merge_dfs(md, L, nprefix, c->m_key.as<unsigned long long>(), c->stream));
+    }
+    PQ_CUDA(cudaMemcpyAsync(&key, c->m_key.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    PQ_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t winner = (int64_t)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
+    {
+      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
+      PQ_CUDA(launch_merge_dfs_path(md, L, nprefix, winner, c->m_path.as<int32_t>(), c->stream));
+    }
+    PQ_CUDA(cudaMemcpyAsync(path.data(), c->m_path.p, 4 * (size_t)M, cudaMemcpyDeviceToHost, c->stream));
+    PQ_CUDA(cudaStreamSynchronize(c->stream));
+    // assignment of the winning path (orientation as in the kernels)
+    std::vector<uint8_t> side(nv, 0);
+    for (int32_t l = 0; l < M; ++l) {
+      const int32_t f = pt->first[l], sz = pt->size[l];
+      uint32_t b = cand[(int64_t)l * K + path[l]];
+      if (l > 0 && (int)(b & 1u) != side[f]) b = ~b & (sz >= 32 ? 0xffffffffu : ((1u << sz) - 1u));
+      for (int32_t v = 0; v < sz; ++v) side[f + v] = (uint8_t)((b >> v) & 1u);
+    }
+    const uint8_t flip = side[0];
+    for (int32_t v = 0; v < nv; ++v) out_side[v] = side[v] ^ flip;
+    *out_cut = (int64_t)(key >> 32);
+    prof_flush(c);
+    return PARAQAOA_OK;
+  }
+  // beam reading
+  if ((int64_t)beam * K > kBeamSortCap) return PARAQAOA_E_INVAL;
+  if (total_w >= (int64_t(1) << 38)) return PARAQAOA_E_INVAL;
+  const int32_t B = (int32_t)beam;
+  for (int q = 0; q < 2; ++q) {
+    PQ_CUDA(c->m_sides[q].ensure(4 * (size_t)B * md.words));
+    PQ_CUDA(c->m_score[q].ensure(8 * (size_t)B));
+    PQ_CUDA(c->m_rank[q].ensure(4 * (size_t)B));
+    PQ_CUDA(c->m_r2s[q].ensure(4 * (size_t)B));
+  }
+  PQ_CUDA(c->m_keys.ensure(8 * (size_t)B * K));
+  PQ_CUDA(c->m_nb.ensure(4));
+  PQ_CUDA(cudaMemsetAsync(c->m_sides[0].p, 0, 4 * (size_t)md.words, c->stream));
+  PQ_CUDA(cudaMemsetAsync(c->m_score[0].p, 0, 8, c->stream));
+  PQ_CUDA(cudaMemsetAsync(c->m_rank[0].p, 0, 4, c->stream));
+  PQ_CUDA(cudaMemsetAsync(c->m_r2s[0].p, 0, 4, c->stream));
+  int32_t nb = 1;
+  int cur = 0;
+  for (int32_t l = 0; l < M; ++l) {
+    const int nx = cur ^ 1;
+    {
+      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
+      PQ_CUDA(launch_beam_level(md, l, nb, B, c->m_keys.as<uint64_t>(), c->m_sides[cur].as<uint32_t>(),
+                                c->m_score[cur].as<int64_t>(), c->m_rank[cur].as<int32_t>(),
+                                c->m_r2s[cur].as<int32_t>(), c->m_sides[nx].as<uint32_t>(),
+                                c->m_score[nx].as<int64_t>(), c->m_rank[nx].as<int32_t>(),
+                                c->m_r2s[nx].as<int32_t>(), c->m_nb.as<int32_t>(), c->stream));
+    }
+    nb = (int32_t)std::min<int64_t>((int64_t)nb * K, B);
+    cur = nx;
+  }
+  int64_t best = 0;
+  PQ_CUDA(cudaMemcpyAsync(packed.data(), c->m_sides[cur].p, 4 * (size_t)md.words, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(&best, c->m_score[cur].p, 8, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  const uint8_t flip = (uint8_t)(packed[0] & 1u);
+  for (int32_t v = 0; v < nv; ++v) out_side[v] = (uint8_t)(((packed[v >> 5] >> (v & 31)) & 1u) ^ flip);
+  *out_cut = best;
+  prof_flush(c);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids,
+                         int32_t count, int32_t points, double* out_gamma, double* out_beta,
+                         double* out_best, double* out_values) {
+  if (!c || !pt || !ids || count < 1 || points < 1 || points > 1024 || !out_gamma || !out_beta || !out_best)
+    return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  int rc = upload_part(c, pt, false);
+  if (rc) return rc;
+  const int32_t G = points * points;
+  const int64_t total = (int64_t)count * G;
+  if (total > 0x7fffffff) return PARAQAOA_E_INVAL;
+  std::vector<int32_t> inst_ids(total);
+  std::vector<double> gam(total), bet(total);
+  const double pi = 3.14159265358979323846;
+  for (int32_t s = 0; s < count; ++s)
+    for (int32_t k = 0; k < G; ++k) {
+      inst_ids[(int64_t)s * G + k] = ids[s];
+      gam[(int64_t)s * G + k] = pi * (double)(k / points) / (double)points;
+      bet[(int64_t)s * G + k] = 0.5 * pi * (double)(k % points) / (double)points;
+    }
+  PQ_CUDA(c->o_vals.ensure(sizeof(double) * total));
+  PQ_CUDA(c->o_best.ensure(sizeof(double) * 3 * count));
+  // chunk subgraphs so that each batch passes admission
+  int32_t s0 = 0;
+  while (s0 < count) {
+    int32_t ns = count - s0;
+    for (;;) {
+      rc = plan_build(c, pt, inst_ids.data() + (int64_t)s0 * G, ns * G, 1, PARAQAOA_SIM_EXPECT);
+      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
+      ns = (ns + 1) / 2;
+    }
+    if (rc) return rc;
+    PQ_CUDA(cudaMemcpyAsync(c->d_gamma.p, gam.data() + (int64_t)s0 * G, sizeof(double) * ns * G, cudaMemcpyHostToDevice, c->stream));
+    PQ_CUDA(cudaMemcpyAsync(c->d_beta.p, bet.data() + (int64_t)s0 * G, sizeof(double) * ns * G, cudaMemcpyHostToDevice, c->stream));
+    rc = plan_run(c);
+    if (rc) return rc;
+    PQ_CUDA(cudaMemcpyAsync(c->o_vals.as<double>() + (int64_t)s0 * G, c->d_expect.p, sizeof(double) * ns * G,
+                            cudaMemcpyDeviceToDevice, c->stream));
+    PQ_CUDA(cudaStreamSynchronize(c->stream));  // host angle arrays are reused by the next chunk
+    s0 += ns;
+  }
+  double* ob = c->o_best.as<double>();
+  {
+    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+    PQ_CUDA(launch_grid_argmax(c->o_vals.as<double>(), count, points, ob, ob + count, ob + 2 * count, c->stream));
+  }
+  PQ_CUDA(cudaMemcpyAsync(out_gamma, ob, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(out_beta, ob + count, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(out_best, ob + 2 * count, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  if (out_values)
+    PQ_CUDA(cudaMemcpyAsync(out_values, c->o_vals.p, sizeof(double) * total, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  c->plan.valid = false;
+  prof_flush(c);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
+                      int32_t p, int32_t steps, double lr, double h, double* gamma_io,
+                      double* beta_io, double* out_value) {
+  if (!c || !pt || !ids || count < 1 || p < 1 || p > PARAQAOA_MAX_P || steps < 0 || !(h > 0) ||
+      !gamma_io || !beta_io || !out_value)
+    return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  int rc = upload_part(c, pt, false);
+  if (rc) return rc;
+  const int32_t D = 2 * p, E = 4 * p;
+  std::vector<double> theta((size_t)count * D), wsum(count);
+  for (int32_t s = 0; s < count; ++s) {
+    if (ids[s] < 0 || ids[s] >= pt->M) return PARAQAOA_E_INVAL;
+    for (int32_t l = 0; l < p; ++l) {
+      theta[(size_t)s * D + l] = gamma_io[(size_t)s * p + l];
+      theta[(size_t)s * D + p + l] = beta_io[(size_t)s * p + l];
+    }
+    wsum[s] = (double)std::max<int64_t>(pt->weight[ids[s]], 1);
+  }
+  PQ_CUDA(c->o_theta.ensure(sizeof(double) * count * D));
+  PQ_CUDA(c->o_m.ensure(sizeof(double) * count * D));
+  PQ_CUDA(c->o_v.ensure(sizeof(double) * count * D));
+  PQ_CUDA(c->o_w.ensure(sizeof(double) * count));
+  PQ_CUDA(cudaMemcpyAsync(c->o_theta.p, theta.data(), sizeof(double) * count * D, cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(c->o_w.p, wsum.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaMemsetAsync(c->o_m.p, 0, sizeof(double) * count * D, c->stream));
+  PQ_CUDA(cudaMemsetAsync(c->o_v.p, 0, sizeof(double) * count * D, c->stream));
+  if (steps > 0) {
+    std::vector<int32_t> ev_ids((size_t)count * E);
+    for (int32_t s = 0; s < count; ++s)
+      for (int32_t e = 0; e < E; ++e) ev_ids[(size_t)s * E + e] = ids[s];
+    rc = plan_build(c, pt, ev_ids.data(), count * E, p, PARAQAOA_SIM_EXPECT);
+    if (rc) return rc;
+    for (int32_t t = 1; t <= steps; ++t) {
+      {
+        ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+        PQ_CUDA(launch_adam_shifts(c->o_theta.as<double>(), count, p, h, c->d_gamma.as<double>(),
+                                   c->d_beta.as<double>(), c->stream));
+      }
+      rc = plan_run(c);
+      if (rc) return rc;
+      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+      PQ_CUDA(launch_adam_update(c->d_expect.as<double>(), c->o_w.as<double>(), count, p, h, lr, t,
+                                 c->o_theta.as<double>(), c->o_m.as<double>(), c->o_v.as<double>(),
+                                 c->stream));
+    }
+  }
+  rc = plan_build(c, pt, ids, count, p, PARAQAOA_SIM_EXPECT);
+  if (rc) return rc;
+  {
+    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+    PQ_CUDA(launch_theta_split(c->o_theta.as<double>(), count, p, c->d_gamma.as<double>(),
+                               c->d_beta.as<double>(), c->stream));
+  }
+  rc = plan_run(c);
+  if (rc) return rc;
+  PQ_CUDA(cudaMemcpyAsync(gamma_io, c->d_gamma.p, sizeof(double) * count * p, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(beta_io, c->d_beta.p, sizeof(double) * count * p, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(out_value, c->d_expect.p, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_profile_enable(paraqaoa_ctx* c, int32_t enable) {
+  if (!c) return PARAQAOA_E_INVAL;
+  prof_flush(c);
+  c->prof = enable != 0;
+  for (int k = 0; k < PARAQAOA_KCLASS_COUNT; ++k) {
+    c->launches[k] = 0;
+    c->ms[k] = 0;
+    c->bytes[k] = 0;
+  }
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_profile_read(paraqaoa_ctx* c, int32_t which, int64_t* launches, double* ms,
+                          double* bytes) {
+  if (!c || which < 0 || which >= PARAQAOA_KCLASS_COUNT) return PARAQAOA_E_INVAL;
+  prof_flush(c);
+  if (launches) *launches = c->launches[which];
+  if (ms) *ms = c->ms[which];
+  if (bytes) *bytes = c->bytes[which];
+  return PARAQAOA_OK;
+}
+
+}  // extern "C"

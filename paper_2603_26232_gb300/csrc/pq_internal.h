@@ -1,0 +1,128 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/paraqaoa.h"
+
+namespace pq {
+
+// Tile geometry of the HBM-streaming layer passes: 2^kTileBits amplitudes
+// per CTA (64 KB of complex64), 32 amplitudes per thread in registers.
+constexpr int kTileBits = 13;
+constexpr int kRegBits = 5;
+constexpr int kSmemMaxQubits = 14;  // states of <= 14 qubits stay on chip
+constexpr int kTinyMaxQubits = 9;   // n <= 9: one small CTA, plain loops
+constexpr int kMaxPlanes = 16;      // weight bit-planes (weights < 2^16)
+
+// One subgraph on the device. Adjacency is stored as bit-planes: bit v of
+// planes[u*P + b] is bit b of w_uv (0 when u, v are not adjacent), so the
+// weighted neighbourhood of u restricted to a vertex mask m has weight
+// sum_b 2^b popc(planes[u*P+b] & m).
+struct SubDev {
+  int32_t n, P, W, first;
+  int32_t plane_off;  // into the planes array
+  int32_t pad[3];
+};
+
+// One simulated instance (a subgraph at one set of angles).
+struct InstDev {
+  int32_t sub;
+  int32_t n, P, W;
+  int64_t state_off;  // float2 offset of its state buffer (-1: none)
+  int64_t table_off;  // float2 offset of its p phase tables of W+1 entries
+  int64_t part_off;   // offset of its per-tile expectation partials
+  float mu[PARAQAOA_MAX_P];  // mixer butterfly coefficient per layer
+  float2 final_scale;        // lambda_p: scalar the last mixer left out
+  float final_scale2;        // |lambda_p|^2
+  int32_t pad;
+};
+
+// One layer pass over every tile of a group of same-size instances.
+struct PassDesc {
+  int32_t c;        // local bits [0, c) are qubits [0, c) (contiguous in HBM)
+  int32_t s;        // local bits [c, kTileBits) are qubits [s, s + kTileBits - c)
+  int32_t mix_lo;   // local bits >= mix_lo are mixed by this pass
+  int32_t layerA;   // finish the mixer of this layer (-1: none)
+  int32_t layerP;   // apply this layer's cost phase (-1: none)
+  int32_t layerB;   // start the mixer of this layer (-1: none)
+  int32_t init;     // start from |+>^n instead of loading
+  int32_t store;    // write the tile back
+  int32_t expect;   // reduce sum |psi|^2 C into the tile partial
+  int32_t last;     // the final pass (stores apply lambda_p)
+};
+
+// Kernel launchers (sim_kernels.cu). All enqueue on `st` and return the
+// launch error (cudaSuccess when queued).
+cudaError_t launch_prep_layers(const InstDev* inst, int32_t count, int32_t p, const double* gamma,
+                               const double* beta, float2* tables, InstDev* inst_rw,
+                               cudaStream_t st);
+cudaError_t launch_tiny_sim(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t p,
+                            const SubDev* subs, const uint32_t* planes, const float2* tables,
+                            float2* states, double* expect, int32_t keep, int32_t want_expect,
+                            int32_t tabcap, cudaStream_t st);
+cudaError_t launch_smem_sim(int n, const InstDev* inst, const int32_t* list, int32_t nlist,
+                            int32_t p, const SubDev* subs, const uint32_t* planes,
+                            const float2* tables, float2* states, double* expect, int32_t keep,
+                            int32_t want_expect, int32_t tabcap, cudaStream_t st);
+cudaError_t launch_layer_pass(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                              int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                              const float2* tables, float2* states, double* partials,
+                              int32_t tabcap, cudaStream_t st);
+cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32_t nlist,
+                                 int32_t tiles, const double* partials, double* expect,
+                                 cudaStream_t st);
+cudaError_t launch_cut_table(const SubDev* sub_dev_one, int n, const uint32_t* planes,
+                             uint16_t* out, cudaStream_t st);
+cudaError_t launch_topk_stages(const InstDev* inst, int32_t count, int32_t K, int32_t raw,
+                               const int64_t* chunk_off_dev, int64_t total_chunks,
+                               const float2* states, uint64_t* scratch, uint32_t* out_z,
+                               float* out_p, cudaStream_t st);
+int64_t topk_chunks_of(int n, int raw);
+
+// Merge (merge_kernels.cu).
+struct MergeDev {
+  int32_t M, K, nv, words;
+  const int32_t* first;     // M
+  const int32_t* size;      // M
+  const int32_t* level_of;  // nv: level at which the vertex is first assigned
+  const uint32_t* cand;     // M*K
+  const int64_t* intra;     // M*K
+  const int64_t* eoff;      // M+1: inter edges bucketed by the level of their larger end
+  const int32_t* eu;        // global smaller end
+  const int32_t* ev;        // local index of the larger end in its level's part
+  const int32_t* ew;
+};
+constexpr int kMaxExhaustiveLevels = 64;
+constexpr int kBeamSortCap = 8192;
+cudaError_t launch_cand_intra(const SubDev* subs, const uint32_t* planes, const uint32_t* cand,
+                              int32_t M, int32_t K, int64_t* intra, cudaStream_t st);
+cudaError_t launch_merge_dfs(const MergeDev& md, int32_t L, int64_t nprefix,
+                             unsigned long long* best_key, cudaStream_t st);
+cudaError_t launch_merge_dfs_path(const MergeDev& md, int32_t L, int64_t nprefix, int64_t winner,
+                                  int32_t* path, cudaStream_t st);
+cudaError_t launch_beam_level(const MergeDev& md, int32_t l, int32_t nb, int64_t beam,
+                              uint64_t* keys, const uint32_t* sides, const int64_t* score,
+                              const int32_t* rank, const int32_t* rank2slot, uint32_t* nsides,
+                              int64_t* nscore, int32_t* nrank, int32_t* nrank2slot,
+                              int32_t* nb_out, cudaStream_t st);
+
+// Angle loop (opt_kernels.cu).
+cudaError_t launch_grid_argmax(const double* vals, int32_t S, int32_t points, double* gamma,
+                               double* beta, double* best, cudaStream_t st);
+cudaError_t launch_adam_shifts(const double* theta, int32_t S, int32_t p, double h,
+                               double* gamma, double* beta, cudaStream_t st);
+cudaError_t launch_adam_update(const double* expect, const double* wsum, int32_t S, int32_t p,
+                               double h, double lr, int32_t t, double* theta, double* m, double* v,
+                               cudaStream_t st);
+cudaError_t launch_theta_split(const double* theta, int32_t S, int32_t p, double* gamma,
+                               double* beta, cudaStream_t st);
+
+// Pass schedule for an n-qubit instance group (layer_pass.cu host helper).
+std::vector<PassDesc> make_schedule(int n, int p, int c_min, bool keep, bool expect);
+
+}  // namespace pq

@@ -1,0 +1,773 @@
+// QAOA state-vector kernels for sm_103a: cost phase, mixer, <C>, cut table.
+//
+// The state is complex64 (float2). A layer l applies exp(-i gamma_l C(z))
+// (Sec. 2.2, the diagonal cost unitary of the Max-Cut objective of Sec. 2.1)
+// and then exp(-i beta_l X_j) on every qubit j (the transverse-field mixer).
+//
+// Mixer arithmetic. exp(-i b X) = cos b I - i sin b X. Writing it as
+//   cos b (I + i mu X),  mu = -tan b      when |cos b| >= |sin b|, or
+//   (-i sin b) X (I + i mu X), mu = cot b otherwise,
+// every qubit costs one butterfly (a, b) -> (a + i mu b, b + i mu a), two
+// FMAs per amplitude, and the scalars cos^n b or (-i sin b)^n of a whole layer
+// are folded into the next layer's phase table (or applied once at the end).
+// The factor X^{(x)n} of the second form is dropped: |+>^n is invariant under
+// the global flip and both unitaries commute with it (C(z) = C(not z)), so
+// it acts as the identity on every state the circuit reaches.
+//
+// Cut values are integers computed on the fly from adjacency bit-planes, so
+// the phase exp(-i gamma C) is a lookup into a table of W+1 entries built in
+// FP64; nothing but the state itself moves through HBM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "pq_internal.h"
+
+namespace pq {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// (x, y) -> (x + i mu y, y + i mu x)
+__device__ __forceinline__ void bfly(float2& x, float2& y, float mu) {
+  float2 nx = make_float2(fmaf(-mu, y.y, x.x), fmaf(mu, y.x, x.y));
+  float2 ny = make_float2(fmaf(-mu, x.y, y.x), fmaf(mu, x.x, y.y));
+  x = nx;
+  y = ny;
+}
+
+// C(z) = sum over u with z_u = 1 of the weight of u's neighbours with z_v = 0.
+__device__ __forceinline__ int cut_eval(uint32_t z, const uint32_t* pl, int n, int P) {
+  int c = 0;
+  for (int u = 0; u < n; ++u) {
+    uint32_t m = ((z >> u) & 1u) ? ~z : 0u;
+    const uint32_t* q = pl + u * P;
+    for (int b = 0; b < P; ++b) c += __popc(q[b] & m) << b;
+  }
+  return c;
+}
+
+// Change of C when qubit u (not in z0, u in kmask) is set, counting only
+// neighbours outside kmask: weight to unset outsiders minus weight to set ones.
+__device__ __forceinline__ int kappa(uint32_t z0, uint32_t kmask, int u, const uint32_t* pl, int P) {
+  const uint32_t* q = pl + u * P;
+  int c = 0;
+  for (int b = 0; b < P; ++b) c += (__popc(q[b] & ~(z0 | kmask)) - __popc(q[b] & z0)) << b;
+  return c;
+}
+
+// Phase-table index: a cut value is in [0, W] by construction; the clamp keeps
+// the shared-memory read in bounds even if a caller's data broke that.
+__device__ __forceinline__ uint32_t tix(int c, int W) { return min((uint32_t)c, (uint32_t)W); }
+
+// Shared-memory slot of local index li: one pad element after every 32, which
+// makes every register-layout transpose bank-conflict free. It is additive
+// over disjoint bits (pad(t | k) = pad(t) + pad(k)), so a thread's addresses
+// are one base register plus compile-time offsets.
+__host__ __device__ __forceinline__ constexpr uint32_t pad(uint32_t li) { return li + (li >> 5); }
+template <int TB>
+__host__ __device__ constexpr int padded_elems() { return (1 << TB) + (1 << (TB - 5)); }
+
+// Register layouts of a 2^TB tile held by 2^(TB-5) threads x 32 registers.
+// Layout RHO puts 5 local index bits in the register index k:
+//   RHO 0: bits [TB-5, TB)   (load/store layout: lanes are consecutive)
+//   RHO 1: bits [TB-10, TB-5)
+//   RHO 2: bits [0, 5)
+// and the remaining bits, in increasing order, in the thread index.
+template <int TB, int RHO>
+__device__ __forceinline__ uint32_t li_of(uint32_t tid, uint32_t k) {
+  if constexpr (RHO == 0) {
+    return tid | (k << (TB - 5));
+  } else if constexpr (RHO == 1) {
+    constexpr int lb = TB - 10;
+    return (tid & ((1u << lb) - 1u)) | (k << lb) | ((tid >> lb) << (TB - 5));
+  } else {
+    return k | (tid << 5);
+  }
+}
+
+template <int TB>
+__device__ __forceinline__ uint32_t li0_rt(int rho, uint32_t tid) {
+  if (rho == 0) return li_of<TB, 0>(tid, 0);
+  if (rho == 1) return li_of<TB, 1>(tid, 0);
+  return li_of<TB, 2>(tid, 0);
+}
+
+__host__ __device__ __forceinline__ int slot_lb(int TB, int rho, int j) {
+  return rho == 0 ? TB - 5 + j : (rho == 1 ? TB - 10 + j : j);
+}
+
+template <int TB, int FROM, int TO>
+__device__ __forceinline__ void transpose(float2 (&a)[32], float2* sm, uint32_t tid) {
+  float2* pf = sm + pad(li_of<TB, FROM>(tid, 0));
+  float2* pt = sm + pad(li_of<TB, TO>(tid, 0));
+#pragma unroll
+  for (int k = 0; k < 32; ++k) pf[pad(li_of<TB, FROM>(0, k))] = a[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 32; ++k) a[k] = pt[pad(li_of<TB, TO>(0, k))];
+  __syncthreads();
+}
+
+template <int TB>
+__device__ __forceinline__ void goto_layout(float2 (&a)[32], float2* sm, uint32_t tid, int& cur, int to) {
+  if (cur == to) return;
+  const int code = cur * 3 + to;
+  if (code == 1) transpose<TB, 0, 1>(a, sm, tid);
+  else if (code == 2) transpose<TB, 0, 2>(a, sm, tid);
+  else if (code == 3) transpose<TB, 1, 0>(a, sm, tid);
+  else if (code == 5) transpose<TB, 1, 2>(a, sm, tid);
+  else if (code == 6) transpose<TB, 2, 0>(a, sm, tid);
+  else transpose<TB, 2, 1>(a, sm, tid);
+  cur = to;
+}
+
+__device__ __forceinline__ void mix_regs(float2 (&a)[32], float mu, uint32_t mask) {
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    if ((mask >> j) & 1u) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        if (!((k >> j) & 1)) bfly(a[k], a[k | (1 << j)], mu);
+    }
+  }
+}
+
+// Per-layout cut decomposition shared by the CTA: for the 5 register qubits
+// Kq of layout rho, ckk[k] = C restricted to edges inside Kq at assignment k.
+struct LayoutCut {
+  int kq[3][5];
+  uint32_t kmask[3];
+  int ckk[3][32];
+  int pad[2];  // 16-byte multiple: a double buffer follows it in shared memory
+};
+static_assert(sizeof(LayoutCut) % 16 == 0, "shared-memory carve-up needs 16-byte multiples");
+
+// Fill LayoutCut for the layouts in use. qubit(lb) maps a local bit to a qubit.
+template <int TB>
+__device__ void build_layout_cut(LayoutCut& lc, int nrounds, int c, int s, const uint32_t* pl,
+                                 int P, uint32_t tid) {
+  if (tid < 3) {
+    int rho = tid;
+    uint32_t m = 0;
+    for (int j = 0; j < 5; ++j) {
+      int lb = slot_lb(TB, rho, j);
+      int q = lb < c ? lb : s + (lb - c);
+      lc.kq[rho][j] = q;
+      m |= 1u << q;
+    }
+    lc.kmask[rho] = m;
+  }
+  __syncthreads();
+  for (uint32_t q = tid; q < 32u * (uint32_t)nrounds; q += (1u << (TB - 5))) {
+    int rho = q >> 5, k = q & 31;
+    uint32_t zk = 0;
+    for (int j = 0; j < 5; ++j)
+      if ((k >> j) & 1) zk |= 1u << lc.kq[rho][j];
+    int cc = 0;
+    for (int j = 0; j < 5; ++j) {
+      if (!((k >> j) & 1)) continue;
+      const uint32_t* row = pl + lc.kq[rho][j] * P;
+      for (int b = 0; b < P; ++b) cc += __popc(row[b] & lc.kmask[rho] & ~zk) << b;
+    }
+    lc.ckk[rho][k] = cc;
+  }
+  __syncthreads();
+}
+
+// Cut values of this thread's 32 amplitudes in layout rho: C = C0 + ckk[k] +
+// sum of kap[j] over the set bits j of k.
+struct ThreadCut {
+  int C0;
+  int kap[5];
+};
+
+__device__ __forceinline__ ThreadCut thread_cut(uint32_t z0, const LayoutCut& lc, int rho,
+                                                const uint32_t* pl, int n, int P) {
+  ThreadCut t;
+  t.C0 = cut_eval(z0, pl, n, P);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) t.kap[j] = kappa(z0, lc.kmask[rho], lc.kq[rho][j], pl, P);
+  return t;
+}
+
+__device__ __forceinline__ int cut_of_reg(const ThreadCut& t, const int* ckk, int k) {
+  int c = t.C0 + ckk[k];
+#pragma unroll
+  for (int j = 0; j < 5; ++j)
+    if ((k >> j) & 1) c += t.kap[j];
+  return c;
+}
+
+// Deterministic block sum of one double per thread (fixed reduction order).
+__device__ __forceinline__ double block_sum(double v, double* red, uint32_t tid, uint32_t nt) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31u) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (uint32_t w = 0; w < (nt >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Per-instance layer constants: phase tables tab_l[c] = exp(-i gamma_l c) S_l
+// in FP64 rounded to complex64, with S_0 = 2^(-n/2) (the |+>^n amplitude)
+// and S_l = lambda_{l-1}, the scalar left out of layer l-1's mixer.
+__global__ void k_prep_layers(const InstDev* __restrict__ inst_ro, int32_t p,
+                              const double* __restrict__ gamma, const double* __restrict__ beta,
+                              float2* __restrict__ tables, InstDev* __restrict__ inst_rw) {
+  const int i = blockIdx.x;
+  const InstDev I = inst_ro[i];
+  const int n = I.n, W = I.W;
+  double sre = pow(2.0, -0.5 * n), sim = 0.0;  // S_0
+  for (int l = 0; l < p; ++l) {
+    const double g = gamma[(int64_t)i * p + l];
+    float2* tab = tables + I.table_off + (int64_t)l * (W + 1);
+    for (int c = threadIdx.x; c <= W; c += blockDim.x) {
+      double sn, cs;
+      sincos(g * (double)c, &sn, &cs);  // exp(-i g c) = cs - i sn
+      tab[c] = make_float2((float)(cs * sre + sn * sim), (float)(cs * sim - sn * sre));
+    }
+    const double b = beta[(int64_t)i * p + l];
+    double sb, cb;
+    sincos(b, &sb, &cb);
+    double lre, lim, mu;
+    if (fabs(cb) >= fabs(sb)) {
+      mu = -sb / cb;
+      lre = pow(cb, (double)n);
+      lim = 0.0;
+    } else {
+      mu = cb / sb;
+      const double mag = pow(sb, (double)n);  // (-i sb)^n = sb^n (-i)^n
+      const int r = n & 3;
+      lre = (r == 0) ? mag : (r == 2 ? -mag : 0.0);
+      lim = (r == 1) ? -mag : (r == 3 ? mag : 0.0);
+    }
+    if (threadIdx.x == 0) {
+      inst_rw[i].mu[l] = (float)mu;
+      if (l == p - 1) {
+        inst_rw[i].final_scale = make_float2((float)lre, (float)lim);
+        inst_rw[i].final_scale2 = (float)(lre * lre + lim * lim);
+      }
+    }
+    sre = lre;
+    sim = lim;
+  }
+}
+
+cudaError_t launch_prep_layers(const InstDev* inst, int32_t count, int32_t p, const double* gamma,
+                               const double* beta, float2* tables, InstDev* inst_rw,
+                               cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_prep_layers<<<count, 128, 0, st>>>(inst, p, gamma, beta, tables, inst_rw);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// n <= 9: one 64-thread CTA per instance, state in shared memory, one qubit at
+// a time. Used for tiny subgraphs and edge cases.
+__global__ void k_tiny_sim(const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list,
+                           int32_t p, const SubDev* __restrict__ subs,
+                           const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
+                           float2* __restrict__ states, double* __restrict__ expect, int32_t keep,
+                           int32_t want_expect, int32_t tabcap) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* psi = reinterpret_cast<float2*>(smraw);    // 512
+  float2* tab = psi + 512;                            // tabcap
+  uint32_t* pl = reinterpret_cast<uint32_t*>(tab + tabcap);  // 9*16
+  double* red = reinterpret_cast<double*>(pl + 9 * kMaxPlanes + 8);
+  const int ii = list[blockIdx.x];
+  const InstDev I = inst_all[ii];
+  const SubDev S = subs[I.sub];
+  const int n = I.n, P = I.P, W = I.W;
+  const uint32_t dim = 1u << n, tid = threadIdx.x, nt = blockDim.x;
+  for (uint32_t q = tid; q < (uint32_t)(n * P); q += nt) pl[q] = planes_all[S.plane_off + q];
+  for (uint32_t z = tid; z < dim; z += nt) psi[z] = make_float2(1.f, 0.f);
+  for (int l = 0; l < p; ++l) {
+    __syncthreads();
+    const float2* tl = tables + I.table_off + (int64_t)l * (W + 1);
+    for (int c = tid; c <= W; c += nt) tab[c] = tl[c];
+    __syncthreads();
+    for (uint32_t z = tid; z < dim; z += nt) psi[z] = cmul(psi[z], tab[tix(cut_eval(z, pl, n, P), W)]);
+    const float mu = I.mu[l];
+    for (int j = 0; j < n; ++j) {
+      __syncthreads();
+      for (uint32_t q = tid; q < (dim >> 1); q += nt) {
+        uint32_t lo = q & ((1u << j) - 1u);
+        uint32_t z0 = ((q >> j) << (j + 1)) | lo;
+        float2 x = psi[z0], y = psi[z0 | (1u << j)];
+        bfly(x, y, mu);
+        psi[z0] = x;
+        psi[z0 | (1u << j)] = y;
+      }
+    }
+  }
+  __syncthreads();
+  if (want_expect) {
+    double acc = 0.0;
+    for (uint32_t z = tid; z < dim; z += nt) {
+      float2 a = psi[z];
+      acc += (double)(a.x * a.x + a.y * a.y) * (double)cut_eval(z, pl, n, P);
+    }
+    double s = block_sum(acc, red, tid, nt);
+    if (tid == 0) expect[ii] = s * (double)I.final_scale2;
+  }
+  if (keep)
+    for (uint32_t z = tid; z < dim; z += nt) states[I.state_off + z] = cmul(psi[z], I.final_scale);
+}
+
+cudaError_t launch_tiny_sim(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t p,
+                            const SubDev* subs, const uint32_t* planes, const float2* tables,
+                            float2* states, double* expect, int32_t keep, int32_t want_expect,
+                            int32_t tabcap, cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  size_t smem = 512 * sizeof(float2) + tabcap * sizeof(float2) + (9 * kMaxPlanes + 8) * 4 + 8 * 8;
+  cudaFuncSetAttribute(k_tiny_sim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_tiny_sim<<<nlist, 64, smem, st>>>(inst, list, p, subs, planes, tables, states, expect, keep,
+                                      want_expect, tabcap);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// 10 <= n <= 14: the whole state of one instance lives in one CTA (registers
+// plus a shared-memory transpose buffer); all p layers, <C> and the optional
+// state write happen without touching HBM in between.
+template <int TB>
+__global__ void __launch_bounds__(1 << (TB - 5))
+    k_smem_sim(const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list, int32_t p,
+               const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes_all,
+               const float2* __restrict__ tables, float2* __restrict__ states,
+               double* __restrict__ expect, int32_t keep, int32_t want_expect, int32_t tabcap) {
+  constexpr uint32_t NT = 1u << (TB - 5);
+  constexpr int NR = (TB > 10) ? 3 : 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);               // padded 2^TB
+  float2* tab = sm + padded_elems<TB>();                        // tabcap
+  uint32_t* pl = reinterpret_cast<uint32_t*>(tab + tabcap);     // 14*16
+  LayoutCut* lc = reinterpret_cast<LayoutCut*>(pl + kSmemMaxQubits * kMaxPlanes);
+  double* red = reinterpret_cast<double*>(lc + 1);
+  const uint32_t tid = threadIdx.x;
+  const int ii = list[blockIdx.x];
+  const InstDev I = inst_all[ii];
+  const SubDev S = subs[I.sub];
+  const int n = TB, P = I.P, W = I.W;
+  for (uint32_t q = tid; q < (uint32_t)(n * P); q += NT) pl[q] = planes_all[S.plane_off + q];
+  __syncthreads();
+  build_layout_cut<TB>(*lc, NR, TB, TB, pl, P, tid);
+  // mix masks: all slots, except that layout 2 only mixes local bits < TB-10
+  const uint32_t mask2 = (1u << (TB - 10)) - 1u;
+  float2 a[32];
+  int cur = NR - 1;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) a[k] = make_float2(1.f, 0.f);
+  for (int l = 0; l < p; ++l) {
+    const float2* tl = tables + I.table_off + (int64_t)l * (W + 1);
+    for (int c = tid; c <= W; c += NT) tab[c] = tl[c];
+    __syncthreads();
+    {
+      ThreadCut t = thread_cut(li0_rt<TB>(cur, tid), *lc, cur, pl, n, P);
+      const int* ckk = lc->ckk[cur];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) a[k] = cmul(a[k], tab[tix(cut_of_reg(t, ckk, k), W)]);
+    }
+    const float mu = I.mu[l];
+    if ((l & 1) == 0) {
+      for (int r = NR - 1; r >= 0; --r) {
+        goto_layout<TB>(a, sm, tid, cur, r);
+        mix_regs(a, mu, r == 2 ? mask2 : 31u);
+      }
+    } else {
+      for (int r = 0; r < NR; ++r) {
+        goto_layout<TB>(a, sm, tid, cur, r);
+        mix_regs(a, mu, r == 2 ? mask2 : 31u);
+      }
+    }
+    __syncthreads();  // before the next table load overwrites tab
+  }
+  if (want_expect) {
+    ThreadCut t = thread_cut(li0_rt<TB>(cur, tid), *lc, cur, pl, n, P);
+    const int* ckk = lc->ckk[cur];
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)cut_of_reg(t, ckk, k), acc);
+    double s = block_sum((double)acc, red, tid, NT);
+    if (tid == 0) expect[ii] = s * (double)I.final_scale2;
+  }
+  if (keep) {
+    goto_layout<TB>(a, sm, tid, cur, 0);
+    float2* out = states + I.state_off;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) out[li_of<TB, 0>(tid, k)] = cmul(a[k], I.final_scale);
+  }
+}
+
+template <int TB>
+static cudaError_t launch_smem_t(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t p,
+                                 const SubDev* subs, const uint32_t* planes, const float2* tables,
+                                 float2* states, double* expect, int32_t keep, int32_t want_expect,
+                                 int32_t tabcap, cudaStream_t st) {
+  size_t smem = (size_t)padded_elems<TB>() * sizeof(float2) + tabcap * sizeof(float2) +
+                kSmemMaxQubits * kMaxPlanes * 4 + sizeof(LayoutCut) + 32 * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_smem_sim<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_smem_sim<TB><<<nlist, 1 << (TB - 5), smem, st>>>(inst, list, p, subs, planes, tables, states,
+                                                      expect, keep, want_expect, tabcap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_smem_sim(int n, const InstDev* inst, const int32_t* list, int32_t nlist,
+                            int32_t p, const SubDev* subs, const uint32_t* planes,
+                            const float2* tables, float2* states, double* expect, int32_t keep,
+                            int32_t want_expect, int32_t tabcap, cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  switch (n) {
+    case 10: return launch_smem_t<10>(inst, list, nlist, p, subs, planes, tables, states, expect, keep, want_expect, tabcap, st);
+    case 11: return launch_smem_t<11>(inst, list, nlist, p, subs, planes, tables, states, expect, keep, want_expect, tabcap, st);
+    case 12: return launch_smem_t<12>(inst, list, nlist, p, subs, planes, tables, states, expect, keep, want_expect, tabcap, st);
+    case 13: return launch_smem_t<13>(inst, list, nlist, p, subs, planes, tables, states, expect, keep, want_expect, tabcap, st);
+    case 14: return launch_smem_t<14>(inst, list, nlist, p, subs, planes, tables, states, expect, keep, want_expect, tabcap, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// n >= 15: layer passes that stream the state through HBM. A tile is 2^13
+// amplitudes whose local bits [0, c) are qubits [0, c) (contiguous in HBM) and
+// whose local bits [c, 13) are qubits [s, s + 13 - c); the remaining qubits are
+// fixed per tile. A pass may finish one layer's mixer on the tile's qubits,
+// apply the next layer's phase and start its mixer, so p layers take p + 1
+// passes when the qubits split into two groups (see make_schedule).
+//
+// CTAs are persistent: CTA b walks a contiguous range of the launch's
+// (instance, tile) pairs, so the per-instance set-up (bit-planes, phase table,
+// per-thread cut constants) is paid once per instance, not once per tile.
+//
+// Cut values. With T the tile's qubits, F the fixed ones, J the qubits of the
+// thread index and K the 5 register qubits of the layout where the cut is
+// needed, C(z) = sum_u d_u z_u - 2 sum_{u<v} w_uv z_u z_v splits into
+//   C = C(z_F)                          per tile (z_T = 0)
+//     + sum_{u in J} lam_u z_u          lam_u = d_u - 2 sum_{v in F} w_uv z_v, per tile
+//     - 2 Q_J(z_J)                      per thread and instance
+//     + sum_{u in K} z_u (lam_u + B_u)  B_u = -2 sum_{v in J} w_uv z_v, per thread
+//     - 2 Q_K(z_K)                      32-entry table per instance
+// so a cut value costs a broadcast load and a few integer adds.
+struct TileConst {
+  int cf;        // C(z_F)
+  int lam[16];   // lam_u per local bit
+  int pad[3];    // keeps what follows in shared memory 16-byte aligned
+};
+static_assert(sizeof(TileConst) % 16 == 0, "shared-memory carve-up needs 16-byte multiples");
+
+__device__ __forceinline__ uint32_t qubit_of(int lb, int c, int s) {
+  return lb < c ? (uint32_t)lb : (uint32_t)(s + (lb - c));
+}
+
+// Visit the 32 registers in Gray-code order so that consecutive registers
+// differ in one bit: per-register offsets then cost one add each.
+__host__ __device__ constexpr int gray(int i) { return i ^ (i >> 1); }
+__host__ __device__ constexpr int gray_bit(int i) { return i & 1 ? 0 : (i & 2 ? 1 : (i & 4 ? 2 : (i & 8 ? 3 : 4))); }
+
+template <int TB, int NR>
+__global__ void __launch_bounds__(1 << (TB - 5), 2)
+    k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, int64_t total_tiles,
+                 const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list,
+                 const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes_all,
+                 const float2* __restrict__ tables, float2* __restrict__ states,
+                 double* __restrict__ partials, int32_t tabcap) {
+  constexpr uint32_t NT = 1u << (TB - 5);
+  constexpr int RC = NR - 1;  // layout of the cut step (phase / <C>)
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* tab = reinterpret_cast<float2*>(smraw);
+  float2* sm = tab + tabcap;
+  uint32_t* pl = reinterpret_cast<uint32_t*>(sm + padded_elems<TB>());
+  int* qk = reinterpret_cast<int*>(pl + PARAQAOA_MAX_QUBITS * kMaxPlanes);  // 32
+  TileConst* tc = reinterpret_cast<TileConst*>(qk + 32);
+  double* red = reinterpret_cast<double*>(tc + 1);
+  const uint32_t tid = threadIdx.x;
+  const int c = pd.c, s = pd.s, g = TB - c;
+  const uint32_t lowt = (uint32_t)(s - c);
+  const uint32_t tmask = (1u << tiles_log2) - 1u;
+
+  // mix masks of the rounds (register slots whose local bit this pass mixes)
+  uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    if (TB - 5 + j >= pd.mix_lo) mm0 |= 1u << j;
+    if (TB - 10 + j >= pd.mix_lo) mm1 |= 1u << j;
+    if (j >= pd.mix_lo && j < TB - 10) mm2 |= 1u << j;
+  }
+  const bool need_cut = pd.layerP >= 0 || pd.expect;
+  // qubit offsets of the load/store layout: thread part and register bits
+  uint32_t zt0 = 0;
+  for (int lb = 0; lb < TB - 5; ++lb)
+    if ((tid >> lb) & 1u) zt0 |= 1u << qubit_of(lb, c, s);
+  uint32_t e[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
+  // the thread's qubits in the cut layout
+  const uint32_t li0 = li_of<TB, RC>(tid, 0);
+  uint32_t zJ = 0;
+  for (int lb = 0; lb < TB; ++lb)
+    if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
+
+  const int64_t per = (total_tiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t_begin = (int64_t)blockIdx.x * per;
+  const int64_t t_end = min(total_tiles, t_begin + per);
+  int cur_inst = -1;
+  int P = 1, W = 0;
+  float muA = 0.f, muB = 0.f;
+  float2 fscale = make_float2(1.f, 0.f);
+  int64_t state_off = 0, part_off = 0;
+  int qJ = 0, Bk[5] = {0, 0, 0, 0, 0};
+  for (int64_t wt = t_begin; wt < t_end; ++wt) {
+    const int li_idx = (int)(wt >> tiles_log2);
+    const uint32_t tile = (uint32_t)(wt & tmask);
+    if (li_idx != cur_inst) {
+      // ---- per-instance set-up
+      cur_inst = li_idx;
+      const InstDev* Ip = inst_all + list[li_idx];
+      const SubDev S = subs[Ip->sub];
+      P = Ip->P;
+      W = Ip->W;
+      state_off = Ip->state_off;
+      part_off = Ip->part_off;
+      fscale = Ip->final_scale;
+      muA = pd.layerA >= 0 ? Ip->mu[pd.layerA] : 0.f;
+      muB = pd.layerB >= 0 ? Ip->mu[pd.layerB] : 0.f;
+      const int64_t table_off = Ip->table_off;
+      __syncthreads();  // the previous tile is done with the shared tables
+      for (uint32_t q = tid; q < (uint32_t)(n * P); q += NT) pl[q] = planes_all[S.plane_off + q];
+      if (pd.layerP >= 0) {
+        const float2* tl = tables + table_off + (int64_t)pd.layerP * (W + 1);
+        for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
+      }
+      __syncthreads();
+      if (need_cut) {
+        if (tid < 32) {  // -2 Q_K(k)
+          uint32_t zk = 0;
+          for (int j = 0; j < 5; ++j)
+            if ((tid >> j) & 1u) zk |= 1u << qubit_of(slot_lb(TB, RC, j), c, s);
+          int acc = 0;
+          for (int j = 0; j < 5; ++j) {
+            if (!((tid >> j) & 1u)) continue;
+            const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
+            for (int b = 0; b < P; ++b) acc += __popc(row[b] & zk) << b;
+          }
+          qk[tid] = -acc;
+        }
+        int acc = 0;  // -2 Q_J(z_J): each pair of set J qubits counted from both ends
+        for (int u = 0; u < n; ++u) {
+          if (!((zJ >> u) & 1u)) continue;
+          const uint32_t* row = pl + u * P;
+          for (int b = 0; b < P; ++b) acc += __popc(row[b] & zJ) << b;
+        }
+        qJ = -acc;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
+          int bj = 0;
+          for (int b = 0; b < P; ++b) bj += __popc(row[b] & zJ) << b;
+          Bk[j] = -2 * bj;
+        }
+      }
+    }
+    const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
+    float2* base = states + state_off + (zbase | zt0);
+    // ---- per-tile constants (one warp), overlapped with the loads below
+    if (need_cut && tid < 32) {
+      if (tid < (uint32_t)TB) {
+        const uint32_t* row = pl + qubit_of(tid, c, s) * P;
+        int d = 0, a = 0;
+        for (int b = 0; b < P; ++b) {
+          d += __popc(row[b]) << b;
+          a += __popc(row[b] & zbase) << b;
+        }
+        tc->lam[tid] = d - 2 * a;
+      }
+      if (tid == 31) tc->cf = cut_eval(zbase, pl, n, P);
+    }
+    float2 a[32];
+    if (pd.init) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) a[k] = make_float2(1.f, 0.f);
+    } else {
+      uint32_t off = 0;
+      a[0] = base[0];
+#pragma unroll
+      for (int i = 1; i < 32; ++i) {
+        const int k = gray(i), b = gray_bit(i);
+        off = ((k >> b) & 1) ? off + e[b] : off - e[b];
+        a[k] = base[off];
+      }
+    }
+    __syncthreads();  // tile constants visible
+    int A = 0, kap[5] = {0, 0, 0, 0, 0};
+    if (need_cut) {
+      A = tc->cf + qJ;
+      for (int lb = 0; lb < TB; ++lb)
+        if ((li0 >> lb) & 1u) A += tc->lam[lb];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) kap[j] = tc->lam[slot_lb(TB, RC, j)] + Bk[j];
+    }
+    if (pd.layerA >= 0) {
+      // a load starts in layout 0; an init tile starts in the cut layout
+      mix_regs(a, muA, mm0);
+      if constexpr (NR > 1) {
+        transpose<TB, 0, 1>(a, sm, tid);
+        mix_regs(a, muA, mm1);
+      }
+      if constexpr (NR > 2) {
+        transpose<TB, 1, 2>(a, sm, tid);
+        mix_regs(a, muA, mm2);
+      }
+    }
+    if (pd.layerP >= 0) {
+      int S = A;
+      a[0] = cmul(a[0], tab[tix(S + qk[0], W)]);
+#pragma unroll
+      for (int i = 1; i < 32; ++i) {
+        const int k = gray(i), b = gray_bit(i);
+        S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
+        a[k] = cmul(a[k], tab[tix(S + qk[k], W)]);
+      }
+    }
+    if (pd.layerB >= 0) {
+      if constexpr (NR > 2) {
+        mix_regs(a, muB, mm2);
+        transpose<TB, 2, 1>(a, sm, tid);
+      }
+      if constexpr (NR > 1) {
+        mix_regs(a, muB, mm1);
+        transpose<TB, 1, 0>(a, sm, tid);
+      }
+      mix_regs(a, muB, mm0);
+    }
+    if (pd.expect) {
+      float acc = 0.f;
+      int S = A;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int k = gray(i);
+        if (i > 0) {
+          const int b = gray_bit(i);
+          S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
+        }
+        acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)(S + qk[k]), acc);
+      }
+      const double sum = block_sum((double)acc, red, tid, NT);
+      if (tid == 0) partials[part_off + tile] = sum;
+    }
+    if (pd.store) {
+      if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
+        if constexpr (NR == 3) transpose<TB, 2, 0>(a, sm, tid);
+        if constexpr (NR == 2) transpose<TB, 1, 0>(a, sm, tid);
+      }
+      if (pd.last) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a[k] = cmul(a[k], fscale);
+      }
+      uint32_t off = 0;
+      base[0] = a[0];
+#pragma unroll
+      for (int i = 1; i < 32; ++i) {
+        const int k = gray(i), b = gray_bit(i);
+        off = ((k >> b) & 1) ? off + e[b] : off - e[b];
+        base[off] = a[k];
+      }
+    }
+    __syncthreads();  // tile constants and transpose buffer free for the next tile
+  }
+}
+
+size_t layer_pass_smem(int tabcap) {
+  return (size_t)tabcap * sizeof(float2) + (size_t)padded_elems<kTileBits>() * sizeof(float2) +
+         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * 4 + sizeof(TileConst) + 16 * sizeof(double);
+}
+
+template <int NR>
+static cudaError_t launch_layer_nr(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                                   int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                                   const float2* tables, float2* states, double* partials,
+                                   int32_t tabcap, cudaStream_t st) {
+  const size_t smem = layer_pass_smem(tabcap);
+  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<kTileBits, NR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  static int num_sm = 0;
+  if (num_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&num_sm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_layer_pass<kTileBits, NR>,
+                                                    1 << (kTileBits - 5), smem);
+  if (e != cudaSuccess) return e;
+  const int tiles_log2 = n - kTileBits;
+  const int64_t total = (int64_t)nlist << tiles_log2;
+  const int64_t grid = std::min<int64_t>(total, (int64_t)num_sm * std::max(per_sm, 1));
+  k_layer_pass<kTileBits, NR><<<(unsigned)grid, 1 << (kTileBits - 5), smem, st>>>(
+      pd, n, tiles_log2, total, inst, list, subs, planes, tables, states, partials, tabcap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_pass(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                              int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                              const float2* tables, float2* states, double* partials,
+                              int32_t tabcap, cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  const int nr = 1 + (pd.mix_lo < kTileBits - 5) + (pd.mix_lo < kTileBits - 10);
+  if (nr == 1) return launch_layer_nr<1>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st);
+  if (nr == 2) return launch_layer_nr<2>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st);
+  return launch_layer_nr<3>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st);
+}
+
+// Sum the per-tile partials of each instance in a fixed order, times |lambda_p|^2.
+__global__ void k_expect_reduce(const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list,
+                                int32_t tiles, const double* __restrict__ partials,
+                                double* __restrict__ expect) {
+  __shared__ double red[8];
+  const int ii = list[blockIdx.x];
+  const InstDev I = inst_all[ii];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) acc += partials[I.part_off + t];
+  double s = block_sum(acc, red, threadIdx.x, blockDim.x);
+  if (threadIdx.x == 0) expect[ii] = s * (double)I.final_scale2;
+}
+
+cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32_t nlist,
+                                 int32_t tiles, const double* partials, double* expect,
+                                 cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  k_expect_reduce<<<nlist, 256, 0, st>>>(inst, list, tiles, partials, expect);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cut table (Sec. 2.1) of one subgraph: out[z] = C(z), one thread per z.
+__global__ void k_cut_table(const SubDev* __restrict__ sub, const uint32_t* __restrict__ planes_all,
+                            uint16_t* __restrict__ out) {
+  __shared__ uint32_t pl[PARAQAOA_MAX_QUBITS * kMaxPlanes];
+  const SubDev S = *sub;
+  for (int q = threadIdx.x; q < S.n * S.P; q += blockDim.x) pl[q] = planes_all[S.plane_off + q];
+  __syncthreads();
+  const uint64_t dim = 1ull << S.n;
+  for (uint64_t z = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; z < dim;
+       z += (uint64_t)gridDim.x * blockDim.x)
+    out[z] = (uint16_t)cut_eval((uint32_t)z, pl, S.n, S.P);
+}
+
+cudaError_t launch_cut_table(const SubDev* sub_dev_one, int n, const uint32_t* planes, uint16_t* out,
+                             cudaStream_t st) {
+  const uint64_t dim = 1ull << n;
+  const unsigned blocks = (unsigned)std::min<uint64_t>((dim + 255) / 256, 152ull * 16);
+  k_cut_table<<<blocks, 256, 0, st>>>(sub_dev_one, planes, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pq

@@ -1,0 +1,347 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Tolerances (stated for the floating-point results): amplitude max error
+<= 1e-5 and |<C>_gpu - <C>_oracle| / W <= 1e-5. Integer results (cut tables,
+partitions, merged cuts) must match exactly.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = 1e-5
+EXP_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    import paper_2603_26232_gb300 as pkg
+    pkg.build()
+    from paper_2603_26232_gb300 import _capi
+    ctx = _capi.paraqaoa_create(0)
+    yield _capi, ctx
+    _capi.paraqaoa_destroy(ctx)
+
+
+def chain_graph(sizes, p_edge, seed, wmax):
+    """A graph whose SIZES partition has parts of exactly the given sizes."""
+    nv = int(sum(sizes) - (len(sizes) - 1))
+    return synth.erdos_renyi(nv, p_edge, seed, wmax=wmax)
+
+
+def oracle_parts(orc, g, sizes):
+    first, size = orc.partition(g.n, len(sizes), 2, sizes)
+    return [orc.get_subgraph(g, int(f), int(s)) for f, s in zip(first, size)]
+
+
+def test_cut_table_bit_exact(api, orc):
+    capi, ctx = api
+    sizes = [2, 2, 5, 10, 13, 14, 15, 17, 20]
+    g = chain_graph(sizes, 0.4, 1, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        subs = oracle_parts(orc, g, sizes)
+        for i, s in enumerate(subs):
+            ours = capi.paraqaoa_cut_table(ctx, part, i, s.n)
+            ref = orc.cut_table(s)
+            assert np.array_equal(ours.astype(np.int64), ref), f"part {i} (n={s.n})"
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def _state_case(capi, ctx, orc, sizes, p, seed, wmax=10, p_edge=0.45):
+    g = chain_graph(sizes, p_edge, seed, wmax)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), p, 1000 + seed)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, p, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+        ex = capi.paraqaoa_expect(ctx, len(ids))
+        for i, s in enumerate(subs):
+            ref = orc.simulate(s, gam[i], bet[i])
+            ours = capi.paraqaoa_state(ctx, i, s.n)
+            err = np.max(np.abs(ours.astype(np.complex128) - ref))
+            assert err <= AMP_TOL, f"n={s.n} p={p}: amplitude error {err}"
+            W = max(s.total_weight, 1)
+            e_ref = orc.expect_state(s, ref)
+            assert abs(ex[i] - e_ref) / W <= EXP_TOL, f"n={s.n} p={p}: <C> {ex[i]} vs {e_ref}"
+        # expectation-only run gives the same <C> without keeping states
+        capi.paraqaoa_simulate_batch(ctx, part, ids, p, gam, bet, capi.SIM_EXPECT)
+        ex2 = capi.paraqaoa_expect(ctx, len(ids))
+        assert np.max(np.abs(ex2 - ex)) <= 1e-9 * max(1.0, np.max(np.abs(ex)))
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_state_parity_small_and_onchip(api, orc, p):
+    """n = 2..14: tiny and whole-state-on-chip kernels, mixed in one batch."""
+    capi, ctx = api
+    _state_case(capi, ctx, orc, [2, 3, 5, 8, 9, 10, 11, 12, 13, 14], p, seed=p)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_state_parity_streaming(api, orc, p):
+    """n = 15..21: HBM layer passes (two qubit groups), mixed sizes in one batch."""
+    capi, ctx = api
+    _state_case(capi, ctx, orc, [15, 16, 17, 19, 21], p, seed=10 + p)
+
+
+def test_state_parity_three_groups(api, orc):
+    """n = 22 and 24: n = 24 needs a third qubit group (2p + 1 passes)."""
+    capi, ctx = api
+    _state_case(capi, ctx, orc, [22, 24], 2, seed=21, p_edge=0.3)
+
+
+def test_unit_weight_and_edgeless_parts(api, orc):
+    capi, ctx = api
+    _state_case(capi, ctx, orc, [4, 12, 16], 2, seed=5, wmax=1, p_edge=0.5)
+    _state_case(capi, ctx, orc, [6, 11, 15], 1, seed=6, wmax=1, p_edge=0.0)
+
+
+def test_extreme_angles(api, orc):
+    """beta near pi/4 and pi/2 exercise both mixer factorisations."""
+    capi, ctx = api
+    sizes = [9, 12, 16]
+    g = chain_graph(sizes, 0.5, 3, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(3, dtype=np.int32)
+        for b in [np.pi / 4, np.pi / 4 + 1e-7, np.pi / 2, -1.2, 0.0]:
+            gam = np.full((3, 2), 0.7)
+            bet = np.full((3, 2), b)
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+            ex = capi.paraqaoa_expect(ctx, 3)
+            for i, s in enumerate(subs):
+                ref = orc.simulate(s, gam[i], bet[i])
+                assert np.max(np.abs(capi.paraqaoa_state(ctx, i, s.n) - ref)) <= AMP_TOL
+                assert abs(ex[i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def _check_topk(orc, s, state_ref, z, pr, K):
+    """Exact ids where the oracle's K-th/(K+1)-th gap is clear; otherwise every
+    pick must be within 1e-5 max P of the oracle's K-th probability."""
+    probs = np.abs(state_ref) ** 2
+    half = 1 << (s.n - 1)
+    cand = np.arange(half)
+    order = np.lexsort((cand, -probs[:half]))
+    oz = cand[order]
+    pmax = probs.max()
+    kth = probs[oz[K - 1]]
+    nxt = probs[oz[K]] if K < half else -1.0
+    assert np.all(z < half)
+    assert len(set(z.tolist())) == K
+    if kth - nxt > 1e-5 * pmax:
+        assert set(z.tolist()) == set(oz[:K].tolist())
+    else:
+        assert np.all(probs[z] >= kth - 1e-5 * pmax)
+    assert np.all(np.diff(pr) <= 0)
+    assert np.max(np.abs(pr - probs[z])) <= 1e-5 * pmax
+
+
+@pytest.mark.parametrize("K", [1, 4, 16, 32])
+def test_topk_parity(api, orc, K):
+    capi, ctx = api
+    sizes = [7, 11, 14, 16, 18]
+    g = chain_graph(sizes, 0.5, 7, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), 2, 77)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_KEEP_STATE)
+        z, pr = capi.paraqaoa_topk(ctx, len(ids), K)
+        for i, s in enumerate(subs):
+            _check_topk(orc, s, orc.simulate(s, gam[i], bet[i]), z[i], pr[i], K)
+        # raw mode ranks both halves: every pick is at least as likely as the
+        # oracle's K-th over all z, up to the tolerance
+        zr, prr = capi.paraqaoa_topk(ctx, len(ids), K, capi.TOPK_RAW)
+        for i, s in enumerate(subs):
+            probs = np.abs(orc.simulate(s, gam[i], bet[i])) ** 2
+            kth = np.sort(probs)[::-1][K - 1]
+            assert len(set(zr[i].tolist())) == K
+            assert np.all(probs[zr[i]] >= kth - 1e-5 * probs.max())
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_merge_exhaustive_parity(api, orc, seed):
+    capi, ctx = api
+    g = synth.erdos_renyi(40, 0.25, seed, wmax=5)
+    G = capi.Graph.of(g)
+    M, K = 4, 4
+    part = capi.paraqaoa_partition(G, M)
+    try:
+        first, size, _, _ = capi.paraqaoa_part_info(part)
+        rng = np.random.default_rng(seed)
+        cand = np.array([rng.integers(0, 1 << int(s), K) for s in size], dtype=np.uint32)
+        ref_side, ref_cut, _ = orc.merge_exhaustive(g, first, size, cand, K, 1)
+        for L in (1, 2, 3, 4):
+            side, cut = capi.paraqaoa_merge(ctx, G, part, cand, K, L, 0)
+            assert cut == ref_cut and np.array_equal(side, ref_side)
+            assert orc.cutval(g, side) == cut
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+@pytest.mark.parametrize("beam", [1, 3, 16, 64])
+def test_merge_beam_parity(api, orc, beam):
+    capi, ctx = api
+    g = synth.erdos_renyi(120, 0.1, 4, wmax=10)
+    G = capi.Graph.of(g)
+    M, K = 7, 8
+    part = capi.paraqaoa_partition(G, M)
+    try:
+        first, size, _, _ = capi.paraqaoa_part_info(part)
+        rng = np.random.default_rng(beam)
+        cand = np.array([rng.integers(0, 1 << int(s), K) for s in size], dtype=np.uint32)
+        ref_side, ref_cut = orc.merge_beam(g, first, size, cand, K, beam)
+        side, cut = capi.paraqaoa_merge(ctx, G, part, cand, K, 1, beam)
+        assert cut == ref_cut and np.array_equal(side, ref_side)
+        assert orc.cutval(g, side) == cut
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def test_grid_search_parity_small_config(api, orc):
+    """Tiny configuration: G(20, 0.5), unit weights, 2 parts, 16 x 16 grid."""
+    capi, ctx = api
+    g = synth.erdos_renyi(20, 0.5, 0)
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, 2)
+    try:
+        subs = orc.subgraphs(g, 2)
+        ids = np.arange(2, dtype=np.int32)
+        gg, bb, best, vals = capi.paraqaoa_grid_search(ctx, part, ids, 16, want_values=True)
+        ovals, oarg, og, ob = orc.grid_search(orc.Batch(subs), 16)
+        for i, s in enumerate(subs):
+            W = s.total_weight
+            assert np.max(np.abs(vals[i] - ovals[i])) / W <= EXP_TOL
+            # the GPU's pick is a maximum of the oracle's values within tolerance
+            k = int(np.argmax(vals[i]))
+            assert ovals[i, k] >= ovals[i].max() - 2 * EXP_TOL * W
+            assert abs(best[i] - vals[i, k]) < 1e-12
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def test_optimize_parity(api, orc):
+    capi, ctx = api
+    g = synth.erdos_renyi(60, 0.3, 2, wmax=10)
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, 4)
+    try:
+        subs = orc.subgraphs(g, 4)
+        batch = orc.Batch(subs)
+        ids = np.arange(4, dtype=np.int32)
+        g0, b0, _, _ = capi.paraqaoa_grid_search(ctx, part, ids, 8)
+        g2, b2 = orc.interp(g0[:, None], b0[:, None])
+        cfg = orc.AdamConfig(steps=12, lr=0.02, h=1e-3)
+        og, ob, oval = orc.adam_optimize(batch, g2, b2, cfg)
+        gg, bb, val = capi.paraqaoa_optimize(ctx, part, ids, 2, g2, b2, cfg.steps, cfg.lr, cfg.h)
+        at_ours = orc.expect_batch(batch, ids, gg, bb)
+        W = np.array([s.total_weight for s in subs], float)
+        assert np.all(np.abs(val - at_ours) / W <= EXP_TOL)
+        assert np.all(val >= oval - 1e-4 * W)
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def test_small_config_end_to_end(api, orc):
+    """G(20, 0.5): grid -> top-4 -> exhaustive merge; the merged cut equals the
+    oracle's merge of the same candidates and is <= the brute-force optimum."""
+    import paper_2603_26232_gb300 as pkg
+    capi, ctx = api
+    g = synth.erdos_renyi(20, 0.5, 0)
+    solver = pkg.Solver()
+    try:
+        res = solver.solve(g, pkg.SolveConfig(M=2, K=4, p=1, grid_points=16))
+    finally:
+        solver.close()
+    first, size = orc.partition(20, 2)
+    side, cut, _ = orc.merge_exhaustive(g, first, size, res.cand, 4, 1)
+    assert res.cut == cut and np.array_equal(res.side, side)
+    assert orc.cutval(g, res.side) == res.cut
+    opt, _ = orc.bruteforce_maxcut(orc.Subgraph(0, g.n, g.eu, g.ev, g.ew))
+    assert res.cut <= opt and res.cut >= 0.8 * opt
+
+
+def test_paper_scale_config_full_size(api, orc):
+    """G(400, 0.1), weights 1..10, 21 parts of 20 qubits, p = 2 at fixed
+    angles, top-16, beam 256: every <C> and top-16 list against the oracle,
+    and the merged cut equal to the oracle's merge of the same lists."""
+    capi, ctx = api
+    g = synth.erdos_renyi(400, 0.1, 0, wmax=10)
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, 21)
+    try:
+        subs = orc.subgraphs(g, 21)
+        ids = np.arange(21, dtype=np.int32)
+        gam, bet = synth.random_angles(21, 2, 400)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+        ex = capi.paraqaoa_expect(ctx, 21)
+        z, pr = capi.paraqaoa_topk(ctx, 21, 16)
+        oex = orc.expect_batch(orc.Batch(subs), ids, gam, bet)
+        W = np.array([s.total_weight for s in subs], float)
+        assert np.all(np.abs(ex - oex) / W <= EXP_TOL)
+        for i in (0, 10, 20):
+            _check_topk(orc, subs[i], orc.simulate(subs[i], gam[i], bet[i]), z[i], pr[i], 16)
+        first, size = orc.partition(400, 21)
+        oside, ocut = orc.merge_beam(g, first, size, z, 16, 256)
+        side, cut = capi.paraqaoa_merge(ctx, G, part, z, 16, 1, 256)
+        assert cut == ocut and np.array_equal(side, oside)
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def test_error_codes(api):
+    capi, ctx = api
+    g = synth.erdos_renyi(30, 0.3, 1)
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, 2)
+    try:
+        ids = np.zeros(1, np.int32)
+        with pytest.raises(capi.ParaQAOAError) as e:
+            capi.paraqaoa_simulate_batch(ctx, part, np.array([5], np.int32), 1, [0.1], [0.1])
+        assert e.value.code == capi.E_INVAL
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 1, [0.1], [0.1], capi.SIM_EXPECT)
+        with pytest.raises(capi.ParaQAOAError) as e:
+            capi.paraqaoa_topk(ctx, 1, 4)  # states were not kept
+        assert e.value.code == capi.E_NO_RESULT
+        with pytest.raises(capi.ParaQAOAError) as e:
+            capi.paraqaoa_expect(ctx, 2)  # count mismatch
+        assert e.value.code == capi.E_NO_RESULT
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 1, [0.1], [0.1], capi.SIM_KEEP_STATE)
+        with pytest.raises(capi.ParaQAOAError):
+            capi.paraqaoa_topk(ctx, 1, 33)
+    finally:
+        capi.paraqaoa_part_free(part)
+    # admission: a budget far below one 20-qubit state is refused
+    small = capi.paraqaoa_create(0, 1 << 20)
+    try:
+        g2 = synth.erdos_renyi(40, 0.2, 1)
+        p2 = capi.paraqaoa_partition(capi.Graph.of(g2), 2)
+        try:
+            with pytest.raises(capi.ParaQAOAError) as e:
+                capi.paraqaoa_simulate_batch(small, p2, np.array([0], np.int32), 1, [0.1], [0.1])
+            assert e.value.code == capi.E_ADMISSION
+        finally:
+            capi.paraqaoa_part_free(p2)
+    finally:
+        capi.paraqaoa_destroy(small)
+    # a part heavier than the phase table is refused
+    heavy = synth.erdos_renyi(12, 0.9, 1, wmax=200)
+    ph = capi.paraqaoa_partition(capi.Graph.of(heavy), 1)
+    try:
+        with pytest.raises(capi.ParaQAOAError) as e:
+            capi.paraqaoa_simulate_batch(ctx, ph, ids, 1, [0.1], [0.1])
+        assert e.value.code == capi.E_INVAL
+    finally:
+        capi.paraqaoa_part_free(ph)
