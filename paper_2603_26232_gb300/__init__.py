@@ -17,7 +17,7 @@ from ._capi import Graph, ParaQAOAError
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .native_build import build as _b
     return _b(force=force)
 
 

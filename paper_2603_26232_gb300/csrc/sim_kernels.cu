@@ -29,10 +29,12 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// (x, y) -> (x + i mu y, y + i mu x)
+// (x, y) -> (x + i mu y, y + i mu x), as two packed FP32x2 FMAs:
+// x + (-mu, mu) * (y.im, y.re) and y + (-mu, mu) * (x.im, x.re).
 __device__ __forceinline__ void bfly(float2& x, float2& y, float mu) {
-  float2 nx = make_float2(fmaf(-mu, y.y, x.x), fmaf(mu, y.x, x.y));
-  float2 ny = make_float2(fmaf(-mu, x.y, y.x), fmaf(mu, x.x, y.y));
+  const float2 m = make_float2(-mu, mu);
+  const float2 nx = __ffma2_rn(m, make_float2(y.y, y.x), x);
+  const float2 ny = __ffma2_rn(m, make_float2(x.y, x.x), y);
   x = nx;
   y = ny;
 }
@@ -473,7 +475,7 @@ __host__ __device__ constexpr int gray(int i) { return i ^ (i >> 1); }
 __host__ __device__ constexpr int gray_bit(int i) { return i & 1 ? 0 : (i & 2 ? 1 : (i & 4 ? 2 : (i & 8 ? 3 : 4))); }
 
 template <int TB, int NR>
-__global__ void __launch_bounds__(1 << (TB - 5), 2)
+__global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
     k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, int64_t total_tiles,
                  const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list,
                  const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes_all,
@@ -680,7 +682,10 @@ __global__ void __launch_bounds__(1 << (TB - 5), 2)
         base[off] = a[k];
       }
     }
-    __syncthreads();  // tile constants and transpose buffer free for the next tile
+    // With two or more rounds, the transposes' barriers already order this
+    // tile's reads of the tile constants and of the transpose buffer before
+    // the next tile's writes; a single-round pass needs its own barrier.
+    if constexpr (NR == 1) __syncthreads();
   }
 }
 

@@ -1,7 +1,7 @@
 """Build libparaqaoa.so in-tree with nvcc for sm_103a (GB300).
 
 Each translation unit is compiled in parallel, then linked into one shared
-library next to this file. Usage: ``python -m paper_2603_26232_gb300.build``.
+library next to this file. Usage: ``python -m paper_2603_26232_gb300.native_build``.
 """
 from __future__ import annotations
 
