@@ -48,6 +48,7 @@ extern "C" {
 #define PARAQAOA_E_CUDA (-6)             /* CUDA runtime error */
 #define PARAQAOA_E_TIMEOUT (-7)          /* a bounded device-side wait gave up */
 #define PARAQAOA_E_NO_RESULT (-8)        /* results requested before a matching simulate call */
+#define PARAQAOA_E_SCRATCH_LIMIT (-9)    /* larger than the fixed scratch of paraqaoa_topk_noalloc */
 
 #define PARAQAOA_MAX_QUBITS 30
 #define PARAQAOA_MAX_SUBGRAPH_WEIGHT 4095
@@ -174,6 +175,31 @@ int paraqaoa_grid_search(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
 int paraqaoa_optimize(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids,
                       int32_t count, int32_t p, int32_t steps, double lr, double h,
                       double *gamma_io, double *beta_io, double *out_value);
+
+/* Top-K of one state without any device allocation (the paper has no
+ * counterpart; this is a deployment variant of paraqaoa_topk).
+ * For callers that must not let a library allocate device memory: a host
+ * whose own caching allocator already holds nearly all device memory, or a
+ * latency-critical loop that cannot take cudaMalloc's implicit device
+ * synchronisation. The call uses a fixed 2 MiB scratch array compiled into
+ * the library, which every GPU that loads the library holds until the
+ * process exits; it calls no cudaMalloc or cudaFree.
+ *  - state_dev: device pointer to 2^n complex64 amplitudes, interleaved
+ *    (re, im), on the calling thread's current device; caller-owned.
+ *  - out_z_dev / out_p_dev: device pointers to K entries each; caller-owned.
+ *    Ranking and flags as paraqaoa_topk (PARAQAOA_TOPK_CANONICAL / RAW).
+ *  - stream: cudaStream_t to run on (NULL: the legacy default stream). The
+ *    call only enqueues work; synchronise the stream before reading outputs.
+ *  - Limits: at most 2^25 ranked entries (canonical n <= 26, raw n <= 25);
+ *    larger inputs return PARAQAOA_E_SCRATCH_LIMIT.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one scratch array: calls whose work overlaps on
+ *    the GPU (other streams, other host threads) race and must be ordered by
+ *    the caller. */
+int paraqaoa_topk_noalloc(const float *state_dev, int32_t n, int32_t K, uint32_t flags,
+                          uint32_t *out_z_dev, float *out_p_dev, void *stream);
 
 /* Per-kernel device time recorded with CUDA events on the context stream.
  * enable != 0 starts recording (and clears the counters). */

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "paraqaoa.h")
 OK = 0
 E_INVAL, E_TOO_MANY_QUBITS, E_ADMISSION, E_NOMEM = -1, -2, -3, -4
 E_SEARCH_TOO_LARGE, E_CUDA, E_TIMEOUT, E_NO_RESULT = -5, -6, -7, -8
+E_SCRATCH_LIMIT = -9
 PART_BALANCED, PART_ALG1_LITERAL, PART_SIZES = 0, 1, 2
 SIM_EXPECT, SIM_KEEP_STATE = 0x1, 0x2
 TOPK_CANONICAL, TOPK_RAW = 0x0, 0x1
@@ -62,6 +63,7 @@ _SIGS = {
     "paraqaoa_profile_enable": ([P, ctypes.c_int32], ctypes.c_int),
     "paraqaoa_profile_read": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "paraqaoa_topk_noalloc": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, P, P, P], ctypes.c_int),
 }
 
 
@@ -77,7 +79,7 @@ def load(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"{path} not found: run `python -m paper_2603_26232_gb300.build` "
+        raise ImportError(f"{path} not found: run `python -m paper_2603_26232_gb300.native_build` "
                           "(the CUDA library is required; there is no CPU fallback)")
     L = ctypes.CDLL(path)
     for name, (args, res) in _SIGS.items():
@@ -248,3 +250,11 @@ def paraqaoa_profile_read(ctx, which: int):
     by = np.zeros(1, np.float64)
     _check(load().paraqaoa_profile_read(ctx, int(which), _ptr(n), _ptr(ms), _ptr(by)), "paraqaoa_profile_read")
     return int(n[0]), float(ms[0]), float(by[0])
+
+
+def paraqaoa_topk_noalloc(state_dev_ptr: int, n: int, K: int, out_z_dev_ptr: int, out_p_dev_ptr: int,
+                          flags: int = TOPK_CANONICAL, stream_handle: int | None = None):
+    """Top-K of one device-resident state with no device allocation; pointers
+    are raw device addresses (e.g. tensor.data_ptr()). Enqueues only."""
+    _check(load().paraqaoa_topk_noalloc(state_dev_ptr, int(n), int(K), int(flags), out_z_dev_ptr,
+                                        out_p_dev_ptr, stream_handle), "paraqaoa_topk_noalloc")

@@ -431,6 +431,7 @@ const char* paraqaoa_strerror(int code) {
     case PARAQAOA_E_CUDA: return "CUDA runtime error";
     case PARAQAOA_E_TIMEOUT: return "device-side wait timed out";
     case PARAQAOA_E_NO_RESULT: return "no matching simulate results";
+    case PARAQAOA_E_SCRATCH_LIMIT: return "input larger than the fixed no-allocation scratch";
     default: return "unknown error";
   }
 }

@@ -10,6 +10,8 @@
 // stage 2 merges the chunk lists of each instance.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "pq_internal.h"
 
 namespace pq {
@@ -122,3 +124,105 @@ int64_t topk_chunks_of(int n, int raw) {
 }
 
 }  // namespace pq
+
+// ---------------------------------------------------------------------------
+// Allocation-free top-K for one state given by a device pointer.
+//
+// Some callers cannot let a library call cudaMalloc: a host process whose own
+// caching allocator already holds nearly all device memory, or a
+// latency-critical loop that cannot take cudaMalloc's implicit device
+// synchronisation. For them the two top-K stages run here on a fixed
+// file-scope scratch array instead of context-owned buffers.
+//
+// The array lives in every GPU that loads this library, for as long as the
+// process runs. In host code its name is only a host-side stand-in, so its
+// device address is fetched with cudaGetSymbolAddress once per device (on the
+// first call made with that device current) and passed to the kernels.
+// Every call shares the array: calls that overlap on the GPU race. Nothing in
+// it needs clearing: stage 1 writes every entry stage 2 reads.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxChunks = 8192;  // 2^25 ranked entries in chunks of 4096
+static __device__ __align__(256) uint64_t g_topk_scratch[kNoAllocMaxChunks * 32];  // 2 MiB
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint64_t* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device (set-up once).
+cudaError_t noalloc_scratch(uint64_t** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_topk_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<uint64_t*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+__global__ void k_topk_chunks_one(const float2* __restrict__ st, uint64_t cnt,
+                                  uint64_t* __restrict__ scratch) {
+  __shared__ uint64_t lists[8][32];
+  const uint64_t base = (uint64_t)blockIdx.x * pq::kTopkChunk;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint64_t top = 0;
+  for (int it = 0; it < pq::kTopkChunk / (8 * 32); ++it) {
+    const uint64_t z = base + (uint64_t)warp * (pq::kTopkChunk / 8) + (uint64_t)it * 32 + lane;
+    uint64_t key = (z < cnt) ? pq::make_key(st[z], (uint32_t)z) : 0ull;
+    key = pq::warp_sort_desc(key, lane);
+    top = pq::warp_merge_desc(top, key, lane);
+  }
+  lists[warp][lane] = top;
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < 8; ++w) top = pq::warp_merge_desc(top, lists[w][lane], lane);
+    scratch[(uint64_t)blockIdx.x * 32 + lane] = top;
+  }
+}
+
+__global__ void k_topk_final_one(int64_t chunks, int32_t K, const uint64_t* __restrict__ scratch,
+                                 uint32_t* __restrict__ out_z, float* __restrict__ out_p) {
+  __shared__ uint64_t lists[8][32];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint64_t top = 0;
+  for (int64_t c = warp; c < chunks; c += 8) top = pq::warp_merge_desc(top, scratch[(uint64_t)c * 32 + lane], lane);
+  lists[warp][lane] = top;
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < 8; ++w) top = pq::warp_merge_desc(top, lists[w][lane], lane);
+    if ((int)lane < K) {
+      out_z[lane] = ~(uint32_t)(top & 0xffffffffu);
+      out_p[lane] = __uint_as_float((uint32_t)(top >> 32));
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" int paraqaoa_topk_noalloc(const float* state_dev, int32_t n, int32_t K, uint32_t flags,
+                                     uint32_t* out_z_dev, float* out_p_dev, void* stream) {
+  if (!state_dev || !out_z_dev || !out_p_dev || n < 1 || n > PARAQAOA_MAX_QUBITS || K < 1 ||
+      K > PARAQAOA_MAX_TOPK)
+    return PARAQAOA_E_INVAL;
+  const int raw = (flags & PARAQAOA_TOPK_RAW) ? 1 : 0;
+  const uint64_t cnt = raw ? (1ull << n) : (n == 1 ? 1ull : (1ull << (n - 1)));
+  if ((uint64_t)K > cnt) return PARAQAOA_E_INVAL;
+  const int64_t chunks = pq::topk_chunks_of(n, raw);
+  if (chunks > kNoAllocMaxChunks) return PARAQAOA_E_SCRATCH_LIMIT;
+  uint64_t* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return PARAQAOA_E_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_topk_chunks_one<<<(unsigned)chunks, 256, 0, st>>>(reinterpret_cast<const float2*>(state_dev), cnt, scratch);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return PARAQAOA_E_CUDA;
+  k_topk_final_one<<<1, 256, 0, st>>>(chunks, K, scratch, out_z_dev, out_p_dev);
+  return cudaGetLastError() == cudaSuccess ? PARAQAOA_OK : PARAQAOA_E_CUDA;
+}
