@@ -177,6 +177,7 @@ def run_layer_case(args):
     ids = np.repeat(np.arange(M, dtype=np.int32), 8)
     gam, bet = synth.random_angles(len(ids), 2, 3)
     capi.paraqaoa_part_upload(ctx, part)
+    tuned = {20: (None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
     for it in range(args.iters):
         if it == args.iters - 1:
             capi.paraqaoa_profile_enable(ctx, True)
@@ -185,6 +186,7 @@ def run_layer_case(args):
     n_l, ms, by = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
     peak, kind = read_peaks()
     print(json.dumps({"case": "layer_pass", "instances": int(len(ids)), "qubits": 20, "p": 2,
+                      "tile_bits": tuned[20][0], "min_run_qubits": tuned[20][1],
                       "launches": n_l, "ms": ms, "algorithmic_bytes": by,
                       "achieved_gbs": by / (ms / 1e3) / 1e9, "peak_gbs": peak,
                       "frac": by / (ms / 1e3) / 1e9 / peak}), flush=True)
@@ -203,6 +205,8 @@ def main():
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the context's default tile choice (fixed launch sequence for ncu)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -231,6 +235,12 @@ def main():
     graphs = workload(rank)
     Gs = [capi.Graph.of(g) for g in graphs]
     cfg = pkg.SolveConfig(M=M, K=K, p=P_FINAL, grid_points=GRID, adam_steps=STEPS_ADAM, beam=BEAM)
+    # tile size per qubit count, measured once on this GPU (outside the timed region)
+    tuned = {}
+    for G in Gs:
+        part = capi.paraqaoa_partition(G, M)
+        tuned = capi.paraqaoa_autotune(solver.ctx, part, P_FINAL)
+        capi.paraqaoa_part_free(part)
 
     def step():
         return [solver.solve(G, cfg) for G in Gs]
@@ -297,6 +307,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(total_launches),
             "clocks": clk,
+            "autotune": {str(n): {"tile_bits": tb, "min_run_qubits": cm} for n, (tb, cm) in tuned.items() if n == 20},
             "cpu_baseline": cb,
         }
         print(json.dumps(line), flush=True)

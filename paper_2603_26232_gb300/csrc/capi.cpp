@@ -101,7 +101,10 @@ struct paraqaoa_ctx {
   int device = 0;
   size_t budget = 0;
   cudaStream_t own = nullptr, stream = nullptr;
-  int c_min = 3;  // fewest contiguous low qubits a high-group tile carries
+  // per qubit count n: tile bits of the layer passes and the fewest contiguous
+  // low qubits a high-group tile carries (heuristic, or measured by autotune)
+  int8_t tile_bits[PARAQAOA_MAX_QUBITS + 1] = {};
+  int8_t c_min[PARAQAOA_MAX_QUBITS + 1] = {};
   // partition on the device
   uint64_t part_serial = 0;
   DevBuf d_subs, d_planes;
@@ -261,7 +264,7 @@ int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int
     }
     if (big) {
       I.part_off = pl.partial_elems;
-      pl.partial_elems += int64_t(1) << (n - kTileBits);
+      pl.partial_elems += int64_t(1) << (n - c->tile_bits[n]);
       hbm[n].push_back(i);
     } else if (n >= 10) {
       smem[n].push_back(i);
@@ -332,18 +335,19 @@ int plan_run(paraqaoa_ctx* c) {
   }
   for (auto& kv : pl.hbm) {
     const int n = kv.first;
-    const auto sched = make_schedule(n, p, c->c_min, keep, want);
+    const int tb = c->tile_bits[n];
+    const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want);
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
     for (const PassDesc& pd : sched) {
       const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
       ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
-      PQ_CUDA(launch_layer_pass(n, pd, inst, lists + kv.second.first, kv.second.second, subs,
+      PQ_CUDA(launch_layer_pass(tb, n, pd, inst, lists + kv.second.first, kv.second.second, subs,
                                 planes, tables, states, partials, pl.tabcap, c->stream));
     }
     if (want) {
       ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
       PQ_CUDA(launch_expect_reduce(inst, lists + kv.second.first, kv.second.second,
-                                   1 << (n - kTileBits), partials, expect, c->stream));
+                                   1 << (n - tb), partials, expect, c->stream));
     }
   }
   return PARAQAOA_OK;
@@ -353,23 +357,27 @@ int plan_run(paraqaoa_ctx* c) {
 
 namespace pq {
 
-// p layers over G qubit groups: group 0 = qubits [0, 13) (a tile is 2^13
-// consecutive amplitudes), groups 1.. split qubits [13, n) evenly, each tile
-// carrying the lowest 13 - g qubits (>= c_min) so that HBM accesses stay in
-// runs of 2^(13-g) amplitudes. Layer l visits the groups in increasing order
+// p layers over G qubit groups: group 0 = qubits [0, tb) (a tile is 2^tb
+// consecutive amplitudes), groups 1.. split qubits [tb, n) evenly, each tile
+// carrying the lowest tb - g qubits (>= c_min) so that HBM accesses stay in
+// runs of 2^(tb-g) amplitudes. Layer l visits the groups in increasing order
 // for even l and decreasing for odd l, so the last group of layer l is the
 // first of layer l+1 and one pass can finish layer l, apply the phase of
 // l+1 and start its mixer: 1 + p (G - 1) passes in all.
-std::vector<PassDesc> make_schedule(int n, int p, int c_min, bool keep, bool expect) {
-  const int TB = kTileBits;
+int schedule_groups(int n, int tb, int c_min) {
+  const int gmax = tb - std::max(0, std::min(c_min, tb - 1));
+  return 1 + (n - tb + gmax - 1) / gmax;
+}
+
+std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect) {
+  const int TB = tb;
   struct Grp {
     int c, s, mix_lo;
   };
   std::vector<Grp> grp;
   grp.push_back({TB, TB, 0});
   const int rest = n - TB;
-  const int gmax = TB - std::max(0, std::min(c_min, TB - 1));
-  const int H = (rest + gmax - 1) / gmax;
+  const int H = schedule_groups(n, tb, c_min) - 1;
   int s = TB;
   for (int h = 0; h < H; ++h) {
     const int g = rest / H + (h < rest % H ? 1 : 0);
@@ -458,6 +466,12 @@ int paraqaoa_create(paraqaoa_ctx** out, int device, size_t hbm_budget) {
     hbm_budget = (size_t)(0.8 * (double)fr);
   }
   c->budget = hbm_budget;
+  for (int n = 0; n <= PARAQAOA_MAX_QUBITS; ++n) {
+    // default: the smaller tile (more CTAs per SM) unless it needs more passes
+    c->c_min[n] = 3;
+    c->tile_bits[n] = (n >= kMaxTileBits && schedule_groups(n, kMinTileBits, 3) > schedule_groups(n, kMaxTileBits, 3))
+                          ? kMaxTileBits : kMinTileBits;
+  }
   *out = c;
   return PARAQAOA_OK;
 }
@@ -1015,6 +1029,73 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
   PQ_CUDA(cudaMemcpyAsync(out_value, c->d_expect.p, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
   prof_flush(c);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32_t* out_tile_bits,
+                      int32_t* out_c_min) {
+  if (!c || !pt || p < 1 || p > PARAQAOA_MAX_P) return PARAQAOA_E_INVAL;
+  PQ_CUDA(cudaSetDevice(c->device));
+  int rc = upload_part(c, pt, false);
+  if (rc) return rc;
+  cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+  const bool prof = c->prof;
+  c->prof = false;
+  for (int n = kSmemMaxQubits + 1; n <= PARAQAOA_MAX_QUBITS; ++n) {
+    int32_t rep = -1;
+    for (int32_t i = 0; i < pt->M && rep < 0; ++i)
+      if (pt->size[i] == n && pt->weight[i] <= PARAQAOA_MAX_SUBGRAPH_WEIGHT) rep = i;
+    if (rep < 0) continue;
+    // enough copies of one part to fill the GPU (>= 256 MB of state)
+    const int64_t copies = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(256) << 20) / (int64_t(8) << n)));
+    std::vector<int32_t> ids(copies, rep);
+    std::vector<double> ang(copies * p, 0.5);
+    float best_ms = 1e30f;
+    int best_tb = c->tile_bits[n], best_cm = c->c_min[n];
+    std::vector<std::pair<int, int>> seen;  // (groups, carried bits) already timed
+    for (int tb = kMinTileBits; tb <= kMaxTileBits; ++tb) {
+      for (int cm = 2; cm <= 4; ++cm) {
+        const int G = schedule_groups(n, tb, cm);
+        const auto sched = make_schedule(n, p, tb, cm, false, true);
+        const std::pair<int, int> key(G * 100 + tb, sched.size() > 1 ? sched[1].c : 0);
+        if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+        seen.push_back(key);
+        c->tile_bits[n] = (int8_t)tb;
+        c->c_min[n] = (int8_t)cm;
+        rc = plan_build(c, pt, ids.data(), (int32_t)copies, p, PARAQAOA_SIM_EXPECT);
+        if (rc == PARAQAOA_E_ADMISSION) continue;
+        if (rc) break;
+        PQ_CUDA(cudaMemcpyAsync(c->d_gamma.p, ang.data(), sizeof(double) * ang.size(), cudaMemcpyHostToDevice, c->stream));
+        PQ_CUDA(cudaMemcpyAsync(c->d_beta.p, ang.data(), sizeof(double) * ang.size(), cudaMemcpyHostToDevice, c->stream));
+        if ((rc = plan_run(c))) break;  // warm-up
+        PQ_CUDA(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < 3 && !rc; ++r) rc = plan_run(c);
+        PQ_CUDA(cudaEventRecord(e1, c->stream));
+        PQ_CUDA(cudaEventSynchronize(e1));
+        if (rc) break;
+        float ms = 0.f;
+        PQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_tb = tb;
+          best_cm = cm;
+        }
+      }
+      if (rc) break;
+    }
+    c->tile_bits[n] = (int8_t)best_tb;
+    c->c_min[n] = (int8_t)best_cm;
+    if (rc) break;
+  }
+  c->pool.push_back(e0);
+  c->pool.push_back(e1);
+  c->prof = prof;
+  c->plan.valid = false;
+  if (rc) return rc;
+  for (int n = 0; n <= PARAQAOA_MAX_QUBITS; ++n) {
+    if (out_tile_bits) out_tile_bits[n] = c->tile_bits[n];
+    if (out_c_min) out_c_min[n] = c->c_min[n];
+  }
   return PARAQAOA_OK;
 }
 

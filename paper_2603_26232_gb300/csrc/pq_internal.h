@@ -11,9 +11,12 @@
 
 namespace pq {
 
-// Tile geometry of the HBM-streaming layer passes: 2^kTileBits amplitudes
-// per CTA (64 KB of complex64), 32 amplitudes per thread in registers.
-constexpr int kTileBits = 13;
+// Tile geometry of the HBM-streaming layer passes: 2^tb amplitudes per CTA,
+// tb in {kMinTileBits, kMaxTileBits} (32 or 64 KB of complex64), 32
+// amplitudes per thread in registers; the tile size per qubit count is a
+// context setting (heuristic default, or measured by paraqaoa_autotune).
+constexpr int kMinTileBits = 12;
+constexpr int kMaxTileBits = 13;
 constexpr int kRegBits = 5;
 constexpr int kSmemMaxQubits = 14;  // states of <= 14 qubits stay on chip
 constexpr int kTinyMaxQubits = 9;   // n <= 9: one small CTA, plain loops
@@ -45,7 +48,7 @@ struct InstDev {
 // One layer pass over every tile of a group of same-size instances.
 struct PassDesc {
   int32_t c;        // local bits [0, c) are qubits [0, c) (contiguous in HBM)
-  int32_t s;        // local bits [c, kTileBits) are qubits [s, s + kTileBits - c)
+  int32_t s;        // local bits [c, tb) are qubits [s, s + tb - c)
   int32_t mix_lo;   // local bits >= mix_lo are mixed by this pass
   int32_t layerA;   // finish the mixer of this layer (-1: none)
   int32_t layerP;   // apply this layer's cost phase (-1: none)
@@ -69,10 +72,10 @@ cudaError_t launch_smem_sim(int n, const InstDev* inst, const int32_t* list, int
                             int32_t p, const SubDev* subs, const uint32_t* planes,
                             const float2* tables, float2* states, double* expect, int32_t keep,
                             int32_t want_expect, int32_t tabcap, cudaStream_t st);
-cudaError_t launch_layer_pass(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
-                              int32_t nlist, const SubDev* subs, const uint32_t* planes,
-                              const float2* tables, float2* states, double* partials,
-                              int32_t tabcap, cudaStream_t st);
+cudaError_t launch_layer_pass(int tb, int n, const PassDesc& pd, const InstDev* inst,
+                              const int32_t* list, int32_t nlist, const SubDev* subs,
+                              const uint32_t* planes, const float2* tables, float2* states,
+                              double* partials, int32_t tabcap, cudaStream_t st);
 cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32_t nlist,
                                  int32_t tiles, const double* partials, double* expect,
                                  cudaStream_t st);
@@ -123,6 +126,7 @@ cudaError_t launch_theta_split(const double* theta, int32_t S, int32_t p, double
                                double* beta, cudaStream_t st);
 
 // Pass schedule for an n-qubit instance group (layer_pass.cu host helper).
-std::vector<PassDesc> make_schedule(int n, int p, int c_min, bool keep, bool expect);
+std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect);
+int schedule_groups(int n, int tb, int c_min);
 
 }  // namespace pq

@@ -14,6 +14,14 @@
 // the global flip and both unitaries commute with it (C(z) = C(not z)), so
 // it acts as the identity on every state the circuit reaches.
 //
+// Gauge. The kernels hold s_z = i^popcount(z) psi_z instead of psi_z. The
+// butterfly on qubit j then becomes real: with z' = z | 2^j,
+//   (s_z, s_z') -> (s_z + mu s_z', s_z' - mu s_z),
+// two packed FP32x2 FMAs with a broadcast mu and no re/im swaps. The phase is
+// diagonal and |s_z| = |psi_z|, so phases, <C> and probabilities are
+// unchanged; only the initial state and a stored final state carry the
+// factor i^(+-popcount(z)).
+//
 // Cut values are integers computed on the fly from adjacency bit-planes, so
 // the phase exp(-i gamma C) is a lookup into a table of W+1 entries built in
 // FP64; nothing but the state itself moves through HBM.
@@ -29,14 +37,23 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// (x, y) -> (x + i mu y, y + i mu x), as two packed FP32x2 FMAs:
-// x + (-mu, mu) * (y.im, y.re) and y + (-mu, mu) * (x.im, x.re).
+// Gauge butterfly (x, y) -> (x + mu y, y - mu x) on both components at once;
+// in the untransformed state it is (a, b) -> (a + i mu b, b + i mu a).
 __device__ __forceinline__ void bfly(float2& x, float2& y, float mu) {
-  const float2 m = make_float2(-mu, mu);
-  const float2 nx = __ffma2_rn(m, make_float2(y.y, y.x), x);
-  const float2 ny = __ffma2_rn(m, make_float2(x.y, x.x), y);
+  const float2 nx = __ffma2_rn(make_float2(mu, mu), y, x);
+  const float2 ny = __ffma2_rn(make_float2(-mu, -mu), x, y);
   x = nx;
   y = ny;
+}
+
+// i^r * (x + i y) for a small integer r (any sign).
+__device__ __forceinline__ float2 rot_i(float2 a, int r) {
+  switch (r & 3) {
+    case 0: return a;
+    case 1: return make_float2(-a.y, a.x);
+    case 2: return make_float2(-a.x, -a.y);
+    default: return make_float2(a.y, -a.x);
+  }
 }
 
 // C(z) = sum over u with z_u = 1 of the weight of u's neighbours with z_v = 0.
@@ -288,7 +305,7 @@ __global__ void k_tiny_sim(const InstDev* __restrict__ inst_all, const int32_t* 
   const int n = I.n, P = I.P, W = I.W;
   const uint32_t dim = 1u << n, tid = threadIdx.x, nt = blockDim.x;
   for (uint32_t q = tid; q < (uint32_t)(n * P); q += nt) pl[q] = planes_all[S.plane_off + q];
-  for (uint32_t z = tid; z < dim; z += nt) psi[z] = make_float2(1.f, 0.f);
+  for (uint32_t z = tid; z < dim; z += nt) psi[z] = rot_i(make_float2(1.f, 0.f), __popc(z));
   for (int l = 0; l < p; ++l) {
     __syncthreads();
     const float2* tl = tables + I.table_off + (int64_t)l * (W + 1);
@@ -319,7 +336,8 @@ __global__ void k_tiny_sim(const InstDev* __restrict__ inst_all, const int32_t* 
     if (tid == 0) expect[ii] = s * (double)I.final_scale2;
   }
   if (keep)
-    for (uint32_t z = tid; z < dim; z += nt) states[I.state_off + z] = cmul(psi[z], I.final_scale);
+    for (uint32_t z = tid; z < dim; z += nt)
+      states[I.state_off + z] = cmul(rot_i(psi[z], -__popc(z)), I.final_scale);
 }
 
 cudaError_t launch_tiny_sim(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t p,
@@ -364,8 +382,11 @@ __global__ void __launch_bounds__(1 << (TB - 5))
   const uint32_t mask2 = (1u << (TB - 10)) - 1u;
   float2 a[32];
   int cur = NR - 1;
+  {
+    const float2 b = rot_i(make_float2(1.f, 0.f), __popc(li0_rt<TB>(cur, tid)));
 #pragma unroll
-  for (int k = 0; k < 32; ++k) a[k] = make_float2(1.f, 0.f);
+    for (int k = 0; k < 32; ++k) a[k] = rot_i(b, __popc(k));
+  }
   for (int l = 0; l < p; ++l) {
     const float2* tl = tables + I.table_off + (int64_t)l * (W + 1);
     for (int c = tid; c <= W; c += NT) tab[c] = tl[c];
@@ -403,8 +424,9 @@ __global__ void __launch_bounds__(1 << (TB - 5))
   if (keep) {
     goto_layout<TB>(a, sm, tid, cur, 0);
     float2* out = states + I.state_off;
+    const float2 fs = rot_i(I.final_scale, -__popc(tid));
 #pragma unroll
-    for (int k = 0; k < 32; ++k) out[li_of<TB, 0>(tid, k)] = cmul(a[k], I.final_scale);
+    for (int k = 0; k < 32; ++k) out[li_of<TB, 0>(tid, k)] = cmul(a[k], rot_i(fs, -__popc(k)));
   }
 }
 
@@ -490,6 +512,7 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   int* qk = reinterpret_cast<int*>(pl + PARAQAOA_MAX_QUBITS * kMaxPlanes);  // 32
   TileConst* tc = reinterpret_cast<TileConst*>(qk + 32);
   double* red = reinterpret_cast<double*>(tc + 1);
+  int* thr = reinterpret_cast<int*>(red + 16);  // per-thread instance constants: [6][NT]
   const uint32_t tid = threadIdx.x;
   const int c = pd.c, s = pd.s, g = TB - c;
   const uint32_t lowt = (uint32_t)(s - c);
@@ -508,9 +531,6 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   uint32_t zt0 = 0;
   for (int lb = 0; lb < TB - 5; ++lb)
     if ((tid >> lb) & 1u) zt0 |= 1u << qubit_of(lb, c, s);
-  uint32_t e[5];
-#pragma unroll
-  for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
   // the thread's qubits in the cut layout
   const uint32_t li0 = li_of<TB, RC>(tid, 0);
   uint32_t zJ = 0;
@@ -525,7 +545,6 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   float muA = 0.f, muB = 0.f;
   float2 fscale = make_float2(1.f, 0.f);
   int64_t state_off = 0, part_off = 0;
-  int qJ = 0, Bk[5] = {0, 0, 0, 0, 0};
   for (int64_t wt = t_begin; wt < t_end; ++wt) {
     const int li_idx = (int)(wt >> tiles_log2);
     const uint32_t tile = (uint32_t)(wt & tmask);
@@ -568,13 +587,12 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
           const uint32_t* row = pl + u * P;
           for (int b = 0; b < P; ++b) acc += __popc(row[b] & zJ) << b;
         }
-        qJ = -acc;
-#pragma unroll
+        thr[tid] = -acc;  // -2 Q_J(z_J)
         for (int j = 0; j < 5; ++j) {
           const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
           int bj = 0;
           for (int b = 0; b < P; ++b) bj += __popc(row[b] & zJ) << b;
-          Bk[j] = -2 * bj;
+          thr[(1 + j) * NT + tid] = -2 * bj;  // B_u of register slot j
         }
       }
     }
@@ -594,10 +612,14 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
       if (tid == 31) tc->cf = cut_eval(zbase, pl, n, P);
     }
     float2 a[32];
-    if (pd.init) {
+    if (pd.init) {  // s_z = i^popcount(z), z = tile base | thread qubits | register qubits
+      const float2 b = rot_i(make_float2(1.f, 0.f), __popc(zbase | zJ));
 #pragma unroll
-      for (int k = 0; k < 32; ++k) a[k] = make_float2(1.f, 0.f);
+      for (int k = 0; k < 32; ++k) a[k] = rot_i(b, __popc(k));
     } else {
+      uint32_t e[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
       uint32_t off = 0;
       a[0] = base[0];
 #pragma unroll
@@ -610,11 +632,11 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
     __syncthreads();  // tile constants visible
     int A = 0, kap[5] = {0, 0, 0, 0, 0};
     if (need_cut) {
-      A = tc->cf + qJ;
+      A = tc->cf + thr[tid];
       for (int lb = 0; lb < TB; ++lb)
         if ((li0 >> lb) & 1u) A += tc->lam[lb];
 #pragma unroll
-      for (int j = 0; j < 5; ++j) kap[j] = tc->lam[slot_lb(TB, RC, j)] + Bk[j];
+      for (int j = 0; j < 5; ++j) kap[j] = tc->lam[slot_lb(TB, RC, j)] + thr[(1 + j) * NT + tid];
     }
     if (pd.layerA >= 0) {
       // a load starts in layout 0; an init tile starts in the cut layout
@@ -669,10 +691,14 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
         if constexpr (NR == 3) transpose<TB, 2, 0>(a, sm, tid);
         if constexpr (NR == 2) transpose<TB, 1, 0>(a, sm, tid);
       }
-      if (pd.last) {
+      if (pd.last) {  // back from the gauge, times lambda_p
+        const float2 fs = rot_i(fscale, -__popc(zbase | zt0));
 #pragma unroll
-        for (int k = 0; k < 32; ++k) a[k] = cmul(a[k], fscale);
+        for (int k = 0; k < 32; ++k) a[k] = cmul(a[k], rot_i(fs, -__popc(k)));
       }
+      uint32_t e[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
       uint32_t off = 0;
       base[0] = a[0];
 #pragma unroll
@@ -689,18 +715,20 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   }
 }
 
-size_t layer_pass_smem(int tabcap) {
-  return (size_t)tabcap * sizeof(float2) + (size_t)padded_elems<kTileBits>() * sizeof(float2) +
-         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * 4 + sizeof(TileConst) + 16 * sizeof(double);
+size_t layer_pass_smem(int tb, int tabcap) {
+  const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - 5));
+  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) +
+         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * 4 + sizeof(TileConst) + 16 * sizeof(double) +
+         6 * sizeof(int) * (size_t(1) << (tb - 5));
 }
 
-template <int NR>
-static cudaError_t launch_layer_nr(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
-                                   int32_t nlist, const SubDev* subs, const uint32_t* planes,
-                                   const float2* tables, float2* states, double* partials,
-                                   int32_t tabcap, cudaStream_t st) {
-  const size_t smem = layer_pass_smem(tabcap);
-  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<kTileBits, NR>,
+template <int TB, int NR>
+static cudaError_t launch_layer_t(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                                  int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                                  const float2* tables, float2* states, double* partials,
+                                  int32_t tabcap, cudaStream_t st) {
+  const size_t smem = layer_pass_smem(TB, tabcap);
+  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, NR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   static int num_sm = 0;
@@ -710,26 +738,37 @@ static cudaError_t launch_layer_nr(int n, const PassDesc& pd, const InstDev* ins
     cudaDeviceGetAttribute(&num_sm, cudaDevAttrMultiProcessorCount, dev);
   }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_layer_pass<kTileBits, NR>,
-                                                    1 << (kTileBits - 5), smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_layer_pass<TB, NR>, 1 << (TB - 5), smem);
   if (e != cudaSuccess) return e;
-  const int tiles_log2 = n - kTileBits;
+  const int tiles_log2 = n - TB;
   const int64_t total = (int64_t)nlist << tiles_log2;
   const int64_t grid = std::min<int64_t>(total, (int64_t)num_sm * std::max(per_sm, 1));
-  k_layer_pass<kTileBits, NR><<<(unsigned)grid, 1 << (kTileBits - 5), smem, st>>>(
+  k_layer_pass<TB, NR><<<(unsigned)grid, 1 << (TB - 5), smem, st>>>(
       pd, n, tiles_log2, total, inst, list, subs, planes, tables, states, partials, tabcap);
   return cudaGetLastError();
 }
 
-cudaError_t launch_layer_pass(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
-                              int32_t nlist, const SubDev* subs, const uint32_t* planes,
-                              const float2* tables, float2* states, double* partials,
-                              int32_t tabcap, cudaStream_t st) {
+cudaError_t launch_layer_pass(int tb, int n, const PassDesc& pd, const InstDev* inst,
+                              const int32_t* list, int32_t nlist, const SubDev* subs,
+                              const uint32_t* planes, const float2* tables, float2* states,
+                              double* partials, int32_t tabcap, cudaStream_t st) {
   if (nlist <= 0) return cudaSuccess;
-  const int nr = 1 + (pd.mix_lo < kTileBits - 5) + (pd.mix_lo < kTileBits - 10);
-  if (nr == 1) return launch_layer_nr<1>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st);
-  if (nr == 2) return launch_layer_nr<2>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st);
-  return launch_layer_nr<3>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st);
+  if (n < tb) return cudaErrorInvalidValue;
+  const int nr = 1 + (pd.mix_lo < tb - 5) + (pd.mix_lo < tb - 10);
+#define PQ_LAUNCH(TBV, NRV) \
+  return launch_layer_t<TBV, NRV>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st)
+  if (tb == 12) {
+    if (nr == 1) PQ_LAUNCH(12, 1);
+    if (nr == 2) PQ_LAUNCH(12, 2);
+    PQ_LAUNCH(12, 3);
+  }
+  if (tb == 13) {
+    if (nr == 1) PQ_LAUNCH(13, 1);
+    if (nr == 2) PQ_LAUNCH(13, 2);
+    PQ_LAUNCH(13, 3);
+  }
+#undef PQ_LAUNCH
+  return cudaErrorInvalidValue;
 }
 
 // Sum the per-tile partials of each instance in a fixed order, times |lambda_p|^2.

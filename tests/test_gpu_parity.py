@@ -345,3 +345,28 @@ def test_error_codes(api):
         assert e.value.code == capi.E_INVAL
     finally:
         capi.paraqaoa_part_free(ph)
+
+
+def test_autotune_choices_keep_parity(api, orc):
+    """The autotuner picks a tile size and contiguous run per qubit count; the
+    tuned passes must still match the oracle."""
+    capi, ctx = api
+    sizes = [15, 18, 20, 22]
+    g = chain_graph(sizes, 0.35, 31, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        choice = capi.paraqaoa_autotune(ctx, part, 2)
+        for n in sizes:
+            tb, cm = choice[n]
+            assert tb in (12, 13) and cm in (2, 3, 4)
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), 2, 99)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+        ex = capi.paraqaoa_expect(ctx, len(ids))
+        for i, s in enumerate(subs):
+            ref = orc.simulate(s, gam[i], bet[i])
+            assert np.max(np.abs(capi.paraqaoa_state(ctx, i, s.n) - ref)) <= AMP_TOL
+            assert abs(ex[i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL
+    finally:
+        capi.paraqaoa_part_free(part)
