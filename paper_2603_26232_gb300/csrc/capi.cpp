@@ -68,6 +68,7 @@ struct ProfRec {
   int cls;
   cudaEvent_t a, b;
   double bytes;
+  int kernels;
 };
 
 }  // namespace
@@ -111,6 +112,7 @@ struct paraqaoa_ctx {
   // simulate
   SimPlan plan;
   DevBuf d_inst, d_lists, d_gamma, d_beta, d_tables, d_states, d_partials, d_expect;
+  DevBuf d_consts;  // per-instance cut constants of the current layer pass
   // top-K
   DevBuf d_chunk_off, d_topk_scratch, d_topk_z, d_topk_p;
   // merge
@@ -143,8 +145,10 @@ struct ProfScope {
   paraqaoa_ctx* c;
   int cls;
   double bytes;
+  int kernels;
   cudaEvent_t a = nullptr;
-  ProfScope(paraqaoa_ctx* c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+  ProfScope(paraqaoa_ctx* c_, int cls_, double bytes_, int kernels_ = 1)
+      : c(c_), cls(cls_), bytes(bytes_), kernels(kernels_) {
     if (c->prof) {
       a = get_event(c);
       cudaEventRecord(a, c->stream);
@@ -154,7 +158,7 @@ struct ProfScope {
     if (c->prof && a) {
       cudaEvent_t b = get_event(c);
       cudaEventRecord(b, c->stream);
-      c->pending.push_back({cls, a, b, bytes});
+      c->pending.push_back({cls, a, b, bytes, kernels});
     }
   }
 };
@@ -165,7 +169,7 @@ void prof_flush(paraqaoa_ctx* c) {
   for (auto& r : c->pending) {
     float t = 0.f;
     cudaEventElapsedTime(&t, r.a, r.b);
-    c->launches[r.cls] += 1;
+    c->launches[r.cls] += r.kernels;
     c->ms[r.cls] += t;
     c->bytes[r.cls] += r.bytes;
     c->pool.push_back(r.a);
@@ -338,11 +342,18 @@ int plan_run(paraqaoa_ctx* c) {
     const int tb = c->tile_bits[n];
     const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want);
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
+    PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * cut_consts_elems(tb, kv.second.second)));
     for (const PassDesc& pd : sched) {
+      if (pd.layerP >= 0 || pd.expect) {
+        ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+        PQ_CUDA(launch_cut_consts(tb, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
+                                  c->d_consts.as<int32_t>(), c->stream));
+      }
       const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
       ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
       PQ_CUDA(launch_layer_pass(tb, n, pd, inst, lists + kv.second.first, kv.second.second, subs,
-                                planes, tables, states, partials, pl.tabcap, c->stream));
+                                planes, tables, states, partials, pl.tabcap, c->d_consts.as<int32_t>(),
+                                c->stream));
     }
     if (want) {
       ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
@@ -492,7 +503,7 @@ void paraqaoa_destroy(paraqaoa_ctx* c) {
                     &c->m_key, &c->m_path, &c->m_sides[0], &c->m_sides[1], &c->m_score[0],
                     &c->m_score[1], &c->m_rank[0], &c->m_rank[1], &c->m_r2s[0], &c->m_r2s[1],
                     &c->m_keys, &c->m_nb, &c->o_vals, &c->o_best, &c->o_theta, &c->o_m, &c->o_v,
-                    &c->o_w, &c->o_g2, &c->o_b2};
+                    &c->o_w, &c->o_g2, &c->o_b2, &c->d_consts};
   for (DevBuf* b : bufs) b->release();
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
@@ -717,7 +728,7 @@ int paraqaoa_topk(paraqaoa_ctx* c, int32_t count, int32_t K, uint32_t* out_z, fl
   PQ_CUDA(cudaMemcpyAsync(c->d_chunk_off.p, off.data(), sizeof(int64_t) * (count + 1),
                           cudaMemcpyHostToDevice, c->stream));
   {
-    ProfScope ps(c, PARAQAOA_KCLASS_TOPK, 0);
+    ProfScope ps(c, PARAQAOA_KCLASS_TOPK, 0, 2);
     PQ_CUDA(launch_topk_stages(c->d_inst.as<InstDev>(), count, K, raw, c->d_chunk_off.as<int64_t>(),
                                off[count], c->d_states.as<float2>(), c->d_topk_scratch.as<uint64_t>(),
                                c->d_topk_z.as<uint32_t>(), c->d_topk_p.as<float>(), c->stream));
@@ -890,7 +901,7 @@ int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* 
   for (int32_t l = 0; l < M; ++l) {
     const int nx = cur ^ 1;
     {
-      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
+      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0, 2);
       PQ_CUDA(launch_beam_level(md, l, nb, B, c->m_keys.as<uint64_t>(), c->m_sides[cur].as<uint32_t>(),
                                 c->m_score[cur].as<int64_t>(), c->m_rank[cur].as<int32_t>(),
                                 c->m_r2s[cur].as<int32_t>(), c->m_sides[nx].as<uint32_t>(),

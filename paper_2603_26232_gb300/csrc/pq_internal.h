@@ -75,7 +75,11 @@ cudaError_t launch_smem_sim(int n, const InstDev* inst, const int32_t* list, int
 cudaError_t launch_layer_pass(int tb, int n, const PassDesc& pd, const InstDev* inst,
                               const int32_t* list, int32_t nlist, const SubDev* subs,
                               const uint32_t* planes, const float2* tables, float2* states,
-                              double* partials, int32_t tabcap, cudaStream_t st);
+                              double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
+int64_t cut_consts_elems(int tb, int32_t nlist);
+cudaError_t launch_cut_consts(int tb, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                              int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                              int32_t* consts, cudaStream_t st);
 cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32_t nlist,
                                  int32_t tiles, const double* partials, double* expect,
                                  cudaStream_t st);

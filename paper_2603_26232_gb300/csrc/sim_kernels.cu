@@ -460,25 +460,26 @@ cudaError_t launch_smem_sim(int n, const InstDev* inst, const int32_t* list, int
 }
 
 // ---------------------------------------------------------------------------
-// n >= 15: layer passes that stream the state through HBM. A tile is 2^13
+// n >= 15: layer passes that stream the state through HBM. A tile is 2^TB
 // amplitudes whose local bits [0, c) are qubits [0, c) (contiguous in HBM) and
-// whose local bits [c, 13) are qubits [s, s + 13 - c); the remaining qubits are
+// whose local bits [c, TB) are qubits [s, s + TB - c); the remaining qubits are
 // fixed per tile. A pass may finish one layer's mixer on the tile's qubits,
 // apply the next layer's phase and start its mixer, so p layers take p + 1
 // passes when the qubits split into two groups (see make_schedule).
 //
-// CTAs are persistent: CTA b walks a contiguous range of the launch's
-// (instance, tile) pairs, so the per-instance set-up (bit-planes, phase table,
-// per-thread cut constants) is paid once per instance, not once per tile.
+// One CTA per tile, tiles of an instance consecutive in blockIdx: the block
+// scheduler then keeps the CTAs resident on the GPU on neighbouring tiles and
+// refills an SM the moment a CTA retires, which measured faster than
+// persistent CTAs walking their own tile ranges.
 //
 // Cut values. With T the tile's qubits, F the fixed ones, J the qubits of the
 // thread index and K the 5 register qubits of the layout where the cut is
 // needed, C(z) = sum_u d_u z_u - 2 sum_{u<v} w_uv z_u z_v splits into
 //   C = C(z_F)                          per tile (z_T = 0)
 //     + sum_{u in J} lam_u z_u          lam_u = d_u - 2 sum_{v in F} w_uv z_v, per tile
-//     - 2 Q_J(z_J)                      per thread and instance
-//     + sum_{u in K} z_u (lam_u + B_u)  B_u = -2 sum_{v in J} w_uv z_v, per thread
-//     - 2 Q_K(z_K)                      32-entry table per instance
+//     - 2 Q_J(z_J)                      per thread and instance (k_cut_consts)
+//     + sum_{u in K} z_u (lam_u + B_u)  B_u = -2 sum_{v in J} w_uv z_v, per thread (k_cut_consts)
+//     - 2 Q_K(z_K)                      32-entry table per instance (k_cut_consts)
 // so a cut value costs a broadcast load and a few integer adds.
 struct TileConst {
   int cf;        // C(z_F)
@@ -487,7 +488,7 @@ struct TileConst {
 };
 static_assert(sizeof(TileConst) % 16 == 0, "shared-memory carve-up needs 16-byte multiples");
 
-__device__ __forceinline__ uint32_t qubit_of(int lb, int c, int s) {
+__host__ __device__ __forceinline__ uint32_t qubit_of(int lb, int c, int s) {
   return lb < c ? (uint32_t)lb : (uint32_t)(s + (lb - c));
 }
 
@@ -496,28 +497,147 @@ __device__ __forceinline__ uint32_t qubit_of(int lb, int c, int s) {
 __host__ __device__ constexpr int gray(int i) { return i ^ (i >> 1); }
 __host__ __device__ constexpr int gray_bit(int i) { return i & 1 ? 0 : (i & 2 ? 1 : (i & 4 ? 2 : (i & 8 ? 3 : 4))); }
 
+// Entries per instance of the k_cut_consts output: 32 (Q_K table) + 6 per thread.
+__host__ __device__ constexpr int cut_consts_stride(int tb) { return 32 + 6 * (1 << (tb - 5)); }
+
+// Per-instance cut constants of one pass, for the cut layout RC:
+// out[0..32) = -2 Q_K(k); out[32 + t] = -2 Q_J(z_J(t)); out[32 + (1+j) NT + t] = B_u(t)
+// of register slot j.
+template <int TB, int RC>
+__global__ void __launch_bounds__(1 << (TB - 5))
+    k_cut_consts(PassDesc pd, int32_t n, const InstDev* __restrict__ inst_all,
+                 const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
+                 const uint32_t* __restrict__ planes_all, int32_t* __restrict__ out) {
+  constexpr uint32_t NT = 1u << (TB - 5);
+  __shared__ uint32_t pl[PARAQAOA_MAX_QUBITS * kMaxPlanes];
+  const uint32_t tid = threadIdx.x;
+  const InstDev* Ip = inst_all + list[blockIdx.x];
+  const SubDev S = subs[Ip->sub];
+  const int P = Ip->P, c = pd.c, s = pd.s;
+  for (uint32_t q = tid; q < (uint32_t)(n * P); q += NT) pl[q] = planes_all[S.plane_off + q];
+  __syncthreads();
+  int32_t* o = out + (int64_t)blockIdx.x * cut_consts_stride(TB);
+  if (tid < 32) {
+    uint32_t zk = 0;
+    for (int j = 0; j < 5; ++j)
+      if ((tid >> j) & 1u) zk |= 1u << qubit_of(slot_lb(TB, RC, j), c, s);
+    int acc = 0;
+    for (int j = 0; j < 5; ++j) {
+      if (!((tid >> j) & 1u)) continue;
+      const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
+      for (int b = 0; b < P; ++b) acc += __popc(row[b] & zk) << b;
+    }
+    o[tid] = -acc;  // each pair of set K qubits counted from both ends
+  }
+  const uint32_t li0 = li_of<TB, RC>(tid, 0);
+  uint32_t zJ = 0;
+  for (int lb = 0; lb < TB; ++lb)
+    if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
+  int acc = 0;
+  for (int u = 0; u < n; ++u) {
+    if (!((zJ >> u) & 1u)) continue;
+    const uint32_t* row = pl + u * P;
+    for (int b = 0; b < P; ++b) acc += __popc(row[b] & zJ) << b;
+  }
+  o[32 + tid] = -acc;
+  for (int j = 0; j < 5; ++j) {
+    const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
+    int bj = 0;
+    for (int b = 0; b < P; ++b) bj += __popc(row[b] & zJ) << b;
+    o[32 + (1 + j) * NT + tid] = -2 * bj;
+  }
+}
+
 template <int TB, int NR>
 __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
-    k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, int64_t total_tiles,
-                 const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list,
-                 const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes_all,
-                 const float2* __restrict__ tables, float2* __restrict__ states,
-                 double* __restrict__ partials, int32_t tabcap) {
+    k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
+                 const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
+                 const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
+                 float2* __restrict__ states, double* __restrict__ partials, int32_t tabcap,
+                 const int32_t* __restrict__ consts) {
   constexpr uint32_t NT = 1u << (TB - 5);
   constexpr int RC = NR - 1;  // layout of the cut step (phase / <C>)
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* tab = reinterpret_cast<float2*>(smraw);
   float2* sm = tab + tabcap;
-  uint32_t* pl = reinterpret_cast<uint32_t*>(sm + padded_elems<TB>());
-  int* qk = reinterpret_cast<int*>(pl + PARAQAOA_MAX_QUBITS * kMaxPlanes);  // 32
+  int* qk = reinterpret_cast<int*>(sm + padded_elems<TB>());  // 32
   TileConst* tc = reinterpret_cast<TileConst*>(qk + 32);
   double* red = reinterpret_cast<double*>(tc + 1);
-  int* thr = reinterpret_cast<int*>(red + 16);  // per-thread instance constants: [6][NT]
   const uint32_t tid = threadIdx.x;
   const int c = pd.c, s = pd.s, g = TB - c;
   const uint32_t lowt = (uint32_t)(s - c);
-  const uint32_t tmask = (1u << tiles_log2) - 1u;
+  const int li_idx = (int)(blockIdx.x >> tiles_log2);
+  const uint32_t tile = blockIdx.x & ((1u << tiles_log2) - 1u);
+  const InstDev* Ip = inst_all + list[li_idx];
+  const int P = Ip->P, W = Ip->W;
+  const uint32_t* pl = planes_all + subs[Ip->sub].plane_off;
+  const bool need_cut = pd.layerP >= 0 || pd.expect;
+  const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
 
+  // ---- set-up: phase table, Q_K table, tile constants (warp 0)
+  if (pd.layerP >= 0) {
+    const float2* tl = tables + Ip->table_off + (int64_t)pd.layerP * (W + 1);
+    for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
+  }
+  const int32_t* cc_inst = consts + (int64_t)li_idx * cut_consts_stride(TB);
+  if (need_cut && tid < 32) {
+    qk[tid] = cc_inst[tid];
+    // lane u < n: contribution of vertex u to C(z_F); lane u < TB: lam of local bit u
+    int cfu = 0;
+    if ((int)tid < n && ((zbase >> tid) & 1u)) {
+      const uint32_t* row = pl + tid * P;
+      for (int b = 0; b < P; ++b) cfu += __popc(row[b] & ~zbase) << b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cfu += __shfl_xor_sync(0xffffffffu, cfu, o);
+    if (tid < (uint32_t)TB) {
+      const uint32_t* row = pl + qubit_of(tid, c, s) * P;
+      int d = 0, a = 0;
+      for (int b = 0; b < P; ++b) {
+        d += __popc(row[b]) << b;
+        a += __popc(row[b] & zbase) << b;
+      }
+      tc->lam[tid] = d - 2 * a;
+    }
+    if (tid == 0) tc->cf = cfu;
+  }
+  // qubit offsets of the load/store layout: thread part and register bits
+  uint32_t zt0 = 0;
+  for (int lb = 0; lb < TB - 5; ++lb)
+    if ((tid >> lb) & 1u) zt0 |= 1u << qubit_of(lb, c, s);
+  float2* base = states + Ip->state_off + (zbase | zt0);
+
+  float2 a[32];
+  const uint32_t li0 = li_of<TB, RC>(tid, 0);
+  if (pd.init) {  // s_z = i^popcount(z), z = tile base | thread qubits | register qubits
+    uint32_t zJ = 0;
+    for (int lb = 0; lb < TB; ++lb)
+      if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
+    const float2 b = rot_i(make_float2(1.f, 0.f), __popc(zbase | zJ));
+#pragma unroll
+    for (int k = 0; k < 32; ++k) a[k] = rot_i(b, __popc(k));
+  } else {
+    uint32_t e[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
+    uint32_t off = 0;
+    a[0] = base[0];
+#pragma unroll
+    for (int i = 1; i < 32; ++i) {
+      const int k = gray(i), b = gray_bit(i);
+      off = ((k >> b) & 1) ? off + e[b] : off - e[b];
+      a[k] = base[off];
+    }
+  }
+  __syncthreads();  // phase table, Q_K and tile constants visible
+  int A = 0, kap[5] = {0, 0, 0, 0, 0};
+  if (need_cut) {
+    A = tc->cf + cc_inst[32 + tid];
+    for (int lb = 0; lb < TB; ++lb)
+      if ((li0 >> lb) & 1u) A += tc->lam[lb];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) kap[j] = tc->lam[slot_lb(TB, RC, j)] + cc_inst[32 + (1 + j) * NT + tid];
+  }
   // mix masks of the rounds (register slots whose local bit this pass mixes)
   uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
 #pragma unroll
@@ -526,237 +646,135 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
     if (TB - 10 + j >= pd.mix_lo) mm1 |= 1u << j;
     if (j >= pd.mix_lo && j < TB - 10) mm2 |= 1u << j;
   }
-  const bool need_cut = pd.layerP >= 0 || pd.expect;
-  // qubit offsets of the load/store layout: thread part and register bits
-  uint32_t zt0 = 0;
-  for (int lb = 0; lb < TB - 5; ++lb)
-    if ((tid >> lb) & 1u) zt0 |= 1u << qubit_of(lb, c, s);
-  // the thread's qubits in the cut layout
-  const uint32_t li0 = li_of<TB, RC>(tid, 0);
-  uint32_t zJ = 0;
-  for (int lb = 0; lb < TB; ++lb)
-    if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
-
-  const int64_t per = (total_tiles + gridDim.x - 1) / gridDim.x;
-  const int64_t t_begin = (int64_t)blockIdx.x * per;
-  const int64_t t_end = min(total_tiles, t_begin + per);
-  int cur_inst = -1;
-  int P = 1, W = 0;
-  float muA = 0.f, muB = 0.f;
-  float2 fscale = make_float2(1.f, 0.f);
-  int64_t state_off = 0, part_off = 0;
-  for (int64_t wt = t_begin; wt < t_end; ++wt) {
-    const int li_idx = (int)(wt >> tiles_log2);
-    const uint32_t tile = (uint32_t)(wt & tmask);
-    if (li_idx != cur_inst) {
-      // ---- per-instance set-up
-      cur_inst = li_idx;
-      const InstDev* Ip = inst_all + list[li_idx];
-      const SubDev S = subs[Ip->sub];
-      P = Ip->P;
-      W = Ip->W;
-      state_off = Ip->state_off;
-      part_off = Ip->part_off;
-      fscale = Ip->final_scale;
-      muA = pd.layerA >= 0 ? Ip->mu[pd.layerA] : 0.f;
-      muB = pd.layerB >= 0 ? Ip->mu[pd.layerB] : 0.f;
-      const int64_t table_off = Ip->table_off;
-      __syncthreads();  // the previous tile is done with the shared tables
-      for (uint32_t q = tid; q < (uint32_t)(n * P); q += NT) pl[q] = planes_all[S.plane_off + q];
-      if (pd.layerP >= 0) {
-        const float2* tl = tables + table_off + (int64_t)pd.layerP * (W + 1);
-        for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
-      }
-      __syncthreads();
-      if (need_cut) {
-        if (tid < 32) {  // -2 Q_K(k)
-          uint32_t zk = 0;
-          for (int j = 0; j < 5; ++j)
-            if ((tid >> j) & 1u) zk |= 1u << qubit_of(slot_lb(TB, RC, j), c, s);
-          int acc = 0;
-          for (int j = 0; j < 5; ++j) {
-            if (!((tid >> j) & 1u)) continue;
-            const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
-            for (int b = 0; b < P; ++b) acc += __popc(row[b] & zk) << b;
-          }
-          qk[tid] = -acc;
-        }
-        int acc = 0;  // -2 Q_J(z_J): each pair of set J qubits counted from both ends
-        for (int u = 0; u < n; ++u) {
-          if (!((zJ >> u) & 1u)) continue;
-          const uint32_t* row = pl + u * P;
-          for (int b = 0; b < P; ++b) acc += __popc(row[b] & zJ) << b;
-        }
-        thr[tid] = -acc;  // -2 Q_J(z_J)
-        for (int j = 0; j < 5; ++j) {
-          const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
-          int bj = 0;
-          for (int b = 0; b < P; ++b) bj += __popc(row[b] & zJ) << b;
-          thr[(1 + j) * NT + tid] = -2 * bj;  // B_u of register slot j
-        }
-      }
+  if (pd.layerA >= 0) {
+    const float muA = Ip->mu[pd.layerA];
+    mix_regs(a, muA, mm0);
+    if constexpr (NR > 1) {
+      transpose<TB, 0, 1>(a, sm, tid);
+      mix_regs(a, muA, mm1);
     }
-    const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
-    float2* base = states + state_off + (zbase | zt0);
-    // ---- per-tile constants (one warp), overlapped with the loads below
-    if (need_cut && tid < 32) {
-      if (tid < (uint32_t)TB) {
-        const uint32_t* row = pl + qubit_of(tid, c, s) * P;
-        int d = 0, a = 0;
-        for (int b = 0; b < P; ++b) {
-          d += __popc(row[b]) << b;
-          a += __popc(row[b] & zbase) << b;
-        }
-        tc->lam[tid] = d - 2 * a;
-      }
-      if (tid == 31) tc->cf = cut_eval(zbase, pl, n, P);
+    if constexpr (NR > 2) {
+      transpose<TB, 1, 2>(a, sm, tid);
+      mix_regs(a, muA, mm2);
     }
-    float2 a[32];
-    if (pd.init) {  // s_z = i^popcount(z), z = tile base | thread qubits | register qubits
-      const float2 b = rot_i(make_float2(1.f, 0.f), __popc(zbase | zJ));
+  }
+  if (pd.layerP >= 0) {
+    int S = A;
+    a[0] = cmul(a[0], tab[tix(S + qk[0], W)]);
 #pragma unroll
-      for (int k = 0; k < 32; ++k) a[k] = rot_i(b, __popc(k));
-    } else {
-      uint32_t e[5];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
-      uint32_t off = 0;
-      a[0] = base[0];
-#pragma unroll
-      for (int i = 1; i < 32; ++i) {
-        const int k = gray(i), b = gray_bit(i);
-        off = ((k >> b) & 1) ? off + e[b] : off - e[b];
-        a[k] = base[off];
-      }
+    for (int i = 1; i < 32; ++i) {
+      const int k = gray(i), b = gray_bit(i);
+      S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
+      a[k] = cmul(a[k], tab[tix(S + qk[k], W)]);
     }
-    __syncthreads();  // tile constants visible
-    int A = 0, kap[5] = {0, 0, 0, 0, 0};
-    if (need_cut) {
-      A = tc->cf + thr[tid];
-      for (int lb = 0; lb < TB; ++lb)
-        if ((li0 >> lb) & 1u) A += tc->lam[lb];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) kap[j] = tc->lam[slot_lb(TB, RC, j)] + thr[(1 + j) * NT + tid];
+  }
+  if (pd.layerB >= 0) {
+    const float muB = Ip->mu[pd.layerB];
+    if constexpr (NR > 2) {
+      mix_regs(a, muB, mm2);
+      transpose<TB, 2, 1>(a, sm, tid);
     }
-    if (pd.layerA >= 0) {
-      // a load starts in layout 0; an init tile starts in the cut layout
-      mix_regs(a, muA, mm0);
-      if constexpr (NR > 1) {
-        transpose<TB, 0, 1>(a, sm, tid);
-        mix_regs(a, muA, mm1);
-      }
-      if constexpr (NR > 2) {
-        transpose<TB, 1, 2>(a, sm, tid);
-        mix_regs(a, muA, mm2);
-      }
+    if constexpr (NR > 1) {
+      mix_regs(a, muB, mm1);
+      transpose<TB, 1, 0>(a, sm, tid);
     }
-    if (pd.layerP >= 0) {
-      int S = A;
-      a[0] = cmul(a[0], tab[tix(S + qk[0], W)]);
+    mix_regs(a, muB, mm0);
+  }
+  if (pd.expect) {
+    float acc = 0.f;
+    int S = A;
 #pragma unroll
-      for (int i = 1; i < 32; ++i) {
-        const int k = gray(i), b = gray_bit(i);
+    for (int i = 0; i < 32; ++i) {
+      const int k = gray(i);
+      if (i > 0) {
+        const int b = gray_bit(i);
         S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
-        a[k] = cmul(a[k], tab[tix(S + qk[k], W)]);
       }
+      acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)(S + qk[k]), acc);
     }
-    if (pd.layerB >= 0) {
-      if constexpr (NR > 2) {
-        mix_regs(a, muB, mm2);
-        transpose<TB, 2, 1>(a, sm, tid);
-      }
-      if constexpr (NR > 1) {
-        mix_regs(a, muB, mm1);
-        transpose<TB, 1, 0>(a, sm, tid);
-      }
-      mix_regs(a, muB, mm0);
+    const double sum = block_sum((double)acc, red, tid, NT);
+    if (tid == 0) partials[Ip->part_off + tile] = sum;
+  }
+  if (pd.store) {
+    if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
+      if constexpr (NR == 3) transpose<TB, 2, 0>(a, sm, tid);
+      if constexpr (NR == 2) transpose<TB, 1, 0>(a, sm, tid);
     }
-    if (pd.expect) {
-      float acc = 0.f;
-      int S = A;
+    if (pd.last) {  // back from the gauge, times lambda_p
+      const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zt0));
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int k = gray(i);
-        if (i > 0) {
-          const int b = gray_bit(i);
-          S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
-        }
-        acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)(S + qk[k]), acc);
-      }
-      const double sum = block_sum((double)acc, red, tid, NT);
-      if (tid == 0) partials[part_off + tile] = sum;
+      for (int k = 0; k < 32; ++k) a[k] = cmul(a[k], rot_i(fs, -__popc(k)));
     }
-    if (pd.store) {
-      if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
-        if constexpr (NR == 3) transpose<TB, 2, 0>(a, sm, tid);
-        if constexpr (NR == 2) transpose<TB, 1, 0>(a, sm, tid);
-      }
-      if (pd.last) {  // back from the gauge, times lambda_p
-        const float2 fs = rot_i(fscale, -__popc(zbase | zt0));
+    uint32_t e[5];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) a[k] = cmul(a[k], rot_i(fs, -__popc(k)));
-      }
-      uint32_t e[5];
+    for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
+    uint32_t off = 0;
+    base[0] = a[0];
 #pragma unroll
-      for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
-      uint32_t off = 0;
-      base[0] = a[0];
-#pragma unroll
-      for (int i = 1; i < 32; ++i) {
-        const int k = gray(i), b = gray_bit(i);
-        off = ((k >> b) & 1) ? off + e[b] : off - e[b];
-        base[off] = a[k];
-      }
+    for (int i = 1; i < 32; ++i) {
+      const int k = gray(i), b = gray_bit(i);
+      off = ((k >> b) & 1) ? off + e[b] : off - e[b];
+      base[off] = a[k];
     }
-    // With two or more rounds, the transposes' barriers already order this
-    // tile's reads of the tile constants and of the transpose buffer before
-    // the next tile's writes; a single-round pass needs its own barrier.
-    if constexpr (NR == 1) __syncthreads();
   }
 }
 
 size_t layer_pass_smem(int tb, int tabcap) {
   const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - 5));
-  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) +
-         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * 4 + sizeof(TileConst) + 16 * sizeof(double) +
-         6 * sizeof(int) * (size_t(1) << (tb - 5));
+  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
+         16 * sizeof(double);
+}
+
+int64_t cut_consts_elems(int tb, int32_t nlist) { return (int64_t)nlist * cut_consts_stride(tb); }
+
+cudaError_t launch_cut_consts(int tb, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                              int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                              int32_t* consts, cudaStream_t st) {
+  if (nlist <= 0 || !(pd.layerP >= 0 || pd.expect)) return cudaSuccess;
+  const int nr = 1 + (pd.mix_lo < tb - 5) + (pd.mix_lo < tb - 10);
+#define PQ_CC(TBV, RCV) \
+  k_cut_consts<TBV, RCV><<<nlist, 1 << (TBV - 5), 0, st>>>(pd, n, inst, list, subs, planes, consts); \
+  return cudaGetLastError()
+  if (tb == 12) {
+    if (nr == 1) { PQ_CC(12, 0); }
+    if (nr == 2) { PQ_CC(12, 1); }
+    PQ_CC(12, 2);
+  }
+  if (tb == 13) {
+    if (nr == 1) { PQ_CC(13, 0); }
+    if (nr == 2) { PQ_CC(13, 1); }
+    PQ_CC(13, 2);
+  }
+#undef PQ_CC
+  return cudaErrorInvalidValue;
 }
 
 template <int TB, int NR>
 static cudaError_t launch_layer_t(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                                   int32_t nlist, const SubDev* subs, const uint32_t* planes,
                                   const float2* tables, float2* states, double* partials,
-                                  int32_t tabcap, cudaStream_t st) {
+                                  int32_t tabcap, int32_t* consts, cudaStream_t st) {
   const size_t smem = layer_pass_smem(TB, tabcap);
   cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, NR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  static int num_sm = 0;
-  if (num_sm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&num_sm, cudaDevAttrMultiProcessorCount, dev);
-  }
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_layer_pass<TB, NR>, 1 << (TB - 5), smem);
-  if (e != cudaSuccess) return e;
   const int tiles_log2 = n - TB;
-  const int64_t total = (int64_t)nlist << tiles_log2;
-  const int64_t grid = std::min<int64_t>(total, (int64_t)num_sm * std::max(per_sm, 1));
-  k_layer_pass<TB, NR><<<(unsigned)grid, 1 << (TB - 5), smem, st>>>(
-      pd, n, tiles_log2, total, inst, list, subs, planes, tables, states, partials, tabcap);
+  const int64_t blocks = (int64_t)nlist << tiles_log2;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  k_layer_pass<TB, NR><<<(unsigned)blocks, 1 << (TB - 5), smem, st>>>(
+      pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts);
   return cudaGetLastError();
 }
 
 cudaError_t launch_layer_pass(int tb, int n, const PassDesc& pd, const InstDev* inst,
                               const int32_t* list, int32_t nlist, const SubDev* subs,
                               const uint32_t* planes, const float2* tables, float2* states,
-                              double* partials, int32_t tabcap, cudaStream_t st) {
+                              double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
   if (nlist <= 0) return cudaSuccess;
   if (n < tb) return cudaErrorInvalidValue;
   const int nr = 1 + (pd.mix_lo < tb - 5) + (pd.mix_lo < tb - 10);
 #define PQ_LAUNCH(TBV, NRV) \
-  return launch_layer_t<TBV, NRV>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, st)
+  return launch_layer_t<TBV, NRV>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st)
   if (tb == 12) {
     if (nr == 1) PQ_LAUNCH(12, 1);
     if (nr == 2) PQ_LAUNCH(12, 2);
