@@ -69,14 +69,18 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_for(kernel_src: str):
-    """ncu DRAM bytes per launch recorded for the current kernel source, else None."""
+def traffic_for(kernel_src: str, alg_bytes_per_launch: float):
+    """DRAM bytes per layer-pass launch: the ncu-measured DRAM/algorithmic ratio
+    of profiles/layer_pass_traffic.json times this run's algorithmic bytes per
+    launch; None when the kernel source changed since that capture."""
     path = os.path.join(ROOT, "profiles", "layer_pass_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return rec.get("dram_bytes_per_launch_full") if rec.get("source_sha256") == h else None
+    if rec.get("source_sha256") != h:
+        return None
+    return rec["dram_over_algorithmic"] * alg_bytes_per_launch
 
 
 class Clocks:
@@ -285,7 +289,8 @@ def main():
     launches, lp_ms, lp_bytes = prof[capi.KCLASS_LAYER_PASS]
     peak, peak_kind = read_peaks()
     achieved = (lp_bytes / (lp_ms / 1e3)) / 1e9 if lp_ms > 0 else 0.0
-    traffic = traffic_for(os.path.join(ROOT, "paper_2603_26232_gb300", "csrc", "sim_kernels.cu"))
+    traffic = traffic_for(os.path.join(ROOT, "paper_2603_26232_gb300", "csrc", "sim_kernels.cu"),
+                          lp_bytes / max(launches, 1))
     total_launches = sum(v[0] for v in prof.values())
     h2d = sum(int(G.row_ptr.nbytes + G.col.nbytes + G.w.nbytes) for G in Gs)
     d2h = len(Gs) * (M * K * 8 + NV + M * 8 * 3)
