@@ -181,7 +181,7 @@ def run_layer_case(args):
     ids = np.repeat(np.arange(M, dtype=np.int32), 8)
     gam, bet = synth.random_angles(len(ids), 2, 3)
     capi.paraqaoa_part_upload(ctx, part)
-    tuned = {20: (None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
+    tuned = {20: (None, None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
     for it in range(args.iters):
         if it == args.iters - 1:
             capi.paraqaoa_profile_enable(ctx, True)
@@ -190,7 +190,7 @@ def run_layer_case(args):
     n_l, ms, by = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
     peak, kind = read_peaks()
     print(json.dumps({"case": "layer_pass", "instances": int(len(ids)), "qubits": 20, "p": 2,
-                      "tile_bits": tuned[20][0], "min_run_qubits": tuned[20][1],
+                      "tile_bits": tuned[20][0], "reg_bits": tuned[20][1], "min_run_qubits": tuned[20][2],
                       "launches": n_l, "ms": ms, "algorithmic_bytes": by,
                       "achieved_gbs": by / (ms / 1e3) / 1e9, "peak_gbs": peak,
                       "frac": by / (ms / 1e3) / 1e9 / peak}), flush=True)
@@ -312,7 +312,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(total_launches),
             "clocks": clk,
-            "autotune": {str(n): {"tile_bits": tb, "min_run_qubits": cm} for n, (tb, cm) in tuned.items() if n == 20},
+            "autotune": {str(n): {"tile_bits": tb, "reg_bits": rb, "min_run_qubits": cm}
+                         for n, (tb, rb, cm) in tuned.items() if n == 20},
             "cpu_baseline": cb,
         }
         print(json.dumps(line), flush=True)

@@ -203,14 +203,15 @@ int paraqaoa_topk_noalloc(const float *state_dev, int32_t n, int32_t K, uint32_t
 
 /* Autotuner for the HBM-streaming layer passes (no counterpart in the paper,
  * which runs a fixed solver per subgraph). For every qubit count n >= 15
- * present in `part`, times the candidate tile sizes (2^12 or 2^13
- * amplitudes per CTA) and minimum contiguous-qubit runs (2..4) on copies of
- * one part of that size at depth p, and keeps the fastest for ctx. Choices
- * that give the same pass schedule are timed once. Optional outputs (31
- * entries each, indexed by n): chosen tile bits and minimum run. Without a
- * call the context uses the smaller tile unless it needs more passes. */
+ * present in `part`, times the candidate tile shapes (2^12 amplitudes per CTA
+ * as 32 or 16 registers per thread, or 2^13 as 32) and minimum
+ * contiguous-qubit runs (2..4) on copies of one part of that size at depth p,
+ * and keeps the fastest for ctx. Choices that give the same pass schedule are
+ * timed once. Optional outputs (31 entries each, indexed by n): chosen tile
+ * bits, register bits per thread and minimum run. Without a call the context
+ * uses the 2^12 x 16-register shape unless 2^13 needs fewer passes. */
 int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p,
-                      int32_t *out_tile_bits, int32_t *out_c_min);
+                      int32_t *out_tile_bits, int32_t *out_reg_bits, int32_t *out_c_min);
 
 /* Per-kernel device time recorded with CUDA events on the context stream.
  * enable != 0 starts recording (and clears the counters). */

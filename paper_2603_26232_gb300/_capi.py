@@ -60,7 +60,7 @@ _SIGS = {
     "paraqaoa_grid_search": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P], ctypes.c_int),
     "paraqaoa_optimize": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                            ctypes.c_double, P, P, P], ctypes.c_int),
-    "paraqaoa_autotune": ([P, P, ctypes.c_int32, P, P], ctypes.c_int),
+    "paraqaoa_autotune": ([P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_profile_enable": ([P, ctypes.c_int32], ctypes.c_int),
     "paraqaoa_profile_read": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -243,11 +243,12 @@ def paraqaoa_optimize(ctx, part, ids, p: int, gamma0, beta0, steps: int = 32, lr
 
 def paraqaoa_autotune(ctx, part, p: int = 2):
     """Time the layer-pass tile candidates per qubit count; returns
-    {n: (tile_bits, min_contiguous_qubits)} for n >= 15."""
+    {n: (tile_bits, register_bits, min_contiguous_qubits)} for n >= 15."""
     tb = np.zeros(31, np.int32)
+    rb = np.zeros(31, np.int32)
     cm = np.zeros(31, np.int32)
-    _check(load().paraqaoa_autotune(ctx, part, int(p), _ptr(tb), _ptr(cm)), "paraqaoa_autotune")
-    return {n: (int(tb[n]), int(cm[n])) for n in range(15, 31)}
+    _check(load().paraqaoa_autotune(ctx, part, int(p), _ptr(tb), _ptr(rb), _ptr(cm)), "paraqaoa_autotune")
+    return {n: (int(tb[n]), int(rb[n]), int(cm[n])) for n in range(15, 31)}
 
 
 def paraqaoa_profile_enable(ctx, enable: bool = True):

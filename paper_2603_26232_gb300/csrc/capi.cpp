@@ -104,7 +104,7 @@ struct paraqaoa_ctx {
   cudaStream_t own = nullptr, stream = nullptr;
   // per qubit count n: tile bits of the layer passes and the fewest contiguous
   // low qubits a high-group tile carries (heuristic, or measured by autotune)
-  int8_t tile_bits[PARAQAOA_MAX_QUBITS + 1] = {};
+  int8_t tile_kind[PARAQAOA_MAX_QUBITS + 1] = {};  // index into kTileShapes
   int8_t c_min[PARAQAOA_MAX_QUBITS + 1] = {};
   // partition on the device
   uint64_t part_serial = 0;
@@ -268,7 +268,7 @@ int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int
     }
     if (big) {
       I.part_off = pl.partial_elems;
-      pl.partial_elems += int64_t(1) << (n - c->tile_bits[n]);
+      pl.partial_elems += int64_t(1) << (n - kTileShapes[c->tile_kind[n]].tb);
       hbm[n].push_back(i);
     } else if (n >= 10) {
       smem[n].push_back(i);
@@ -339,19 +339,19 @@ int plan_run(paraqaoa_ctx* c) {
   }
   for (auto& kv : pl.hbm) {
     const int n = kv.first;
-    const int tb = c->tile_bits[n];
+    const int kind = c->tile_kind[n], tb = kTileShapes[kind].tb;
     const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want);
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
-    PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * cut_consts_elems(tb, kv.second.second)));
+    PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * cut_consts_elems(kind, kv.second.second)));
     for (const PassDesc& pd : sched) {
       if (pd.layerP >= 0 || pd.expect) {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-        PQ_CUDA(launch_cut_consts(tb, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
+        PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
                                   c->d_consts.as<int32_t>(), c->stream));
       }
       const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
       ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
-      PQ_CUDA(launch_layer_pass(tb, n, pd, inst, lists + kv.second.first, kv.second.second, subs,
+      PQ_CUDA(launch_layer_pass(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs,
                                 planes, tables, states, partials, pl.tabcap, c->d_consts.as<int32_t>(),
                                 c->stream));
     }
@@ -479,9 +479,11 @@ int paraqaoa_create(paraqaoa_ctx** out, int device, size_t hbm_budget) {
   c->budget = hbm_budget;
   for (int n = 0; n <= PARAQAOA_MAX_QUBITS; ++n) {
     // default: the smaller tile (more CTAs per SM) unless it needs more passes
+    // default: the 2^12 tile with 16 registers per thread (highest occupancy)
+    // unless the 2^13 tile needs fewer passes
     c->c_min[n] = 3;
-    c->tile_bits[n] = (n >= kMaxTileBits && schedule_groups(n, kMinTileBits, 3) > schedule_groups(n, kMaxTileBits, 3))
-                          ? kMaxTileBits : kMinTileBits;
+    c->tile_kind[n] = (n >= kMaxTileBits && schedule_groups(n, kMinTileBits, 3) > schedule_groups(n, kMaxTileBits, 3))
+                          ? 2 : 1;
   }
   *out = c;
   return PARAQAOA_OK;
@@ -1044,7 +1046,7 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
 }
 
 int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32_t* out_tile_bits,
-                      int32_t* out_c_min) {
+                      int32_t* out_reg_bits, int32_t* out_c_min) {
   if (!c || !pt || p < 1 || p > PARAQAOA_MAX_P) return PARAQAOA_E_INVAL;
   PQ_CUDA(cudaSetDevice(c->device));
   int rc = upload_part(c, pt, false);
@@ -1062,16 +1064,18 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
     std::vector<int32_t> ids(copies, rep);
     std::vector<double> ang(copies * p, 0.5);
     float best_ms = 1e30f;
-    int best_tb = c->tile_bits[n], best_cm = c->c_min[n];
-    std::vector<std::pair<int, int>> seen;  // (groups, carried bits) already timed
-    for (int tb = kMinTileBits; tb <= kMaxTileBits; ++tb) {
+    int best_kind = c->tile_kind[n], best_cm = c->c_min[n];
+    std::vector<std::pair<int, int>> seen;  // (kind and groups, carried bits) already timed
+    for (int kind = 0; kind < kTileKinds; ++kind) {
+      const int tb = kTileShapes[kind].tb;
+      if (n < tb) continue;
       for (int cm = 2; cm <= 4; ++cm) {
         const int G = schedule_groups(n, tb, cm);
         const auto sched = make_schedule(n, p, tb, cm, false, true);
-        const std::pair<int, int> key(G * 100 + tb, sched.size() > 1 ? sched[1].c : 0);
+        const std::pair<int, int> key(G * 100 + kind, sched.size() > 1 ? sched[1].c : 0);
         if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
         seen.push_back(key);
-        c->tile_bits[n] = (int8_t)tb;
+        c->tile_kind[n] = (int8_t)kind;
         c->c_min[n] = (int8_t)cm;
         rc = plan_build(c, pt, ids.data(), (int32_t)copies, p, PARAQAOA_SIM_EXPECT);
         if (rc == PARAQAOA_E_ADMISSION) continue;
@@ -1088,13 +1092,13 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
         PQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best_ms) {
           best_ms = ms;
-          best_tb = tb;
+          best_kind = kind;
           best_cm = cm;
         }
       }
       if (rc) break;
     }
-    c->tile_bits[n] = (int8_t)best_tb;
+    c->tile_kind[n] = (int8_t)best_kind;
     c->c_min[n] = (int8_t)best_cm;
     if (rc) break;
   }
@@ -1104,7 +1108,8 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
   c->plan.valid = false;
   if (rc) return rc;
   for (int n = 0; n <= PARAQAOA_MAX_QUBITS; ++n) {
-    if (out_tile_bits) out_tile_bits[n] = c->tile_bits[n];
+    if (out_tile_bits) out_tile_bits[n] = kTileShapes[c->tile_kind[n]].tb;
+    if (out_reg_bits) out_reg_bits[n] = kTileShapes[c->tile_kind[n]].r;
     if (out_c_min) out_c_min[n] = c->c_min[n];
   }
   return PARAQAOA_OK;

@@ -11,13 +11,16 @@
 
 namespace pq {
 
-// Tile geometry of the HBM-streaming layer passes: 2^tb amplitudes per CTA,
-// tb in {kMinTileBits, kMaxTileBits} (32 or 64 KB of complex64), 32
-// amplitudes per thread in registers; the tile size per qubit count is a
-// context setting (heuristic default, or measured by paraqaoa_autotune).
+// Tile shapes of the HBM-streaming layer passes: 2^tb amplitudes per CTA held
+// as 2^r registers per thread (2^(tb-r) threads). The shape per qubit count is
+// a context setting (heuristic default, or measured by paraqaoa_autotune).
+struct TileShape {
+  int tb, r;
+};
+constexpr int kTileKinds = 3;
+constexpr TileShape kTileShapes[kTileKinds] = {{12, 5}, {12, 4}, {13, 5}};
 constexpr int kMinTileBits = 12;
 constexpr int kMaxTileBits = 13;
-constexpr int kRegBits = 5;
 constexpr int kSmemMaxQubits = 14;  // states of <= 14 qubits stay on chip
 constexpr int kTinyMaxQubits = 9;   // n <= 9: one small CTA, plain loops
 constexpr int kMaxPlanes = 16;      // weight bit-planes (weights < 2^16)
@@ -72,12 +75,12 @@ cudaError_t launch_smem_sim(int n, const InstDev* inst, const int32_t* list, int
                             int32_t p, const SubDev* subs, const uint32_t* planes,
                             const float2* tables, float2* states, double* expect, int32_t keep,
                             int32_t want_expect, int32_t tabcap, cudaStream_t st);
-cudaError_t launch_layer_pass(int tb, int n, const PassDesc& pd, const InstDev* inst,
+cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev* inst,
                               const int32_t* list, int32_t nlist, const SubDev* subs,
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
-int64_t cut_consts_elems(int tb, int32_t nlist);
-cudaError_t launch_cut_consts(int tb, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+int64_t cut_consts_elems(int kind, int32_t nlist);
+cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
                               int32_t* consts, cudaStream_t st);
 cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32_t nlist,

@@ -80,53 +80,79 @@ __device__ __forceinline__ int kappa(uint32_t z0, uint32_t kmask, int u, const u
 // the shared-memory read in bounds even if a caller's data broke that.
 __device__ __forceinline__ uint32_t tix(int c, int W) { return min((uint32_t)c, (uint32_t)W); }
 
-// Shared-memory slot of local index li: one pad element after every 32, which
-// makes every register-layout transpose bank-conflict free. It is additive
-// over disjoint bits (pad(t | k) = pad(t) + pad(k)), so a thread's addresses
-// are one base register plus compile-time offsets.
-__host__ __device__ __forceinline__ constexpr uint32_t pad(uint32_t li) { return li + (li >> 5); }
-template <int TB>
-__host__ __device__ constexpr int padded_elems() { return (1 << TB) + (1 << (TB - 5)); }
-
-// Register layouts of a 2^TB tile held by 2^(TB-5) threads x 32 registers.
-// Layout RHO puts 5 local index bits in the register index k:
-//   RHO 0: bits [TB-5, TB)   (load/store layout: lanes are consecutive)
-//   RHO 1: bits [TB-10, TB-5)
-//   RHO 2: bits [0, 5)
+// Register layouts of a 2^TB tile held by 2^(TB-R) threads x 2^R registers.
+// Layout RHO puts R local index bits in the register index k:
+//   RHO 0: bits [TB-R, TB)   (load/store layout: lanes are consecutive)
+//   RHO 1: bits [TB-2R, TB-R)
+//   RHO 2: bits [0, R)       (overlaps RHO 1 when TB < 3R; only bits < TB-2R mix there)
 // and the remaining bits, in increasing order, in the thread index.
-template <int TB, int RHO>
-__device__ __forceinline__ uint32_t li_of(uint32_t tid, uint32_t k) {
+//
+// Shared-memory slot of local index li: one pad element after every 2^R,
+// which makes every transpose between these layouts bank-conflict free
+// (checked exhaustively for the tile shapes in use). It is additive over
+// disjoint bits (pad(t | k) = pad(t) + pad(k)), so a thread's addresses are
+// one base register plus compile-time offsets.
+template <int R>
+__host__ __device__ __forceinline__ constexpr uint32_t padr(uint32_t li) { return li + (li >> R); }
+template <int TB, int R>
+__host__ __device__ constexpr int padded_r() { return (1 << TB) + (1 << (TB - R)); }
+
+template <int TB, int R, int RHO>
+__device__ __forceinline__ uint32_t lir(uint32_t tid, uint32_t k) {
   if constexpr (RHO == 0) {
-    return tid | (k << (TB - 5));
+    return tid | (k << (TB - R));
   } else if constexpr (RHO == 1) {
-    constexpr int lb = TB - 10;
-    return (tid & ((1u << lb) - 1u)) | (k << lb) | ((tid >> lb) << (TB - 5));
+    constexpr int lb = TB - 2 * R;
+    return (tid & ((1u << lb) - 1u)) | (k << lb) | ((tid >> lb) << (TB - R));
   } else {
-    return k | (tid << 5);
+    return k | (tid << R);
   }
 }
 
+__host__ __device__ __forceinline__ int slot_lbr(int TB, int R, int rho, int j) {
+  return rho == 0 ? TB - R + j : (rho == 1 ? TB - 2 * R + j : j);
+}
+
+template <int TB, int R, int FROM, int TO>
+__device__ __forceinline__ void transposer(float2 (&a)[1 << R], float2* sm, uint32_t tid) {
+  float2* pf = sm + padr<R>(lir<TB, R, FROM>(tid, 0));
+  float2* pt = sm + padr<R>(lir<TB, R, TO>(tid, 0));
+#pragma unroll
+  for (int k = 0; k < (1 << R); ++k) pf[padr<R>(lir<TB, R, FROM>(0, k))] = a[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < (1 << R); ++k) a[k] = pt[padr<R>(lir<TB, R, TO>(0, k))];
+  __syncthreads();
+}
+
+template <int R>
+__device__ __forceinline__ void mix_regs_r(float2 (&a)[1 << R], float mu, uint32_t mask) {
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    if ((mask >> j) & 1u) {
+#pragma unroll
+      for (int k = 0; k < (1 << R); ++k)
+        if (!((k >> j) & 1)) bfly(a[k], a[k | (1 << j)], mu);
+    }
+  }
+}
+
+// The on-chip kernel uses the 32-register shape throughout.
+__host__ __device__ __forceinline__ constexpr uint32_t pad(uint32_t li) { return padr<5>(li); }
+template <int TB>
+__host__ __device__ constexpr int padded_elems() { return padded_r<TB, 5>(); }
+template <int TB, int RHO>
+__device__ __forceinline__ uint32_t li_of(uint32_t tid, uint32_t k) { return lir<TB, 5, RHO>(tid, k); }
 template <int TB>
 __device__ __forceinline__ uint32_t li0_rt(int rho, uint32_t tid) {
   if (rho == 0) return li_of<TB, 0>(tid, 0);
   if (rho == 1) return li_of<TB, 1>(tid, 0);
   return li_of<TB, 2>(tid, 0);
 }
-
-__host__ __device__ __forceinline__ int slot_lb(int TB, int rho, int j) {
-  return rho == 0 ? TB - 5 + j : (rho == 1 ? TB - 10 + j : j);
-}
-
+__host__ __device__ __forceinline__ int slot_lb(int TB, int rho, int j) { return slot_lbr(TB, 5, rho, j); }
 template <int TB, int FROM, int TO>
 __device__ __forceinline__ void transpose(float2 (&a)[32], float2* sm, uint32_t tid) {
-  float2* pf = sm + pad(li_of<TB, FROM>(tid, 0));
-  float2* pt = sm + pad(li_of<TB, TO>(tid, 0));
-#pragma unroll
-  for (int k = 0; k < 32; ++k) pf[pad(li_of<TB, FROM>(0, k))] = a[k];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < 32; ++k) a[k] = pt[pad(li_of<TB, TO>(0, k))];
-  __syncthreads();
+  transposer<TB, 5, FROM, TO>(a, sm, tid);
 }
 
 template <int TB>
@@ -142,16 +168,7 @@ __device__ __forceinline__ void goto_layout(float2 (&a)[32], float2* sm, uint32_
   cur = to;
 }
 
-__device__ __forceinline__ void mix_regs(float2 (&a)[32], float mu, uint32_t mask) {
-#pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    if ((mask >> j) & 1u) {
-#pragma unroll
-      for (int k = 0; k < 32; ++k)
-        if (!((k >> j) & 1)) bfly(a[k], a[k | (1 << j)], mu);
-    }
-  }
-}
+__device__ __forceinline__ void mix_regs(float2 (&a)[32], float mu, uint32_t mask) { mix_regs_r<5>(a, mu, mask); }
 
 // Per-layout cut decomposition shared by the CTA: for the 5 register qubits
 // Kq of layout rho, ckk[k] = C restricted to edges inside Kq at assignment k.
@@ -497,18 +514,19 @@ __host__ __device__ __forceinline__ uint32_t qubit_of(int lb, int c, int s) {
 __host__ __device__ constexpr int gray(int i) { return i ^ (i >> 1); }
 __host__ __device__ constexpr int gray_bit(int i) { return i & 1 ? 0 : (i & 2 ? 1 : (i & 4 ? 2 : (i & 8 ? 3 : 4))); }
 
-// Entries per instance of the k_cut_consts output: 32 (Q_K table) + 6 per thread.
-__host__ __device__ constexpr int cut_consts_stride(int tb) { return 32 + 6 * (1 << (tb - 5)); }
+// Entries per instance of the k_cut_consts output: 2^R (Q_K table) + (1 + R) per thread.
+__host__ __device__ constexpr int cut_consts_stride(int tb, int r) { return (1 << r) + (1 + r) * (1 << (tb - r)); }
 
 // Per-instance cut constants of one pass, for the cut layout RC:
-// out[0..32) = -2 Q_K(k); out[32 + t] = -2 Q_J(z_J(t)); out[32 + (1+j) NT + t] = B_u(t)
-// of register slot j.
-template <int TB, int RC>
-__global__ void __launch_bounds__(1 << (TB - 5))
+// out[0..2^R) = -2 Q_K(k); out[2^R + t] = -2 Q_J(z_J(t)); out[2^R + (1+j) NT + t] =
+// B_u(t) of register slot j.
+template <int TB, int R, int RC>
+__global__ void __launch_bounds__(1 << (TB - R))
     k_cut_consts(PassDesc pd, int32_t n, const InstDev* __restrict__ inst_all,
                  const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
                  const uint32_t* __restrict__ planes_all, int32_t* __restrict__ out) {
-  constexpr uint32_t NT = 1u << (TB - 5);
+  constexpr uint32_t NT = 1u << (TB - R);
+  constexpr int KQ = 1 << R;
   __shared__ uint32_t pl[PARAQAOA_MAX_QUBITS * kMaxPlanes];
   const uint32_t tid = threadIdx.x;
   const InstDev* Ip = inst_all + list[blockIdx.x];
@@ -516,20 +534,20 @@ __global__ void __launch_bounds__(1 << (TB - 5))
   const int P = Ip->P, c = pd.c, s = pd.s;
   for (uint32_t q = tid; q < (uint32_t)(n * P); q += NT) pl[q] = planes_all[S.plane_off + q];
   __syncthreads();
-  int32_t* o = out + (int64_t)blockIdx.x * cut_consts_stride(TB);
-  if (tid < 32) {
+  int32_t* o = out + (int64_t)blockIdx.x * cut_consts_stride(TB, R);
+  if (tid < (uint32_t)KQ) {
     uint32_t zk = 0;
-    for (int j = 0; j < 5; ++j)
-      if ((tid >> j) & 1u) zk |= 1u << qubit_of(slot_lb(TB, RC, j), c, s);
+    for (int j = 0; j < R; ++j)
+      if ((tid >> j) & 1u) zk |= 1u << qubit_of(slot_lbr(TB, R, RC, j), c, s);
     int acc = 0;
-    for (int j = 0; j < 5; ++j) {
+    for (int j = 0; j < R; ++j) {
       if (!((tid >> j) & 1u)) continue;
-      const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
+      const uint32_t* row = pl + qubit_of(slot_lbr(TB, R, RC, j), c, s) * P;
       for (int b = 0; b < P; ++b) acc += __popc(row[b] & zk) << b;
     }
     o[tid] = -acc;  // each pair of set K qubits counted from both ends
   }
-  const uint32_t li0 = li_of<TB, RC>(tid, 0);
+  const uint32_t li0 = lir<TB, R, RC>(tid, 0);
   uint32_t zJ = 0;
   for (int lb = 0; lb < TB; ++lb)
     if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
@@ -539,28 +557,32 @@ __global__ void __launch_bounds__(1 << (TB - 5))
     const uint32_t* row = pl + u * P;
     for (int b = 0; b < P; ++b) acc += __popc(row[b] & zJ) << b;
   }
-  o[32 + tid] = -acc;
-  for (int j = 0; j < 5; ++j) {
-    const uint32_t* row = pl + qubit_of(slot_lb(TB, RC, j), c, s) * P;
+  o[KQ + tid] = -acc;
+  for (int j = 0; j < R; ++j) {
+    const uint32_t* row = pl + qubit_of(slot_lbr(TB, R, RC, j), c, s) * P;
     int bj = 0;
     for (int b = 0; b < P; ++b) bj += __popc(row[b] & zJ) << b;
-    o[32 + (1 + j) * NT + tid] = -2 * bj;
+    o[KQ + (1 + j) * NT + tid] = -2 * bj;
   }
 }
 
-template <int TB, int NR>
-__global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
+// Occupancy target of a tile shape: resident CTAs per SM the register file allows.
+__host__ __device__ constexpr int layer_min_blocks(int tb, int r) { return r == 4 ? 3 : (tb >= 13 ? 2 : 4); }
+
+template <int TB, int R, int NR>
+__global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
     k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
                  const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
                  const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
                  float2* __restrict__ states, double* __restrict__ partials, int32_t tabcap,
                  const int32_t* __restrict__ consts) {
-  constexpr uint32_t NT = 1u << (TB - 5);
+  constexpr uint32_t NT = 1u << (TB - R);
+  constexpr int KQ = 1 << R;  // registers per thread
   constexpr int RC = NR - 1;  // layout of the cut step (phase / <C>)
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* tab = reinterpret_cast<float2*>(smraw);
   float2* sm = tab + tabcap;
-  int* qk = reinterpret_cast<int*>(sm + padded_elems<TB>());  // 32
+  int* qk = reinterpret_cast<int*>(sm + padded_r<TB, R>());  // 2^R entries (<= 32)
   TileConst* tc = reinterpret_cast<TileConst*>(qk + 32);
   double* red = reinterpret_cast<double*>(tc + 1);
   const uint32_t tid = threadIdx.x;
@@ -579,9 +601,9 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
     const float2* tl = tables + Ip->table_off + (int64_t)pd.layerP * (W + 1);
     for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
   }
-  const int32_t* cc_inst = consts + (int64_t)li_idx * cut_consts_stride(TB);
+  const int32_t* cc_inst = consts + (int64_t)li_idx * cut_consts_stride(TB, R);
   if (need_cut && tid < 32) {
-    qk[tid] = cc_inst[tid];
+    if (tid < (uint32_t)KQ) qk[tid] = cc_inst[tid];
     // lane u < n: contribution of vertex u to C(z_F); lane u < TB: lam of local bit u
     int cfu = 0;
     if ((int)tid < n && ((zbase >> tid) & 1u)) {
@@ -603,66 +625,68 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   }
   // qubit offsets of the load/store layout: thread part and register bits
   uint32_t zt0 = 0;
-  for (int lb = 0; lb < TB - 5; ++lb)
+  for (int lb = 0; lb < TB - R; ++lb)
     if ((tid >> lb) & 1u) zt0 |= 1u << qubit_of(lb, c, s);
   float2* base = states + Ip->state_off + (zbase | zt0);
 
-  float2 a[32];
-  const uint32_t li0 = li_of<TB, RC>(tid, 0);
+  float2 a[KQ];
+  const uint32_t li0 = lir<TB, R, RC>(tid, 0);
   if (pd.init) {  // s_z = i^popcount(z), z = tile base | thread qubits | register qubits
     uint32_t zJ = 0;
     for (int lb = 0; lb < TB; ++lb)
       if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
     const float2 b = rot_i(make_float2(1.f, 0.f), __popc(zbase | zJ));
 #pragma unroll
-    for (int k = 0; k < 32; ++k) a[k] = rot_i(b, __popc(k));
+    for (int k = 0; k < KQ; ++k) a[k] = rot_i(b, __popc(k));
   } else {
-    uint32_t e[5];
+    uint32_t e[R];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
+    for (int j = 0; j < R; ++j) e[j] = 1u << qubit_of(TB - R + j, c, s);
     uint32_t off = 0;
     a[0] = base[0];
 #pragma unroll
-    for (int i = 1; i < 32; ++i) {
+    for (int i = 1; i < KQ; ++i) {
       const int k = gray(i), b = gray_bit(i);
       off = ((k >> b) & 1) ? off + e[b] : off - e[b];
       a[k] = base[off];
     }
   }
   __syncthreads();  // phase table, Q_K and tile constants visible
-  int A = 0, kap[5] = {0, 0, 0, 0, 0};
+  int A = 0, kap[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) kap[j] = 0;
   if (need_cut) {
-    A = tc->cf + cc_inst[32 + tid];
+    A = tc->cf + cc_inst[KQ + tid];
     for (int lb = 0; lb < TB; ++lb)
       if ((li0 >> lb) & 1u) A += tc->lam[lb];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) kap[j] = tc->lam[slot_lb(TB, RC, j)] + cc_inst[32 + (1 + j) * NT + tid];
+    for (int j = 0; j < R; ++j) kap[j] = tc->lam[slot_lbr(TB, R, RC, j)] + cc_inst[KQ + (1 + j) * NT + tid];
   }
   // mix masks of the rounds (register slots whose local bit this pass mixes)
   uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
 #pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    if (TB - 5 + j >= pd.mix_lo) mm0 |= 1u << j;
-    if (TB - 10 + j >= pd.mix_lo) mm1 |= 1u << j;
-    if (j >= pd.mix_lo && j < TB - 10) mm2 |= 1u << j;
+  for (int j = 0; j < R; ++j) {
+    if (TB - R + j >= pd.mix_lo) mm0 |= 1u << j;
+    if (TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
+    if (j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
   }
   if (pd.layerA >= 0) {
     const float muA = Ip->mu[pd.layerA];
-    mix_regs(a, muA, mm0);
+    mix_regs_r<R>(a, muA, mm0);
     if constexpr (NR > 1) {
-      transpose<TB, 0, 1>(a, sm, tid);
-      mix_regs(a, muA, mm1);
+      transposer<TB, R, 0, 1>(a, sm, tid);
+      mix_regs_r<R>(a, muA, mm1);
     }
     if constexpr (NR > 2) {
-      transpose<TB, 1, 2>(a, sm, tid);
-      mix_regs(a, muA, mm2);
+      transposer<TB, R, 1, 2>(a, sm, tid);
+      mix_regs_r<R>(a, muA, mm2);
     }
   }
   if (pd.layerP >= 0) {
     int S = A;
     a[0] = cmul(a[0], tab[tix(S + qk[0], W)]);
 #pragma unroll
-    for (int i = 1; i < 32; ++i) {
+    for (int i = 1; i < KQ; ++i) {
       const int k = gray(i), b = gray_bit(i);
       S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
       a[k] = cmul(a[k], tab[tix(S + qk[k], W)]);
@@ -671,20 +695,20 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   if (pd.layerB >= 0) {
     const float muB = Ip->mu[pd.layerB];
     if constexpr (NR > 2) {
-      mix_regs(a, muB, mm2);
-      transpose<TB, 2, 1>(a, sm, tid);
+      mix_regs_r<R>(a, muB, mm2);
+      transposer<TB, R, 2, 1>(a, sm, tid);
     }
     if constexpr (NR > 1) {
-      mix_regs(a, muB, mm1);
-      transpose<TB, 1, 0>(a, sm, tid);
+      mix_regs_r<R>(a, muB, mm1);
+      transposer<TB, R, 1, 0>(a, sm, tid);
     }
-    mix_regs(a, muB, mm0);
+    mix_regs_r<R>(a, muB, mm0);
   }
   if (pd.expect) {
     float acc = 0.f;
     int S = A;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < KQ; ++i) {
       const int k = gray(i);
       if (i > 0) {
         const int b = gray_bit(i);
@@ -697,21 +721,21 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   }
   if (pd.store) {
     if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
-      if constexpr (NR == 3) transpose<TB, 2, 0>(a, sm, tid);
-      if constexpr (NR == 2) transpose<TB, 1, 0>(a, sm, tid);
+      if constexpr (NR == 3) transposer<TB, R, 2, 0>(a, sm, tid);
+      if constexpr (NR == 2) transposer<TB, R, 1, 0>(a, sm, tid);
     }
     if (pd.last) {  // back from the gauge, times lambda_p
       const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zt0));
 #pragma unroll
-      for (int k = 0; k < 32; ++k) a[k] = cmul(a[k], rot_i(fs, -__popc(k)));
+      for (int k = 0; k < KQ; ++k) a[k] = cmul(a[k], rot_i(fs, -__popc(k)));
     }
-    uint32_t e[5];
+    uint32_t e[R];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) e[j] = 1u << qubit_of(TB - 5 + j, c, s);
+    for (int j = 0; j < R; ++j) e[j] = 1u << qubit_of(TB - R + j, c, s);
     uint32_t off = 0;
     base[0] = a[0];
 #pragma unroll
-    for (int i = 1; i < 32; ++i) {
+    for (int i = 1; i < KQ; ++i) {
       const int k = gray(i), b = gray_bit(i);
       off = ((k >> b) & 1) ? off + e[b] : off - e[b];
       base[off] = a[k];
@@ -719,72 +743,87 @@ __global__ void __launch_bounds__(1 << (TB - 5), (TB >= 13 ? 2 : 4))
   }
 }
 
-size_t layer_pass_smem(int tb, int tabcap) {
-  const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - 5));
+size_t layer_pass_smem(int kind, int tabcap) {
+  const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
+  const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - r));
   return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
          16 * sizeof(double);
 }
 
-int64_t cut_consts_elems(int tb, int32_t nlist) { return (int64_t)nlist * cut_consts_stride(tb); }
+int64_t cut_consts_elems(int kind, int32_t nlist) {
+  return (int64_t)nlist * cut_consts_stride(kTileShapes[kind].tb, kTileShapes[kind].r);
+}
 
-cudaError_t launch_cut_consts(int tb, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+static int pass_rounds(int tb, int r, const PassDesc& pd) {
+  return 1 + (pd.mix_lo < tb - r) + (pd.mix_lo < tb - 2 * r);
+}
+
+template <int TB, int R, int RC>
+static cudaError_t launch_cc_t(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                               int32_t* consts, cudaStream_t st) {
+  k_cut_consts<TB, R, RC><<<nlist, 1 << (TB - R), 0, st>>>(pd, n, inst, list, subs, planes, consts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
                               int32_t* consts, cudaStream_t st) {
   if (nlist <= 0 || !(pd.layerP >= 0 || pd.expect)) return cudaSuccess;
-  const int nr = 1 + (pd.mix_lo < tb - 5) + (pd.mix_lo < tb - 10);
-#define PQ_CC(TBV, RCV) \
-  k_cut_consts<TBV, RCV><<<nlist, 1 << (TBV - 5), 0, st>>>(pd, n, inst, list, subs, planes, consts); \
-  return cudaGetLastError()
-  if (tb == 12) {
-    if (nr == 1) { PQ_CC(12, 0); }
-    if (nr == 2) { PQ_CC(12, 1); }
-    PQ_CC(12, 2);
-  }
-  if (tb == 13) {
-    if (nr == 1) { PQ_CC(13, 0); }
-    if (nr == 2) { PQ_CC(13, 1); }
-    PQ_CC(13, 2);
-  }
+  const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
+  const int rc = pass_rounds(tb, r, pd) - 1;
+#define PQ_CC(TBV, RV) \
+  do { \
+    if (tb == TBV && r == RV) { \
+      if (rc == 0) return launch_cc_t<TBV, RV, 0>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      if (rc == 1) return launch_cc_t<TBV, RV, 1>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      return launch_cc_t<TBV, RV, 2>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+    } \
+  } while (0)
+  PQ_CC(12, 5);
+  PQ_CC(12, 4);
+  PQ_CC(13, 5);
 #undef PQ_CC
   return cudaErrorInvalidValue;
 }
 
-template <int TB, int NR>
-static cudaError_t launch_layer_t(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
-                                  int32_t nlist, const SubDev* subs, const uint32_t* planes,
-                                  const float2* tables, float2* states, double* partials,
-                                  int32_t tabcap, int32_t* consts, cudaStream_t st) {
-  const size_t smem = layer_pass_smem(TB, tabcap);
-  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, NR>,
+template <int TB, int R, int NR>
+static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const InstDev* inst,
+                                  const int32_t* list, int32_t nlist, const SubDev* subs,
+                                  const uint32_t* planes, const float2* tables, float2* states,
+                                  double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
+  const size_t smem = layer_pass_smem(kind, tabcap);
+  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, R, NR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles_log2 = n - TB;
   const int64_t blocks = (int64_t)nlist << tiles_log2;
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-  k_layer_pass<TB, NR><<<(unsigned)blocks, 1 << (TB - 5), smem, st>>>(
+  k_layer_pass<TB, R, NR><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
       pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts);
   return cudaGetLastError();
 }
 
-cudaError_t launch_layer_pass(int tb, int n, const PassDesc& pd, const InstDev* inst,
+cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev* inst,
                               const int32_t* list, int32_t nlist, const SubDev* subs,
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
   if (nlist <= 0) return cudaSuccess;
+  if (kind < 0 || kind >= kTileKinds) return cudaErrorInvalidValue;
+  const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
   if (n < tb) return cudaErrorInvalidValue;
-  const int nr = 1 + (pd.mix_lo < tb - 5) + (pd.mix_lo < tb - 10);
-#define PQ_LAUNCH(TBV, NRV) \
-  return launch_layer_t<TBV, NRV>(n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st)
-  if (tb == 12) {
-    if (nr == 1) PQ_LAUNCH(12, 1);
-    if (nr == 2) PQ_LAUNCH(12, 2);
-    PQ_LAUNCH(12, 3);
-  }
-  if (tb == 13) {
-    if (nr == 1) PQ_LAUNCH(13, 1);
-    if (nr == 2) PQ_LAUNCH(13, 2);
-    PQ_LAUNCH(13, 3);
-  }
+  const int nr = pass_rounds(tb, r, pd);
+#define PQ_LAUNCH(TBV, RV) \
+  do { \
+    if (tb == TBV && r == RV) { \
+      if (nr == 1) return launch_layer_t<TBV, RV, 1>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      if (nr == 2) return launch_layer_t<TBV, RV, 2>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      return launch_layer_t<TBV, RV, 3>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+    } \
+  } while (0)
+  PQ_LAUNCH(12, 5);
+  PQ_LAUNCH(12, 4);
+  PQ_LAUNCH(13, 5);
 #undef PQ_LAUNCH
   return cudaErrorInvalidValue;
 }

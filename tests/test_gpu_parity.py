@@ -357,8 +357,8 @@ def test_autotune_choices_keep_parity(api, orc):
     try:
         choice = capi.paraqaoa_autotune(ctx, part, 2)
         for n in sizes:
-            tb, cm = choice[n]
-            assert tb in (12, 13) and cm in (2, 3, 4)
+            tb, rb, cm = choice[n]
+            assert (tb, rb) in ((12, 5), (12, 4), (13, 5)) and cm in (2, 3, 4)
         subs = oracle_parts(orc, g, sizes)
         ids = np.arange(len(sizes), dtype=np.int32)
         gam, bet = synth.random_angles(len(sizes), 2, 99)
