@@ -106,6 +106,9 @@ struct paraqaoa_ctx {
   // low qubits a high-group tile carries (heuristic, or measured by autotune)
   int8_t tile_kind[PARAQAOA_MAX_QUBITS + 1] = {};  // index into kTileShapes
   int8_t c_min[PARAQAOA_MAX_QUBITS + 1] = {};
+  // L2-prefetch distance of the layer passes, in waves of resident CTAs (0: off)
+  int8_t pf_waves[PARAQAOA_MAX_QUBITS + 1] = {};
+  int num_sms = 0;
   // partition on the device
   uint64_t part_serial = 0;
   DevBuf d_subs, d_planes;
@@ -343,7 +346,9 @@ int plan_run(paraqaoa_ctx* c) {
     const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want);
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
     PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * cut_consts_elems(kind, kv.second.second)));
-    for (const PassDesc& pd : sched) {
+    const int pf = c->pf_waves[n] * c->num_sms * layer_resident_per_sm(kind);
+    for (PassDesc pd : sched) {
+      pd.pf = pf;
       if (pd.layerP >= 0 || pd.expect) {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
         PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
@@ -471,6 +476,7 @@ int paraqaoa_create(paraqaoa_ctx** out, int device, size_t hbm_budget) {
     return cuda_rc(e);
   }
   c->stream = c->own;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) c->num_sms = 1;
   if (hbm_budget == 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);

@@ -60,6 +60,7 @@ struct PassDesc {
   int32_t store;    // write the tile back
   int32_t expect;   // reduce sum |psi|^2 C into the tile partial
   int32_t last;     // the final pass (stores apply lambda_p)
+  int32_t pf;       // L2-prefetch the tile this many CTAs ahead (0: off)
 };
 
 // Kernel launchers (sim_kernels.cu). All enqueue on `st` and return the
@@ -80,6 +81,7 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
 int64_t cut_consts_elems(int kind, int32_t nlist);
+int layer_resident_per_sm(int kind);  // occupancy target of a tile shape (CTAs per SM)
 cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
                               int32_t* consts, cudaStream_t st);

@@ -46,14 +46,17 @@ __device__ __forceinline__ void bfly(float2& x, float2& y, float mu) {
   y = ny;
 }
 
-// i^r * (x + i y) for a small integer r (any sign).
+// i^r * (x + i y) for a small integer r (any sign). Selects, not branches:
+// with r known at compile time it folds to a register permutation.
 __device__ __forceinline__ float2 rot_i(float2 a, int r) {
-  switch (r & 3) {
-    case 0: return a;
-    case 1: return make_float2(-a.y, a.x);
-    case 2: return make_float2(-a.x, -a.y);
-    default: return make_float2(a.y, -a.x);
-  }
+  const float2 t = (r & 1) ? make_float2(-a.y, a.x) : a;
+  return (r & 2) ? make_float2(-t.x, -t.y) : t;
+}
+
+// Population count of a register index (< 64), written out so that it folds
+// to a constant inside unrolled loops.
+__host__ __device__ constexpr int popc_c(uint32_t x) {
+  return (int)((x & 1u) + ((x >> 1) & 1u) + ((x >> 2) & 1u) + ((x >> 3) & 1u) + ((x >> 4) & 1u) + ((x >> 5) & 1u));
 }
 
 // C(z) = sum over u with z_u = 1 of the weight of u's neighbours with z_v = 0.
@@ -109,6 +112,12 @@ __device__ __forceinline__ uint32_t lir(uint32_t tid, uint32_t k) {
   }
 }
 
+// Local bit that thread-index bit b occupies in layout RHO (inverse of lir's thread part).
+template <int TB, int R, int RHO>
+__host__ __device__ constexpr int thread_bit_local(int b) {
+  return RHO == 0 ? b : (RHO == 1 ? (b < TB - 2 * R ? b : b + R) : b + R);
+}
+
 __host__ __device__ __forceinline__ int slot_lbr(int TB, int R, int rho, int j) {
   return rho == 0 ? TB - R + j : (rho == 1 ? TB - 2 * R + j : j);
 }
@@ -134,6 +143,22 @@ __device__ __forceinline__ void mix_regs_r(float2 (&a)[1 << R], float mu, uint32
       for (int k = 0; k < (1 << R); ++k)
         if (!((k >> j) & 1)) bfly(a[k], a[k | (1 << j)], mu);
     }
+  }
+}
+
+// Butterflies of one round without data-dependent branches: slots outside
+// `mask` get mu = 0, an exact identity, so every register keeps one fixed
+// home and no copies are needed where paths would join. Slots outside the
+// compile-time set ALLOWED (never mixed in this round) are skipped.
+template <int R, uint32_t ALLOWED>
+__device__ __forceinline__ void mix_regs_sel(float2 (&a)[1 << R], float mu, uint32_t mask) {
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    if (!((ALLOWED >> j) & 1u)) continue;
+    const float m = ((mask >> j) & 1u) ? mu : 0.f;
+#pragma unroll
+    for (int k = 0; k < (1 << R); ++k)
+      if (!((k >> j) & 1)) bfly(a[k], a[k | (1 << j)], m);
   }
 }
 
@@ -575,7 +600,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
                  const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
                  const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
                  float2* __restrict__ states, double* __restrict__ partials, int32_t tabcap,
-                 const int32_t* __restrict__ consts) {
+                 const int32_t* __restrict__ consts, uint32_t mm0, uint32_t mm1, uint32_t mm2) {
   constexpr uint32_t NT = 1u << (TB - R);
   constexpr int KQ = 1 << R;  // registers per thread
   constexpr int RC = NR - 1;  // layout of the cut step (phase / <C>)
@@ -623,25 +648,41 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
     }
     if (tid == 0) tc->cf = cfu;
   }
-  // qubit offsets of the load/store layout: thread part and register bits
-  uint32_t zt0 = 0;
-  for (int lb = 0; lb < TB - R; ++lb)
-    if ((tid >> lb) & 1u) zt0 |= 1u << qubit_of(lb, c, s);
-  float2* base = states + Ip->state_off + (zbase | zt0);
+  // Local index -> qubit offset: local bits [0, c) are qubits [0, c), bits
+  // [c, TB) move up by s - c (a monotone bit map, so it keeps popcounts).
+  const uint32_t lowm = (1u << c) - 1u;
+  const int sh = s - c;
+  auto zmap = [&](uint32_t li) -> uint32_t { return (li & lowm) | ((li & ~lowm) << sh); };
+  // load/store layout: thread bits are local bits [0, TB - R), registers the rest
+  float2* base = states + Ip->state_off + (zbase | zmap(tid));
+
+  // L2 prefetch of the tile pd.pf CTAs ahead (the block scheduler starts CTAs
+  // in index order, so that tile is processed about pd.pf / resident CTA
+  // lifetimes from now): its 2^(TB-c) runs of 2^c contiguous amplitudes.
+  if (pd.pf > 0 && !pd.init) {
+    const uint32_t t2 = blockIdx.x + (uint32_t)pd.pf;
+    if (t2 < gridDim.x) {
+      const uint32_t tile2 = t2 & ((1u << tiles_log2) - 1u);
+      const uint32_t zb2 = ((tile2 & ((1u << lowt) - 1u)) << c) | ((tile2 >> lowt) << (s + g));
+      const float2* p2 = states + inst_all[list[t2 >> tiles_log2]].state_off + zb2;
+      for (uint32_t r = tid; r < (1u << g); r += NT)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p2 + ((size_t)r << s)), "r"(8u << c)
+                     : "memory");
+    }
+  }
 
   float2 a[KQ];
   const uint32_t li0 = lir<TB, R, RC>(tid, 0);
   if (pd.init) {  // s_z = i^popcount(z), z = tile base | thread qubits | register qubits
-    uint32_t zJ = 0;
-    for (int lb = 0; lb < TB; ++lb)
-      if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
-    const float2 b = rot_i(make_float2(1.f, 0.f), __popc(zbase | zJ));
+    const int r = __popc(zbase | zmap(li0));
+    const float sg = (r & 2) ? -1.f : 1.f;
+    const float2 b = (r & 1) ? make_float2(0.f, sg) : make_float2(sg, 0.f);
 #pragma unroll
-    for (int k = 0; k < KQ; ++k) a[k] = rot_i(b, __popc(k));
+    for (int k = 0; k < KQ; ++k) a[k] = rot_i(b, popc_c(k));
   } else {
-    uint32_t e[R];
+    uint32_t e[R];  // qubit offsets of the register slots
 #pragma unroll
-    for (int j = 0; j < R; ++j) e[j] = 1u << qubit_of(TB - R + j, c, s);
+    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (TB - R + j));
     uint32_t off = 0;
     a[0] = base[0];
 #pragma unroll
@@ -657,29 +698,24 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   for (int j = 0; j < R; ++j) kap[j] = 0;
   if (need_cut) {
     A = tc->cf + cc_inst[KQ + tid];
-    for (int lb = 0; lb < TB; ++lb)
-      if ((li0 >> lb) & 1u) A += tc->lam[lb];
+#pragma unroll
+    for (int b = 0; b < TB - R; ++b) A += ((tid >> b) & 1u) ? tc->lam[thread_bit_local<TB, R, RC>(b)] : 0;
 #pragma unroll
     for (int j = 0; j < R; ++j) kap[j] = tc->lam[slot_lbr(TB, R, RC, j)] + cc_inst[KQ + (1 + j) * NT + tid];
   }
-  // mix masks of the rounds (register slots whose local bit this pass mixes)
-  uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
-#pragma unroll
-  for (int j = 0; j < R; ++j) {
-    if (TB - R + j >= pd.mix_lo) mm0 |= 1u << j;
-    if (TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
-    if (j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
-  }
+  // round 2 (layout 2) only ever mixes slots below TB - 2R (the others repeat layout 1's)
+  constexpr uint32_t kAll = (1u << R) - 1u;
+  constexpr uint32_t kLow2 = (TB - 2 * R) >= R ? kAll : ((1u << (TB - 2 * R > 0 ? TB - 2 * R : 0)) - 1u);
   if (pd.layerA >= 0) {
     const float muA = Ip->mu[pd.layerA];
-    mix_regs_r<R>(a, muA, mm0);
+    mix_regs_sel<R, kAll>(a, muA, mm0);
     if constexpr (NR > 1) {
       transposer<TB, R, 0, 1>(a, sm, tid);
-      mix_regs_r<R>(a, muA, mm1);
+      mix_regs_sel<R, kAll>(a, muA, mm1);
     }
     if constexpr (NR > 2) {
       transposer<TB, R, 1, 2>(a, sm, tid);
-      mix_regs_r<R>(a, muA, mm2);
+      mix_regs_sel<R, kLow2>(a, muA, mm2);
     }
   }
   if (pd.layerP >= 0) {
@@ -695,14 +731,14 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   if (pd.layerB >= 0) {
     const float muB = Ip->mu[pd.layerB];
     if constexpr (NR > 2) {
-      mix_regs_r<R>(a, muB, mm2);
+      mix_regs_sel<R, kLow2>(a, muB, mm2);
       transposer<TB, R, 2, 1>(a, sm, tid);
     }
     if constexpr (NR > 1) {
-      mix_regs_r<R>(a, muB, mm1);
+      mix_regs_sel<R, kAll>(a, muB, mm1);
       transposer<TB, R, 1, 0>(a, sm, tid);
     }
-    mix_regs_r<R>(a, muB, mm0);
+    mix_regs_sel<R, kAll>(a, muB, mm0);
   }
   if (pd.expect) {
     float acc = 0.f;
@@ -725,13 +761,13 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
       if constexpr (NR == 2) transposer<TB, R, 1, 0>(a, sm, tid);
     }
     if (pd.last) {  // back from the gauge, times lambda_p
-      const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zt0));
+      const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zmap(tid)));
 #pragma unroll
-      for (int k = 0; k < KQ; ++k) a[k] = cmul(a[k], rot_i(fs, -__popc(k)));
+      for (int k = 0; k < KQ; ++k) a[k] = cmul(a[k], rot_i(fs, -popc_c(k)));
     }
     uint32_t e[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) e[j] = 1u << qubit_of(TB - R + j, c, s);
+    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (TB - R + j));
     uint32_t off = 0;
     base[0] = a[0];
 #pragma unroll
@@ -749,6 +785,8 @@ size_t layer_pass_smem(int kind, int tabcap) {
   return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
          16 * sizeof(double);
 }
+
+int layer_resident_per_sm(int kind) { return layer_min_blocks(kTileShapes[kind].tb, kTileShapes[kind].r); }
 
 int64_t cut_consts_elems(int kind, int32_t nlist) {
   return (int64_t)nlist * cut_consts_stride(kTileShapes[kind].tb, kTileShapes[kind].r);
@@ -799,8 +837,15 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
   const int tiles_log2 = n - TB;
   const int64_t blocks = (int64_t)nlist << tiles_log2;
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  // register slots each round mixes (mm0: layout 0, mm1: layout 1, mm2: layout 2)
+  uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
+  for (int j = 0; j < R; ++j) {
+    if (TB - R + j >= pd.mix_lo) mm0 |= 1u << j;
+    if (TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
+    if (j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
+  }
   k_layer_pass<TB, R, NR><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
-      pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts);
+      pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts, mm0, mm1, mm2);
   return cudaGetLastError();
 }
 
