@@ -591,8 +591,10 @@ __global__ void __launch_bounds__(1 << (TB - R))
   }
 }
 
-// Occupancy target of a tile shape: resident CTAs per SM the register file allows.
-__host__ __device__ constexpr int layer_min_blocks(int tb, int r) { return r == 4 ? 3 : (tb >= 13 ? 2 : 4); }
+// Occupancy target of a tile shape: resident CTAs per SM the register file
+// allows (the 16-register shape fits 64 registers per thread without spills,
+// four CTAs of 256 threads).
+__host__ __device__ constexpr int layer_min_blocks(int tb, int r) { return r == 4 ? 4 : (tb >= 13 ? 2 : 4); }
 
 template <int TB, int R, int NR>
 __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
