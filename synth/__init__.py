@@ -164,3 +164,62 @@ def random_angles(count: int, p: int, seed: int) -> tuple[np.ndarray, np.ndarray
     u = draws_unit(key, 0, 2 * count * p).reshape(2, count, p)
     return u[0] * np.pi, (u[1] - 0.5) * (np.pi / 2)
 
+
+
+MLP_STREAM = 0x4d4c5049  # "MLPI"
+ORDER_STREAM = 0x4f524452  # "ORDR"
+GRAPHS_STREAM = 0x47525048  # "GRPH"
+
+
+def mlp_init(p: int, seed: int, fan=((64, 256), (256, 256), (256, None))) -> np.ndarray:
+    """Initial parameters of the 64 -> 256 -> 256 -> 2p angle network, flat in
+    storage order (W1, b1, W2, b2, W3, b3; W as in x out, row-major): weights
+    uniform in +-sqrt(6 / (in + out)) (Glorot and Bengio, 2010), biases 0.
+    Values are rounded to float32 so every consumer starts from the same numbers."""
+    key = stream_key(seed, MLP_STREAM)
+    out, m = [], 0
+    for fi, fo in fan:
+        fo = 2 * p if fo is None else fo
+        a = np.sqrt(6.0 / (fi + fo))
+        u = draws_unit(key, m, fi * fo)
+        m += fi * fo
+        out.append(((2.0 * u - 1.0) * a).astype(np.float32))
+        out.append(np.zeros(fo, np.float32))
+    return np.concatenate(out).astype(np.float32)
+
+
+def epoch_orders(rows: int, epochs: int, seed: int) -> np.ndarray:
+    """One permutation of range(rows) per epoch (sort keys drawn per row)."""
+    key = stream_key(seed, ORDER_STREAM)
+    d = draws_u64(key, 0, rows * epochs).reshape(epochs, rows)
+    return np.argsort(d, axis=1, kind="stable").astype(np.int32)
+
+
+def graph_specs(count: int, n_lo: int, n_hi: int, p_lo: float, p_hi: float, seed: int):
+    """Per random subgraph: (n, edge probability, graph seed), n uniform in
+    {n_lo..n_hi}, probability uniform in [p_lo, p_hi); graph seeds are
+    seed * 1_000_003 + index."""
+    key = stream_key(seed, GRAPHS_STREAM)
+    d = draws_u64(key, 0, 2 * count).reshape(2, count)
+    ns = n_lo + (d[0] % np.uint64(n_hi - n_lo + 1)).astype(np.int64)
+    ps = p_lo + (d[1] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53) * (p_hi - p_lo)
+    return [(int(n), float(pe), int(seed) * 1_000_003 + i) for i, (n, pe) in enumerate(zip(ns, ps))]
+
+
+def chain_of_graphs(specs, wmax: int = 10):
+    """Place independent G(n, P) graphs on a chain of vertex ranges that
+    overlap in one vertex, [o_i, o_i + n_i) with o_{i+1} = o_i + n_i - 1, so
+    that the SIZES partition with sizes n_i recovers graph i as part i
+    (no edge of graph i+1 has both ends in part i and vice versa).
+    Returns (whole graph, sizes)."""
+    us, vs, ws, sizes = [], [], [], []
+    o = 0
+    for n, pe, s in specs:
+        g = erdos_renyi(n, pe, s, wmax=wmax)
+        us.append(g.eu.astype(np.int64) + o)
+        vs.append(g.ev.astype(np.int64) + o)
+        ws.append(g.ew.astype(np.int64))
+        sizes.append(n)
+        o += n - 1
+    total = o + 1
+    return Graph(total, np.concatenate(us), np.concatenate(vs), np.concatenate(ws)), np.asarray(sizes, np.int32)
