@@ -201,6 +201,89 @@ int paraqaoa_optimize(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_
 int paraqaoa_topk_noalloc(const float *state_dev, int32_t n, int32_t K, uint32_t flags,
                           uint32_t *out_z_dev, float *out_p_dev, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned angles. The paper leaves the classical optimiser's starting angles
+ * open and notes that initialisation matters (Sec. 2.2). The plain form
+ * below is the optimiser this library uses (p = 1 grid, fixed-iteration
+ * Adam, INTERP to deeper circuits); the learned form predicts its angles
+ * with a 64 -> 256 -> 256 -> 2p network from subgraph features, judges each
+ * prediction by <C> and sends the rejected subgraphs to the plain form.
+ * Network arithmetic: matrix products take BF16 operands (round to nearest
+ * even) and accumulate in FP32; biases, ReLU masks, the loss and Adam are
+ * FP32 on FP32 master weights.
+ * ------------------------------------------------------------------------- */
+
+#define PARAQAOA_FEATURES 64
+
+/* The 64 features of each part in ids (count x 64 floats, row-major):
+ * [0] n/32, [1] edge density, [2]/[3] mean/std edge weight over 16,
+ * [4..8) mean/std/max/min degree over n, [8..24) degree histogram (bin
+ * min(deg, 15)) over n, [24..40) weight histogram (bin min(w, 16) - 1) over
+ * |E|, [40..56) weighted-degree histogram (bin min(15, floor(16 D / (max D +
+ * 1)))) over n, [56] triangles / C(n,3), [57] total weight / (10 C(n,2)),
+ * [58..64) zero. Parts must have at most 32 vertices. Synchronises. */
+int paraqaoa_features(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count,
+                      float *out_host);
+
+/* Plain form of the angle search for depth p: the p = 1 grid search
+ * (16 x 16 points), `steps` Adam steps (lr 0.02, central differences h =
+ * 1e-3), then for d = 2..p INTERP (Zhou et al., PRX 10, 021067, 2020) from
+ * depth d-1 and `steps` Adam steps at depth d. gamma_out / beta_out receive
+ * count x p angles folded into the fundamental domain (gamma_0 in [0, pi],
+ * other gammas in (-pi, pi], betas in (-pi/4, pi/4]; (gamma, beta) ->
+ * (-gamma, -beta), gamma period 2 pi and beta period pi/2 leave <C>
+ * unchanged), value_out (optional) <C> there. steps = 0 skips Adam. */
+int paraqaoa_solve_plain(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count,
+                         int32_t p, int32_t steps, double *gamma_out, double *beta_out, double *value_out);
+
+typedef struct paraqaoa_mlp paraqaoa_mlp;
+
+/* Number of FP32 parameters of the depth-p network: W1[64 x 256], b1[256],
+ * W2[256 x 256], b2[256], W3[256 x 2p], b3[2p] in this order (W stored in x
+ * out, row-major). 0 for an invalid p. */
+int64_t paraqaoa_mlp_param_count(int32_t p);
+
+/* Create a depth-p angle network on ctx's device from init_params
+ * (paraqaoa_mlp_param_count(p) floats, host, copied). The network's outputs
+ * are [gamma_0..gamma_{p-1} | beta_0..beta_{p-1}]. Free with paraqaoa_mlp_free. */
+int paraqaoa_mlp_create(paraqaoa_ctx *ctx, int32_t p, const float *init_params, paraqaoa_mlp **out);
+void paraqaoa_mlp_free(paraqaoa_mlp *mlp);
+
+/* Current FP32 master parameters (param_count floats). Synchronises. */
+int paraqaoa_mlp_get_params(paraqaoa_mlp *mlp, float *out_host);
+
+/* Loss L = sum (Y - T)^2 / (rows * 2p) over the rows of X (rows x 64) and
+ * targets T (rows x 2p), and its gradient (param_count floats) at the
+ * current parameters, without updating them. Synchronises. */
+int paraqaoa_mlp_grad(paraqaoa_mlp *mlp, const float *X, const float *T, int32_t rows, float *grad_out,
+                      double *loss_out);
+
+/* Minibatch Adam (Kingma and Ba, 2015; beta1 0.9, beta2 0.999, eps 1e-8,
+ * learning rate lr) on the MSE loss. Epoch e visits rows order[e*rows ..
+ * (e+1)*rows) (each a permutation of 0..rows-1) in consecutive slices of
+ * `batch` rows; epoch_loss (optional, `epochs` entries) receives the mean
+ * minibatch loss of each epoch. Afterwards the judge's reference angles are
+ * the column means of T (the best constant predictor). Synchronises. */
+int paraqaoa_mlp_train(paraqaoa_mlp *mlp, const float *X, const float *T, int32_t rows, int32_t epochs,
+                       int32_t batch, double lr, const int32_t *order, double *epoch_loss);
+
+/* Predicted angles for the rows of X (rows x 64): gamma / beta rows x p. */
+int paraqaoa_mlp_predict(paraqaoa_mlp *mlp, const float *X, int32_t rows, double *gamma, double *beta);
+
+/* The judge's reference angles (p entries each). */
+int paraqaoa_mlp_reference(paraqaoa_mlp *mlp, double *gamma_out, double *beta_out);
+
+/* Learned form of the angle search at the network's depth p: features,
+ * prediction, then one batch that evaluates <C> at the prediction and at the
+ * reference angles. A prediction is kept when its <C> is at least the
+ * reference's; the other parts go to paraqaoa_solve_plain(fallback_steps)
+ * and fallback_out[i] (optional) is set to 1 for them. gamma_out / beta_out
+ * receive count x p angles, value_out (optional) <C> there. The network must
+ * belong to ctx. */
+int paraqaoa_solve_learned(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count,
+                           paraqaoa_mlp *mlp, int32_t fallback_steps, double *gamma_out, double *beta_out,
+                           double *value_out, int32_t *fallback_out);
+
 /* Autotuner for the HBM-streaming layer passes (no counterpart in the paper,
  * which runs a fixed solver per subgraph). For every qubit count n >= 15
  * present in `part`, times the candidate tile shapes (2^12 amplitudes per CTA

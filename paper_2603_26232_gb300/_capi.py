@@ -65,6 +65,18 @@ _SIGS = {
     "paraqaoa_profile_read": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "paraqaoa_topk_noalloc": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, P, P, P], ctypes.c_int),
+    "paraqaoa_features": ([P, P, P, ctypes.c_int32, P], ctypes.c_int),
+    "paraqaoa_solve_plain": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "paraqaoa_mlp_param_count": ([ctypes.c_int32], ctypes.c_int64),
+    "paraqaoa_mlp_create": ([P, ctypes.c_int32, P, ctypes.POINTER(P)], ctypes.c_int),
+    "paraqaoa_mlp_free": ([P], None),
+    "paraqaoa_mlp_get_params": ([P, P], ctypes.c_int),
+    "paraqaoa_mlp_grad": ([P, P, P, ctypes.c_int32, P, P], ctypes.c_int),
+    "paraqaoa_mlp_train": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P, P],
+                           ctypes.c_int),
+    "paraqaoa_mlp_predict": ([P, P, ctypes.c_int32, P, P], ctypes.c_int),
+    "paraqaoa_mlp_reference": ([P, P, P], ctypes.c_int),
+    "paraqaoa_solve_learned": ([P, P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
 }
 
 
@@ -269,3 +281,93 @@ def paraqaoa_topk_noalloc(state_dev_ptr: int, n: int, K: int, out_z_dev_ptr: int
     are raw device addresses (e.g. tensor.data_ptr()). Enqueues only."""
     _check(load().paraqaoa_topk_noalloc(state_dev_ptr, int(n), int(K), int(flags), out_z_dev_ptr,
                                         out_p_dev_ptr, stream_handle), "paraqaoa_topk_noalloc")
+
+
+# ---------------------------------------------------------------- learned angles
+FEATURES = 64
+
+
+def paraqaoa_features(ctx, part, ids) -> np.ndarray:
+    ids = _arr(ids, np.int32)
+    out = np.zeros((ids.size, FEATURES), np.float32)
+    _check(load().paraqaoa_features(ctx, part, _ptr(ids), ids.size, _ptr(out)), "paraqaoa_features")
+    return out
+
+
+def paraqaoa_solve_plain(ctx, part, ids, p: int, steps: int = 32):
+    ids = _arr(ids, np.int32)
+    g = np.zeros((ids.size, p))
+    b = np.zeros((ids.size, p))
+    v = np.zeros(ids.size)
+    _check(load().paraqaoa_solve_plain(ctx, part, _ptr(ids), ids.size, p, steps, _ptr(g), _ptr(b), _ptr(v)),
+           "paraqaoa_solve_plain")
+    return g, b, v
+
+
+def paraqaoa_mlp_param_count(p: int) -> int:
+    return int(load().paraqaoa_mlp_param_count(p))
+
+
+def paraqaoa_mlp_create(ctx, p: int, init_params):
+    w = _arr(init_params, np.float32)
+    if w.size != paraqaoa_mlp_param_count(p):
+        raise ValueError("init_params has the wrong size")
+    out = P()
+    _check(load().paraqaoa_mlp_create(ctx, p, _ptr(w), ctypes.byref(out)), "paraqaoa_mlp_create")
+    return out
+
+
+def paraqaoa_mlp_free(mlp):
+    load().paraqaoa_mlp_free(mlp)
+
+
+def paraqaoa_mlp_get_params(mlp, p: int) -> np.ndarray:
+    out = np.zeros(paraqaoa_mlp_param_count(p), np.float32)
+    _check(load().paraqaoa_mlp_get_params(mlp, _ptr(out)), "paraqaoa_mlp_get_params")
+    return out
+
+
+def paraqaoa_mlp_grad(mlp, p: int, X, T):
+    X = _arr(X, np.float32)
+    T = _arr(T, np.float32)
+    g = np.zeros(paraqaoa_mlp_param_count(p), np.float32)
+    loss = ctypes.c_double(0.0)
+    _check(load().paraqaoa_mlp_grad(mlp, _ptr(X), _ptr(T), X.shape[0], _ptr(g), ctypes.byref(loss)),
+           "paraqaoa_mlp_grad")
+    return g, loss.value
+
+
+def paraqaoa_mlp_train(mlp, X, T, epochs: int, batch: int, lr: float, order):
+    X = _arr(X, np.float32)
+    T = _arr(T, np.float32)
+    order = _arr(order, np.int32)
+    losses = np.zeros(epochs)
+    _check(load().paraqaoa_mlp_train(mlp, _ptr(X), _ptr(T), X.shape[0], epochs, batch, lr, _ptr(order),
+                                     _ptr(losses)), "paraqaoa_mlp_train")
+    return losses
+
+
+def paraqaoa_mlp_predict(mlp, p: int, X):
+    X = _arr(X, np.float32)
+    g = np.zeros((X.shape[0], p))
+    b = np.zeros((X.shape[0], p))
+    _check(load().paraqaoa_mlp_predict(mlp, _ptr(X), X.shape[0], _ptr(g), _ptr(b)), "paraqaoa_mlp_predict")
+    return g, b
+
+
+def paraqaoa_mlp_reference(mlp, p: int):
+    g = np.zeros(p)
+    b = np.zeros(p)
+    _check(load().paraqaoa_mlp_reference(mlp, _ptr(g), _ptr(b)), "paraqaoa_mlp_reference")
+    return g, b
+
+
+def paraqaoa_solve_learned(ctx, part, ids, mlp, p: int, fallback_steps: int = 32):
+    ids = _arr(ids, np.int32)
+    g = np.zeros((ids.size, p))
+    b = np.zeros((ids.size, p))
+    v = np.zeros(ids.size)
+    fb = np.zeros(ids.size, np.int32)
+    _check(load().paraqaoa_solve_learned(ctx, part, _ptr(ids), ids.size, mlp, fallback_steps, _ptr(g), _ptr(b),
+                                         _ptr(v), _ptr(fb)), "paraqaoa_solve_learned")
+    return g, b, v, fb

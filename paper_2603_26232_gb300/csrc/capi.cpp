@@ -373,6 +373,16 @@ int plan_run(paraqaoa_ctx* c) {
 
 namespace pq {
 
+cudaStream_t ctx_stream(paraqaoa_ctx* c) { return c->stream; }
+int ctx_device(paraqaoa_ctx* c) { return c->device; }
+int ctx_part_device(paraqaoa_ctx* c, const paraqaoa_part* pt, const SubDev** subs, const uint32_t** planes) {
+  int rc = upload_part(c, pt, false);
+  if (rc) return rc;
+  *subs = c->d_subs.as<SubDev>();
+  *planes = c->d_planes.as<uint32_t>();
+  return PARAQAOA_OK;
+}
+
 // p layers over G qubit groups: group 0 = qubits [0, tb) (a tile is 2^tb
 // consecutive amplitudes), groups 1.. split qubits [tb, n) evenly, each tile
 // carrying the lowest tb - g qubits (>= c_min) so that HBM accesses stay in

@@ -134,6 +134,31 @@ cudaError_t launch_adam_update(const double* expect, const double* wsum, int32_t
 cudaError_t launch_theta_split(const double* theta, int32_t S, int32_t p, double* gamma,
                                double* beta, cudaStream_t st);
 
+// Learned angles (mlp_kernels.cu). Operands __nv_bfloat16 are passed as
+// uint16_t storage so that host translation units need no CUDA BF16 header.
+constexpr int kFeatures = 64;
+constexpr int kHidden = 256;
+typedef uint16_t bf16_t;
+cudaError_t launch_features(const SubDev* subs, const uint32_t* planes, const int32_t* ids, int32_t count,
+                            float* out, cudaStream_t st);
+cudaError_t launch_gemm_bf16_raw(bool ta, bool tb, int M, int N, int K, const bf16_t* A, int lda, const bf16_t* B,
+                                 int ldb, float* C, int ldc, const float* bias, int relu, bf16_t* Cb, cudaStream_t st);
+cudaError_t launch_to_bf16_raw(const float* x, bf16_t* y, int64_t n, cudaStream_t st);
+cudaError_t launch_gather_rows_raw(const float* X, int cols, const float* T, int tcols, const int32_t* idx, int rows,
+                                   bf16_t* Xb, float* Tb, cudaStream_t st);
+cudaError_t launch_mse_grad_raw(const float* Y, const float* T, int64_t n, float* dY, bf16_t* dYb, double* loss,
+                                cudaStream_t st);
+cudaError_t launch_relu_back_raw(float* dH, const float* Z, int64_t n, bf16_t* dZb, cudaStream_t st);
+cudaError_t launch_colsum(const float* dZ, int rows, int cols, float* db, cudaStream_t st);
+cudaError_t launch_adam_raw(float* w, const float* g, float* m, float* v, int64_t n, float lr, int t, bf16_t* wb,
+                            cudaStream_t st);
+cudaError_t launch_split_angles(const float* Y, int rows, int p, double* gamma, double* beta, cudaStream_t st);
+
+// Context internals the learned-angle entry points share (capi.cpp).
+cudaStream_t ctx_stream(paraqaoa_ctx* c);
+int ctx_device(paraqaoa_ctx* c);
+int ctx_part_device(paraqaoa_ctx* c, const paraqaoa_part* pt, const SubDev** subs, const uint32_t** planes);
+
 // Pass schedule for an n-qubit instance group (layer_pass.cu host helper).
 std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect);
 int schedule_groups(int n, int tb, int c_min);

@@ -1,0 +1,223 @@
+"""GPU parity of the learned-angle path (features, BF16 network, Adam, judge)
+against the FP64 oracle of oracle/mlp.py, called through the C ABI.
+
+Tolerances. Features: 1e-6 absolute (FP32 divisions of exact integer
+counts). Network: the oracle rounds the same operands to BF16, so the sides
+differ by FP32 versus FP64 accumulation (relative ~1e-6) and by rare one-ulp
+BF16 rounding differences (2^-8 relative on single elements); gradients must
+agree to 1e-2 of each tensor's largest entry and 3e-3 in relative L2 norm,
+the loss to 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import paper_2603_26232_gb300 as pkg
+    pkg.build()
+    from paper_2603_26232_gb300 import _capi
+    ctx = _capi.paraqaoa_create(0)
+    yield _capi, ctx
+    _capi.paraqaoa_destroy(ctx)
+
+
+def _chain(specs, wmax=10):
+    G, sizes = synth.chain_of_graphs(specs, wmax=wmax)
+    return G, sizes
+
+
+def test_features_match_oracle(api, orc):
+    capi, ctx = api
+    specs = synth.graph_specs(40, 2, 26, 0.0, 0.9, 4) + [(30, 0.3, 77), (32, 0.5, 78), (3, 1.0, 79)]
+    for wmax in (1, 10):
+        G, sizes = _chain(specs, wmax)
+        part = capi.paraqaoa_partition(capi.Graph.of(G), len(sizes), capi.PART_SIZES, sizes)
+        try:
+            ids = np.arange(len(sizes), dtype=np.int32)
+            ours = capi.paraqaoa_features(ctx, part, ids)
+            subs = orc.subgraphs(G, len(sizes), 2, sizes)
+            for i, s in enumerate(subs):
+                ref = omlp.features(s.n, s.eu, s.ev, s.ew)
+                np.testing.assert_allclose(ours[i], ref, rtol=0, atol=1e-6, err_msg=f"part {i} n={s.n}")
+        finally:
+            capi.paraqaoa_part_free(part)
+
+
+def _params(p, seed):
+    w = synth.mlp_init(p, seed).astype(np.float64)
+    d = omlp.unpack(w, p)
+    rng = np.random.default_rng(seed)
+    for k in ("b1", "b2", "b3"):
+        d[k] = rng.normal(0, 0.05, d[k].shape)
+    return omlp.pack(d, p).astype(np.float32).astype(np.float64)
+
+
+def _data(rows, p, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, (rows, omlp.F)).astype(np.float32)
+    T = rng.normal(0, 1, (rows, 2 * p)).astype(np.float32)
+    return X, T
+
+
+def _close_tensors(g_gpu, g_ref, p):
+    o = 0
+    for name, shp in omlp.param_shapes(p):
+        k = int(np.prod(shp))
+        a, b = g_gpu[o:o + k].astype(np.float64), g_ref[o:o + k]
+        scale = max(np.abs(b).max(), 1e-30)
+        assert np.abs(a - b).max() <= 1e-2 * scale, (name, np.abs(a - b).max(), scale)
+        assert np.linalg.norm(a - b) <= 3e-3 * max(np.linalg.norm(b), 1e-30), name
+        o += k
+
+
+@pytest.mark.parametrize("p,rows", [(1, 1), (2, 300), (3, 777)])
+def test_gradient_matches_oracle(api, p, rows):
+    capi, ctx = api
+    w = _params(p, 10 + p)
+    X, T = _data(rows, p, 20 + p)
+    net = capi.paraqaoa_mlp_create(ctx, p, w.astype(np.float32))
+    try:
+        g, loss = capi.paraqaoa_mlp_grad(net, p, X, T)
+    finally:
+        capi.paraqaoa_mlp_free(net)
+    L, gd = omlp.loss_and_grad(omlp.unpack(w, p), X.astype(np.float64), T.astype(np.float64), bf=True)
+    assert abs(loss - L) <= 1e-5 * L
+    _close_tensors(g, omlp.pack(gd, p), p)
+
+
+def test_training_and_prediction_match_oracle(api):
+    capi, ctx = api
+    p, rows, epochs, batch, lr = 2, 200, 3, 48, 1e-3
+    w = _params(p, 31)
+    X, T = _data(rows, p, 32)
+    order = synth.epoch_orders(rows, epochs, 5)
+    net = capi.paraqaoa_mlp_create(ctx, p, w.astype(np.float32))
+    try:
+        losses = capi.paraqaoa_mlp_train(net, X, T, epochs, batch, lr, order)
+        w_gpu = capi.paraqaoa_mlp_get_params(net, p).astype(np.float64)
+        gp, bp = capi.paraqaoa_mlp_predict(net, p, X[:50])
+        rg, rb = capi.paraqaoa_mlp_reference(net, p)
+    finally:
+        capi.paraqaoa_mlp_free(net)
+    w_ref, l_ref = omlp.train(w, p, X.astype(np.float64), T.astype(np.float64), order, batch, lr, bf=True)
+    np.testing.assert_allclose(losses, l_ref, rtol=1e-3)
+    steps = epochs * ((rows + batch - 1) // batch)
+    # Adam moves each weight by at most ~lr per step whatever the gradient's
+    # size, so weights whose gradients sit at the rounding-noise level can
+    # drift apart by O(lr) per step; the bulk of the movement must agree
+    assert np.abs(w_gpu - w_ref).max() <= 2 * lr * steps
+    assert np.linalg.norm(w_gpu - w_ref) <= 5e-2 * np.linalg.norm(w_ref - w)
+    # prediction at the GPU's trained weights: same BF16 model in the oracle
+    og, ob = omlp.predict(w_gpu, p, X[:50].astype(np.float64), bf=True)
+    scale = max(np.abs(og).max(), np.abs(ob).max())
+    assert np.abs(gp - og).max() <= 1e-2 * scale and np.abs(bp - ob).max() <= 1e-2 * scale
+    np.testing.assert_allclose(np.concatenate([rg, rb]), T.astype(np.float64).mean(axis=0), rtol=1e-12, atol=1e-12)
+
+
+def test_solve_plain_matches_oracle_optimiser(api, orc):
+    capi, ctx = api
+    specs = synth.graph_specs(6, 6, 11, 0.2, 0.6, 8)
+    G, sizes = _chain(specs)
+    part = capi.paraqaoa_partition(capi.Graph.of(G), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        ids = np.arange(len(sizes), dtype=np.int32)
+        g, b, v = capi.paraqaoa_solve_plain(ctx, part, ids, 2, steps=8)
+        # the plain form's first stage on its own (deterministic)
+        g0, b0, best0, _ = capi.paraqaoa_grid_search(ctx, part, ids)
+    finally:
+        capi.paraqaoa_part_free(part)
+    subs = orc.subgraphs(G, len(sizes), 2, sizes)
+    batch = orc.Batch(subs)
+    W = np.array([s.total_weight for s in subs], float)
+    # the oracle's <C> at the GPU's final angles equals the GPU's value
+    ex = orc.expect_batch(batch, ids, g, b)
+    assert np.all(np.abs(ex - v) <= 1e-5 * W)
+    # the angles are folded into the fundamental domain
+    assert np.all((g[:, 0] >= 0) & (g[:, 0] <= np.pi)) and np.all(np.abs(b) <= np.pi / 4 + 1e-12)
+    # the grid stage reaches the oracle's grid maximum (near-ties may pick
+    # another point of the same value)
+    vals, arg, _, _ = orc.grid_search(batch)
+    assert np.all(np.abs(best0 - vals.max(axis=1)) <= 1e-5 * W)
+    # the oracle's Adam -> INTERP -> Adam from the same grid point. Near an
+    # optimum Adam divides the gradient by its own running magnitude, so the
+    # GPU's FP32 central differences (noise ~1e-4 of W / W per unit angle at
+    # h = 1e-3) make it jitter by up to ~lr = 0.02 in angle; on these small
+    # parts that costs up to ~2e-3 W against the oracle's FP64 trajectory
+    cfg = orc.AdamConfig(steps=8)
+    g1, b1, _ = orc.adam_optimize(batch, g0[:, None], b0[:, None], cfg)
+    g2, b2 = orc.interp(g1, b1)
+    g2, b2, f2 = orc.adam_optimize(batch, g2, b2, cfg)
+    assert np.all(v >= f2 - 5e-3 * W)
+
+
+def _workload(capi, count, seed, wmax):
+    specs = synth.graph_specs(count, 8, 14, 0.05, 0.5, seed)
+    G, sizes = synth.chain_of_graphs(specs, wmax=wmax)
+    part = capi.paraqaoa_partition(capi.Graph.of(G), len(sizes), capi.PART_SIZES, sizes)
+    return G, sizes, part, np.arange(len(sizes), dtype=np.int32)
+
+
+def test_learned_angles_gain_over_plain_and_constant(api, orc):
+    """Unit-weight random subgraphs (n 8..14, edge probability 0.05..0.5):
+    labels from the plain form, a p = 1 network trained on the GPU, and on
+    held-out subgraphs the learned form against (a) the plain form, (b) the
+    best constant prediction (mean label) and (c) the untrained network."""
+    capi, ctx = api
+    p, ntr, nte, epochs, steps = 1, 2048, 256, 100, 32
+    _, _, ptr, itr = _workload(capi, ntr, 1, 1)
+    Gte, sizes_te, pte, ite = _workload(capi, nte, 100000, 1)
+    nets = []
+    try:
+        gl, bl, _ = capi.paraqaoa_solve_plain(ctx, ptr, itr, p, steps)
+        Xtr = capi.paraqaoa_features(ctx, ptr, itr)
+        Xte = capi.paraqaoa_features(ctx, pte, ite)
+        T = np.concatenate([gl, bl], axis=1).astype(np.float32)
+        untrained = capi.paraqaoa_mlp_create(ctx, p, synth.mlp_init(p, 0))
+        net = capi.paraqaoa_mlp_create(ctx, p, synth.mlp_init(p, 0))
+        nets = [untrained, net]
+        losses = capi.paraqaoa_mlp_train(net, Xtr, T, epochs, 128, 1e-3, synth.epoch_orders(ntr, epochs, 1))
+        assert losses[-1] < 0.1 * losses[0]
+        gp, bp, vp = capi.paraqaoa_solve_plain(ctx, pte, ite, p, steps)
+        gq, bq, vq, fb = capi.paraqaoa_solve_learned(ctx, pte, ite, net, p, steps)
+
+        def value_at(g, b):
+            capi.paraqaoa_simulate_batch(ctx, pte, ite, p, g, b)
+            return capi.paraqaoa_expect(ctx, nte)
+
+        g0, b0 = capi.paraqaoa_mlp_predict(net, p, Xte)
+        v_pred = value_at(g0, b0)
+        rg, rb = capi.paraqaoa_mlp_reference(net, p)
+        v_ref = value_at(np.tile(rg, (nte, 1)), np.tile(rb, (nte, 1)))
+        gu, bu = capi.paraqaoa_mlp_predict(untrained, p, Xte)
+        v_untrained = value_at(gu, bu)
+    finally:
+        for q in nets:
+            capi.paraqaoa_mlp_free(q)
+        capi.paraqaoa_part_free(ptr)
+        capi.paraqaoa_part_free(pte)
+    m = vp > 0
+    ratio = lambda v: v[m].sum() / vp[m].sum()
+    assert ratio(vq) >= 0.99                       # within 1% of the plain form
+    assert ratio(v_pred) >= ratio(v_ref) + 0.01    # beats the best constant guess
+    assert ratio(v_pred) >= ratio(v_untrained) + 0.05
+    # circuit evaluations: plain = 256 grid points + steps x (4p + ...) ; learned = 2 + fallbacks
+    plain_evals = 256 + steps * 4 * p + 1
+    learned_evals = 2 + fb.mean() * plain_evals
+    assert plain_evals / learned_evals >= 10
+    # the judge: a prediction is kept exactly when the oracle's <C> there is at
+    # least the oracle's <C> at the reference angles (up to the 1e-5 W tolerance)
+    subs = orc.subgraphs(Gte, len(sizes_te), 2, sizes_te)
+    batch = orc.Batch(subs)
+    W = np.array([max(s.total_weight, 1) for s in subs], float)
+    o_pred = orc.expect_batch(batch, ite, g0, b0)
+    o_ref = orc.expect_batch(batch, ite, np.tile(rg, (nte, 1)), np.tile(rb, (nte, 1)))
+    decided = np.abs(o_pred - o_ref) > 1e-5 * W
+    assert np.array_equal(fb[decided] == 0, (o_pred >= o_ref)[decided])
+    kept = fb == 0
+    np.testing.assert_allclose(gq[kept], g0[kept]), np.testing.assert_allclose(bq[kept], b0[kept])
