@@ -198,6 +198,73 @@ def run_layer_case(args):
     capi.paraqaoa_destroy(ctx)
 
 
+LARGE_N, LARGE_P_EDGE, LARGE_M, LARGE_K, LARGE_BEAM, LARGE_DEPTH = 16000, 0.01, 640, 32, 64, 2
+LARGE_JUDGE_TOL = 1e-3
+
+
+def train_large_model(capi, ctx, depth=LARGE_DEPTH, count=2048, epochs=100, seed=7):
+    """Angle network for the large workload: labels from the plain form on
+    method-generated unit-weight random subgraphs of 12..16 vertices whose
+    edge counts span those of the workload's parts (G(n, P), P in
+    [0.005, 0.06]); returns the network and the seconds spent."""
+    t0 = time.perf_counter()
+    specs = synth.graph_specs(count, 12, 16, 0.005, 0.06, seed)
+    G, sizes = synth.chain_of_graphs(specs, wmax=1)
+    part = capi.paraqaoa_partition(capi.Graph.of(G), len(sizes), capi.PART_SIZES, sizes)
+    ids = np.arange(len(sizes), dtype=np.int32)
+    g, b, _ = capi.paraqaoa_solve_plain(ctx, part, ids, depth, STEPS_ADAM)
+    X = capi.paraqaoa_features(ctx, part, ids)
+    capi.paraqaoa_part_free(part)
+    T = np.concatenate([g, b], axis=1).astype(np.float32)
+    net = capi.paraqaoa_mlp_create(ctx, depth, synth.mlp_init(depth, seed))
+    losses = capi.paraqaoa_mlp_train(net, X, T, epochs, 128, 1e-3, synth.epoch_orders(count, epochs, seed))
+    return net, time.perf_counter() - t0, float(losses[-1])
+
+
+def run_large_case(args):
+    """16,000-vertex time-to-cut: G(16000, 0.01), unit weights, 640 parts of
+    25-26 qubits (complex64 states of 256-512 MB, batched by the device-memory
+    budget), p = 2, top-32, beam-64 merge. The learned form (network trained
+    beforehand on small method-generated subgraphs, judge + plain fallback)
+    against the plain form (grid + Adam + INTERP + Adam) on the same GPU."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    free, total = torch.cuda.mem_get_info()
+    solver = pkg.Solver(hbm_budget=int(0.6 * free))
+    g = synth.erdos_renyi(LARGE_N, LARGE_P_EDGE, 0, wmax=1)
+    G = capi.Graph.of(g)
+    net, train_s, loss = train_large_model(capi, solver.ctx)
+    out = {"case": "large", "workload": f"G({LARGE_N},{LARGE_P_EDGE}) unit weights, seed 0; {LARGE_M} parts of "
+           f"25-26 qubits; p={LARGE_DEPTH}; top-{LARGE_K}; beam-{LARGE_BEAM}", "edges": g.num_edges,
+           "train_s": train_s, "train_loss": loss}
+    forms = [("learned", pkg.SolveConfig(M=LARGE_M, K=LARGE_K, p=LARGE_DEPTH, beam=LARGE_BEAM, mlp=net,
+                                          fallback_steps=STEPS_ADAM, judge_tol=LARGE_JUDGE_TOL))]
+    if not args.learned_only:
+        forms.append(("plain", pkg.SolveConfig(M=LARGE_M, K=LARGE_K, p=LARGE_DEPTH, grid_points=GRID,
+                                                adam_steps=STEPS_ADAM, beam=LARGE_BEAM)))
+    for name, cfg in forms:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = solver.solve(G, cfg)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"time_to_cut_s": dt, "cut": int(r.cut), "times": r.times,
+                     "mean_expect": float(np.mean(r.expect))}
+        if r.fallback is not None:
+            out[name]["verdicts"] = {"network": int(np.sum(r.fallback == 0)), "plain_fallback": int(np.sum(r.fallback == 1)),
+                                     "reference": int(np.sum(r.fallback == 2))}
+        print(json.dumps(out), flush=True)
+    if "plain" in out:
+        out["cut_ratio"] = out["learned"]["cut"] / out["plain"]["cut"]
+        out["speedup"] = out["plain"]["time_to_cut_s"] / out["learned"]["time_to_cut_s"]
+    capi.paraqaoa_mlp_free(net)
+    solver.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,7 +272,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="solve", choices=["solve", "layer_pass"],
+    ap.add_argument("--learned-only", action="store_true", help="large case: skip the plain form")
+    ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large"],
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
@@ -219,6 +287,8 @@ def main():
         return run_reference(args, rank, world)
     if args.case == "layer_pass":
         return run_layer_case(args)
+    if args.case == "large":
+        return run_large_case(args)
 
     import torch
     import paper_2603_26232_gb300 as pkg
@@ -266,7 +336,7 @@ def main():
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    prof = {k: capi.paraqaoa_profile_read(solver.ctx, k) for k in range(5)}
+    prof = {k: capi.paraqaoa_profile_read(solver.ctx, k) for k in range(6)}
     capi.paraqaoa_profile_enable(solver.ctx, False)
     # end to end through the public API with host buffers: partition, upload,
     # every host<->device copy and the merge readback inside the timed region

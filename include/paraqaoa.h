@@ -274,15 +274,39 @@ int paraqaoa_mlp_predict(paraqaoa_mlp *mlp, const float *X, int32_t rows, double
 int paraqaoa_mlp_reference(paraqaoa_mlp *mlp, double *gamma_out, double *beta_out);
 
 /* Learned form of the angle search at the network's depth p: features,
- * prediction, then one batch that evaluates <C> at the prediction and at the
- * reference angles. A prediction is kept when its <C> is at least the
- * reference's; the other parts go to paraqaoa_solve_plain(fallback_steps)
- * and fallback_out[i] (optional) is set to 1 for them. gamma_out / beta_out
- * receive count x p angles, value_out (optional) <C> there. The network must
- * belong to ctx. */
+ * prediction, then batches that evaluate <C> at the prediction and at the
+ * reference angles (the judge). Per part, with W its total weight:
+ *  - <C>(prediction) >= <C>(reference): the prediction is kept (verdict 0);
+ *  - otherwise, if <C>(prediction) >= <C>(reference) - tol W: the reference
+ *    angles are taken (verdict 2);
+ *  - otherwise the part goes to paraqaoa_solve_plain(fallback_steps) (verdict 1).
+ * tol >= 0 (tol = 0: any loss against the reference means fallback).
+ * gamma_out / beta_out receive count x p angles, value_out (optional) <C>
+ * there, fallback_out (optional) the verdicts. The network must belong to ctx. */
 int paraqaoa_solve_learned(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count,
-                           paraqaoa_mlp *mlp, int32_t fallback_steps, double *gamma_out, double *beta_out,
-                           double *value_out, int32_t *fallback_out);
+                           paraqaoa_mlp *mlp, int32_t fallback_steps, double tol, double *gamma_out,
+                           double *beta_out, double *value_out, int32_t *fallback_out);
+
+/* Split-precision tensor-core variant of paraqaoa_simulate_batch.
+ * The mixer of each layer is applied as dense 2^k x 2^k products on blocks
+ * of consecutive qubits, ceil(n / block_qubits) blocks of even sizes
+ * (block_qubits in 5..7; fewer, larger blocks of up to 7 qubits where that
+ * would leave blocks of under 5), on the tcgen05 tensor
+ * cores: every FP32 amplitude component and matrix entry is split into two
+ * 16-bit parts (precision PARAQAOA_TC_BF16 or PARAQAOA_TC_FP16; FP16 parts
+ * are taken of the amplitudes scaled by 2^ceil(n/2)) and the three products
+ * hi*hi + hi*lo + lo*hi accumulate in FP32. Phases use an integer cut table
+ * per instance. Every part must have at least 12 vertices. <C> is always
+ * reduced (paraqaoa_expect); with PARAQAOA_SIM_KEEP_STATE in flags the final
+ * states stay for paraqaoa_state / paraqaoa_topk. The paper has no such
+ * variant: it exists to measure what 16-bit tensor-core arithmetic costs in
+ * accuracy against the FP32 butterflies of paraqaoa_simulate_batch.
+ * Synchronises; PARAQAOA_E_TIMEOUT if a bounded device wait gave up. */
+#define PARAQAOA_TC_BF16 0
+#define PARAQAOA_TC_FP16 1
+int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count, int32_t p,
+                         const double *gamma, const double *beta, uint32_t flags, int32_t precision,
+                         int32_t block_qubits);
 
 /* Autotuner for the HBM-streaming layer passes (no counterpart in the paper,
  * which runs a fixed solver per subgraph). For every qubit count n >= 15
@@ -309,7 +333,8 @@ int paraqaoa_profile_read(paraqaoa_ctx *ctx, int32_t which, int64_t *launches, d
 #define PARAQAOA_KCLASS_TOPK 2
 #define PARAQAOA_KCLASS_MERGE 3
 #define PARAQAOA_KCLASS_OTHER 4
-#define PARAQAOA_KCLASS_COUNT 5
+#define PARAQAOA_KCLASS_TC_MIXER 5 /* split-precision tensor-core mixer passes */
+#define PARAQAOA_KCLASS_COUNT 6
 
 const char *paraqaoa_strerror(int code);
 

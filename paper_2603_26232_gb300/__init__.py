@@ -34,6 +34,9 @@ class SolveConfig:
     beam: int = 0            # 0: exhaustive merge; > 0: beam width
     mode: int = _capi.PART_BALANCED
     sizes: np.ndarray | None = None
+    mlp: object = None       # trained angle network (paraqaoa_mlp) of depth p: learned form
+    fallback_steps: int = 32  # Adam steps of the plain form for parts the judge rejects
+    judge_tol: float = 0.0   # judge tolerance (fraction of W) before a part falls back
 
 
 @dataclass
@@ -78,6 +81,31 @@ class Solver:
         except Exception:
             pass
 
+    def final_topk(self, part, ids, p, gam, bet, K):
+        """Final simulation (states kept) and top-K per part, in chunks that
+        pass the context's device-memory admission."""
+        n = len(ids)
+        ex = np.zeros(n)
+        cand = np.zeros((n, K), np.uint32)
+        cand_p = np.zeros((n, K), np.float32)
+        s0, ns = 0, n
+        while s0 < n:
+            ns = min(ns, n - s0)
+            try:
+                _capi.paraqaoa_simulate_batch(self.ctx, part, ids[s0:s0 + ns], p, gam[s0:s0 + ns],
+                                              bet[s0:s0 + ns], _capi.SIM_EXPECT | _capi.SIM_KEEP_STATE)
+            except ParaQAOAError as e:
+                if e.code != _capi.E_ADMISSION or ns == 1:
+                    raise
+                ns = (ns + 1) // 2
+                continue
+            ex[s0:s0 + ns] = _capi.paraqaoa_expect(self.ctx, ns)
+            z, pr = _capi.paraqaoa_topk(self.ctx, ns, K)
+            cand[s0:s0 + ns] = z.reshape(ns, K)
+            cand_p[s0:s0 + ns] = pr.reshape(ns, K)
+            s0 += ns
+        return ex, cand, cand_p
+
     def solve(self, g, cfg: SolveConfig, sync_times: bool = False) -> SolveResult:
         G = Graph.of(g)
         t = {}
@@ -88,25 +116,29 @@ class Solver:
             ids = np.arange(len(size), dtype=np.int32)
             _capi.paraqaoa_part_upload(self.ctx, part)
             t["partition"] = time.perf_counter() - t0
-            gam, bet, best, _ = _capi.paraqaoa_grid_search(self.ctx, part, ids, cfg.grid_points)
-            gam, bet = gam[:, None], bet[:, None]
-            val = best
-            if cfg.adam_steps > 0:
-                gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, 1, gam, bet, cfg.adam_steps,
-                                                        cfg.lr, cfg.h)
-            for depth in range(2, cfg.p + 1):
-                gam, bet = interp(gam, bet)
-                gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, depth, gam, bet,
-                                                        cfg.adam_steps, cfg.lr, cfg.h)
+            fallback = None
+            if cfg.mlp is not None:
+                gam, bet, val, fallback = _capi.paraqaoa_solve_learned(self.ctx, part, ids, cfg.mlp, cfg.p,
+                                                                       cfg.fallback_steps, cfg.judge_tol)
+            else:
+                gam, bet, best, _ = _capi.paraqaoa_grid_search(self.ctx, part, ids, cfg.grid_points)
+                gam, bet = gam[:, None], bet[:, None]
+                val = best
+                if cfg.adam_steps > 0:
+                    gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, 1, gam, bet, cfg.adam_steps,
+                                                            cfg.lr, cfg.h)
+                for depth in range(2, cfg.p + 1):
+                    gam, bet = interp(gam, bet)
+                    gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, depth, gam, bet,
+                                                            cfg.adam_steps, cfg.lr, cfg.h)
             t["angles"] = time.perf_counter() - t0 - t["partition"]
-            _capi.paraqaoa_simulate_batch(self.ctx, part, ids, cfg.p, gam, bet,
-                                          _capi.SIM_EXPECT | _capi.SIM_KEEP_STATE)
-            ex = _capi.paraqaoa_expect(self.ctx, len(ids))
-            cand, cand_p = _capi.paraqaoa_topk(self.ctx, len(ids), cfg.K)
+            ex, cand, cand_p = self.final_topk(part, ids, cfg.p, gam, bet, cfg.K)
             t["final"] = time.perf_counter() - t0 - t["partition"] - t["angles"]
             side, cut = _capi.paraqaoa_merge(self.ctx, G, part, cand, cfg.K, cfg.L, cfg.beam)
             t["merge"] = time.perf_counter() - t0 - t["partition"] - t["angles"] - t["final"]
             t["total"] = time.perf_counter() - t0
-            return SolveResult(side, cut, gam, bet, ex, cand, cand_p, t)
+            res = SolveResult(side, cut, gam, bet, ex, cand, cand_p, t)
+            res.fallback = fallback
+            return res
         finally:
             _capi.paraqaoa_part_free(part)

@@ -24,7 +24,8 @@ E_SCRATCH_LIMIT = -9
 PART_BALANCED, PART_ALG1_LITERAL, PART_SIZES = 0, 1, 2
 SIM_EXPECT, SIM_KEEP_STATE = 0x1, 0x2
 TOPK_CANONICAL, TOPK_RAW = 0x0, 0x1
-KCLASS_LAYER_PASS, KCLASS_SMEM_SIM, KCLASS_TOPK, KCLASS_MERGE, KCLASS_OTHER = range(5)
+KCLASS_LAYER_PASS, KCLASS_SMEM_SIM, KCLASS_TOPK, KCLASS_MERGE, KCLASS_OTHER, KCLASS_TC_MIXER = range(6)
+TC_BF16, TC_FP16 = 0, 1
 MAX_TOPK = 32
 MAX_SUBGRAPH_WEIGHT = 4095
 
@@ -66,6 +67,8 @@ _SIGS = {
     "paraqaoa_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "paraqaoa_topk_noalloc": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, P, P, P], ctypes.c_int),
     "paraqaoa_features": ([P, P, P, ctypes.c_int32, P], ctypes.c_int),
+    "paraqaoa_simulate_tc": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_uint32, ctypes.c_int32,
+                              ctypes.c_int32], ctypes.c_int),
     "paraqaoa_solve_plain": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_mlp_param_count": ([ctypes.c_int32], ctypes.c_int64),
     "paraqaoa_mlp_create": ([P, ctypes.c_int32, P, ctypes.POINTER(P)], ctypes.c_int),
@@ -76,7 +79,8 @@ _SIGS = {
                            ctypes.c_int),
     "paraqaoa_mlp_predict": ([P, P, ctypes.c_int32, P, P], ctypes.c_int),
     "paraqaoa_mlp_reference": ([P, P, P], ctypes.c_int),
-    "paraqaoa_solve_learned": ([P, P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
+    "paraqaoa_solve_learned": ([P, P, P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_double, P, P, P, P],
+                               ctypes.c_int),
 }
 
 
@@ -362,12 +366,24 @@ def paraqaoa_mlp_reference(mlp, p: int):
     return g, b
 
 
-def paraqaoa_solve_learned(ctx, part, ids, mlp, p: int, fallback_steps: int = 32):
+def paraqaoa_solve_learned(ctx, part, ids, mlp, p: int, fallback_steps: int = 32, tol: float = 0.0):
+    """Returns angles, <C> and per-part verdicts (0 network, 1 plain fallback, 2 reference)."""
     ids = _arr(ids, np.int32)
     g = np.zeros((ids.size, p))
     b = np.zeros((ids.size, p))
     v = np.zeros(ids.size)
     fb = np.zeros(ids.size, np.int32)
-    _check(load().paraqaoa_solve_learned(ctx, part, _ptr(ids), ids.size, mlp, fallback_steps, _ptr(g), _ptr(b),
-                                         _ptr(v), _ptr(fb)), "paraqaoa_solve_learned")
+    _check(load().paraqaoa_solve_learned(ctx, part, _ptr(ids), ids.size, mlp, fallback_steps, float(tol), _ptr(g),
+                                         _ptr(b), _ptr(v), _ptr(fb)), "paraqaoa_solve_learned")
     return g, b, v, fb
+
+
+def paraqaoa_simulate_tc(ctx, part, ids, p: int, gamma, beta, flags: int = SIM_EXPECT, precision: int = TC_FP16,
+                         block_qubits: int = 7):
+    ids = _arr(ids, np.int32)
+    g = _arr(gamma, np.float64)
+    b = _arr(beta, np.float64)
+    if g.size != ids.size * p or b.size != ids.size * p:
+        raise ValueError("gamma/beta must hold count x p angles")
+    _check(load().paraqaoa_simulate_tc(ctx, part, _ptr(ids), ids.size, int(p), _ptr(g), _ptr(b), int(flags),
+                                       int(precision), int(block_qubits)), "paraqaoa_simulate_tc")

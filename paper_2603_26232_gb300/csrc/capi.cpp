@@ -123,6 +123,8 @@ struct paraqaoa_ctx {
   DevBuf m_sides[2], m_score[2], m_rank[2], m_r2s[2], m_keys, m_nb;
   // angle loop
   DevBuf o_vals, o_best, o_theta, o_m, o_v, o_w, o_g2, o_b2;
+  // tensor-core variant: device error flag of its bounded waits
+  DevBuf d_tc_err;
   // profiling
   bool prof = false;
   std::vector<ProfRec> pending;
@@ -521,7 +523,7 @@ void paraqaoa_destroy(paraqaoa_ctx* c) {
                     &c->m_key, &c->m_path, &c->m_sides[0], &c->m_sides[1], &c->m_score[0],
                     &c->m_score[1], &c->m_rank[0], &c->m_rank[1], &c->m_r2s[0], &c->m_r2s[1],
                     &c->m_keys, &c->m_nb, &c->o_vals, &c->o_best, &c->o_theta, &c->o_m, &c->o_v,
-                    &c->o_w, &c->o_g2, &c->o_b2, &c->d_consts};
+                    &c->o_w, &c->o_g2, &c->o_b2, &c->d_consts, &c->d_tc_err};
   for (DevBuf* b : bufs) b->release();
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
@@ -1024,40 +1026,163 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
   PQ_CUDA(cudaMemcpyAsync(c->o_w.p, wsum.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
   PQ_CUDA(cudaMemsetAsync(c->o_m.p, 0, sizeof(double) * count * D, c->stream));
   PQ_CUDA(cudaMemsetAsync(c->o_v.p, 0, sizeof(double) * count * D, c->stream));
-  if (steps > 0) {
-    std::vector<int32_t> ev_ids((size_t)count * E);
-    for (int32_t s = 0; s < count; ++s)
-      for (int32_t e = 0; e < E; ++e) ev_ids[(size_t)s * E + e] = ids[s];
-    rc = plan_build(c, pt, ev_ids.data(), count * E, p, PARAQAOA_SIM_EXPECT);
+  // Subgraphs are independent: chunk them so that each batch of 4p shifted
+  // evaluations per subgraph passes admission (halving until it does).
+  std::vector<int32_t> ev_ids((size_t)count * E);
+  for (int32_t s = 0; s < count; ++s)
+    for (int32_t e = 0; e < E; ++e) ev_ids[(size_t)s * E + e] = ids[s];
+  int32_t s0 = 0;
+  while (steps > 0 && s0 < count) {
+    int32_t ns = count - s0;
+    for (;;) {
+      rc = plan_build(c, pt, ev_ids.data() + (size_t)s0 * E, ns * E, p, PARAQAOA_SIM_EXPECT);
+      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
+      ns = (ns + 1) / 2;
+    }
     if (rc) return rc;
+    double* th = c->o_theta.as<double>() + (size_t)s0 * D;
+    double* mm = c->o_m.as<double>() + (size_t)s0 * D;
+    double* vv = c->o_v.as<double>() + (size_t)s0 * D;
+    const double* ww = c->o_w.as<double>() + s0;
     for (int32_t t = 1; t <= steps; ++t) {
       {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-        PQ_CUDA(launch_adam_shifts(c->o_theta.as<double>(), count, p, h, c->d_gamma.as<double>(),
-                                   c->d_beta.as<double>(), c->stream));
+        PQ_CUDA(launch_adam_shifts(th, ns, p, h, c->d_gamma.as<double>(), c->d_beta.as<double>(), c->stream));
       }
       rc = plan_run(c);
       if (rc) return rc;
       ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-      PQ_CUDA(launch_adam_update(c->d_expect.as<double>(), c->o_w.as<double>(), count, p, h, lr, t,
-                                 c->o_theta.as<double>(), c->o_m.as<double>(), c->o_v.as<double>(),
-                                 c->stream));
+      PQ_CUDA(launch_adam_update(c->d_expect.as<double>(), ww, ns, p, h, lr, t, th, mm, vv, c->stream));
     }
+    s0 += ns;
   }
-  rc = plan_build(c, pt, ids, count, p, PARAQAOA_SIM_EXPECT);
+  // final <C> at the optimised angles, chunked the same way
+  PQ_CUDA(c->o_vals.ensure(sizeof(double) * count));
+  s0 = 0;
+  while (s0 < count) {
+    int32_t ns = count - s0;
+    for (;;) {
+      rc = plan_build(c, pt, ids + s0, ns, p, PARAQAOA_SIM_EXPECT);
+      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
+      ns = (ns + 1) / 2;
+    }
+    if (rc) return rc;
+    {
+      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+      PQ_CUDA(launch_theta_split(c->o_theta.as<double>() + (size_t)s0 * D, ns, p, c->d_gamma.as<double>(),
+                                 c->d_beta.as<double>(), c->stream));
+    }
+    rc = plan_run(c);
+    if (rc) return rc;
+    PQ_CUDA(cudaMemcpyAsync(gamma_io + (size_t)s0 * p, c->d_gamma.p, sizeof(double) * ns * p, cudaMemcpyDeviceToHost,
+                            c->stream));
+    PQ_CUDA(cudaMemcpyAsync(beta_io + (size_t)s0 * p, c->d_beta.p, sizeof(double) * ns * p, cudaMemcpyDeviceToHost,
+                            c->stream));
+    PQ_CUDA(cudaMemcpyAsync(out_value + s0, c->d_expect.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->stream));
+    PQ_CUDA(cudaStreamSynchronize(c->stream));
+    s0 += ns;
+  }
+  prof_flush(c);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t p,
+                         const double* gamma, const double* beta, uint32_t flags, int32_t precision,
+                         int32_t block_qubits) {
+  if (!c || !pt || !ids || !gamma || !beta || count < 1 || p < 1 || p > PARAQAOA_MAX_P) return PARAQAOA_E_INVAL;
+  if ((precision != PARAQAOA_TC_BF16 && precision != PARAQAOA_TC_FP16) || block_qubits < 5 || block_qubits > 7)
+    return PARAQAOA_E_INVAL;
+  for (int32_t i = 0; i < count; ++i) {
+    if (ids[i] < 0 || ids[i] >= pt->M) return PARAQAOA_E_INVAL;
+    if (pt->size[ids[i]] < 12) return PARAQAOA_E_INVAL;
+  }
+  PQ_CUDA(cudaSetDevice(c->device));
+  int rc = upload_part(c, pt, false);
   if (rc) return rc;
+  const uint32_t fl = (flags & (PARAQAOA_SIM_EXPECT | PARAQAOA_SIM_KEEP_STATE)) | PARAQAOA_SIM_KEEP_STATE;
+  rc = plan_build(c, pt, ids, count, p, fl);
+  if (rc) return rc;
+  SimPlan& pl = c->plan;
+  pl.flags = flags | PARAQAOA_SIM_EXPECT;  // <C> is always reduced; states kept only on request
+  // instances grouped by qubit count; cut tables (uint16, 2^n each) per instance
+  std::map<int, std::vector<int32_t>> by_n;
+  for (int32_t i = 0; i < count; ++i) by_n[pl.inst[i].n].push_back(i);
+  std::vector<int32_t> lists;
+  std::vector<std::pair<int, std::pair<int32_t, int32_t>>> groups;
+  int64_t cut_elems = 0, part_elems = 0;
+  for (auto& kv : by_n) {
+    groups.push_back({kv.first, {(int32_t)lists.size(), (int32_t)kv.second.size()}});
+    lists.insert(lists.end(), kv.second.begin(), kv.second.end());
+    cut_elems = std::max<int64_t>(cut_elems, (int64_t)kv.second.size() << kv.first);
+    part_elems = std::max<int64_t>(part_elems, (int64_t)kv.second.size() * tc_finish_blocks(kv.first));
+  }
+  const double extra = (double)cut_elems * 2 + (double)part_elems * 8;
+  const double need = (double)pl.state_elems * 8 + (double)pl.table_elems * 8 + extra;
+  if (need > (double)c->budget) return PARAQAOA_E_ADMISSION;
+  PQ_CUDA(c->d_consts.ensure(std::max<size_t>(sizeof(int32_t) * lists.size(), 4)));
+  PQ_CUDA(c->d_topk_scratch.ensure((size_t)cut_elems * 2 + 256));
+  PQ_CUDA(c->d_partials.ensure(sizeof(double) * std::max<int64_t>(part_elems, 1)));
+  PQ_CUDA(c->d_tc_err.ensure(sizeof(int)));
+  int32_t* dl = c->d_consts.as<int32_t>();
+  uint16_t* cuts = reinterpret_cast<uint16_t*>(c->d_topk_scratch.p);
+  int* err = c->d_tc_err.as<int>();
+  PQ_CUDA(cudaMemcpyAsync(dl, lists.data(), sizeof(int32_t) * lists.size(), cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+  PQ_CUDA(cudaMemcpyAsync(c->d_gamma.p, gamma, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
+  PQ_CUDA(cudaMemcpyAsync(c->d_beta.p, beta, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
+  InstDev* inst = c->d_inst.as<InstDev>();
   {
     ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-    PQ_CUDA(launch_theta_split(c->o_theta.as<double>(), count, p, c->d_gamma.as<double>(),
-                               c->d_beta.as<double>(), c->stream));
+    PQ_CUDA(launch_prep_layers(inst, count, p, c->d_gamma.as<double>(), c->d_beta.as<double>(),
+                               c->d_tables.as<float2>(), inst, c->stream));
   }
-  rc = plan_run(c);
-  if (rc) return rc;
-  PQ_CUDA(cudaMemcpyAsync(gamma_io, c->d_gamma.p, sizeof(double) * count * p, cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(beta_io, c->d_beta.p, sizeof(double) * count * p, cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(out_value, c->d_expect.p, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+  const bool fp16 = precision == PARAQAOA_TC_FP16;
+  float2* states = c->d_states.as<float2>();
+  for (auto& gr : groups) {
+    const int n = gr.first;
+    const int32_t off = gr.second.first, cnt = gr.second.second;
+    const int64_t stride = int64_t(1) << n;
+    for (int32_t j = 0; j < cnt; ++j) {
+      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)stride * 2);
+      PQ_CUDA(launch_cut_table(c->d_subs.as<SubDev>() + pl.inst[lists[off + j]].sub, n, c->d_planes.as<uint32_t>(),
+                               cuts + (int64_t)j * stride, c->stream));
+    }
+    // ceil(n / block_qubits) blocks of as even sizes as possible; fewer blocks
+    // (sizes up to 7) when that would leave blocks under 5 qubits. Every block
+    // has 5..7 qubits and at most n - 6, so that a tile holds 64 groups.
+    int nb = (n + block_qubits - 1) / block_qubits;
+    if (n / nb < 5) nb = n / 5;
+    std::vector<int> bs(nb, n / nb);
+    for (int b = 0; b < n % nb; ++b) ++bs[b];
+    for (int b : bs)
+      if (b < 5 || b > n - 6) return PARAQAOA_E_INVAL;
+    const float scale = fp16 ? std::ldexp(1.f, (n + 1) / 2) : 1.f;
+    for (int l = 0; l < p; ++l) {
+      {
+        ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)cnt * stride * (l == 0 ? 10.0 : 18.0));
+        PQ_CUDA(launch_tc_phase(inst, dl + off, cnt, n, l, l == 0, c->d_tables.as<float2>(), cuts, stride, states,
+                                c->stream));
+      }
+      int q0 = 0;
+      for (int b : bs) {
+        ProfScope ps(c, PARAQAOA_KCLASS_TC_MIXER, (double)cnt * stride * 16.0);
+        PQ_CUDA(launch_mixer_tc(b, fp16, inst, dl + off, cnt, n, q0, l, states, scale, err, c->num_sms, c->stream));
+        q0 += b;
+      }
+    }
+    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)cnt * stride * (flags & PARAQAOA_SIM_KEEP_STATE ? 18.0 : 10.0));
+    PQ_CUDA(launch_tc_finish(inst, dl + off, cnt, n, cuts, stride, states, c->d_partials.as<double>(),
+                             (flags & PARAQAOA_SIM_KEEP_STATE) ? 1 : 0, c->d_expect.as<double>(), c->stream));
+  }
+  int herr = 0;
+  PQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
   prof_flush(c);
+  if (herr) {
+    pl.valid = false;
+    return PARAQAOA_E_TIMEOUT;
+  }
+  if (!(flags & PARAQAOA_SIM_KEEP_STATE)) pl.flags &= ~PARAQAOA_SIM_KEEP_STATE;
   return PARAQAOA_OK;
 }
 

@@ -199,6 +199,27 @@ void canonicalize(double* g, double* b, int p) {
   }
 }
 
+// <C> of count instances through simulate/expect, in chunks that pass the
+// context's admission (halving the chunk until it does).
+int expect_chunked(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int32_t* ids, int32_t count, int p,
+                   const double* g, const double* b, double* out) {
+  int32_t s0 = 0;
+  while (s0 < count) {
+    int32_t ns = count - s0;
+    int rc;
+    for (;;) {
+      rc = paraqaoa_simulate_batch(ctx, part, ids + s0, ns, p, g + (size_t)s0 * p, b + (size_t)s0 * p,
+                                   PARAQAOA_SIM_EXPECT);
+      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
+      ns = (ns + 1) / 2;
+    }
+    if (rc) return rc;
+    LQ_RC(paraqaoa_expect(ctx, ns, out + s0));
+    s0 += ns;
+  }
+  return PARAQAOA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -376,8 +397,7 @@ int paraqaoa_solve_plain(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int
     if (steps > 0) {
       LQ_RC(paraqaoa_optimize(ctx, part, ids, count, d, steps, 0.02, 1e-3, g.data(), b.data(), val.data()));
     } else {
-      LQ_RC(paraqaoa_simulate_batch(ctx, part, ids, count, d, g.data(), b.data(), PARAQAOA_SIM_EXPECT));
-      LQ_RC(paraqaoa_expect(ctx, count, val.data()));
+      LQ_RC(expect_chunked(ctx, part, ids, count, d, g.data(), b.data(), val.data()));
     }
   }
   for (int i = 0; i < count; ++i) canonicalize(g.data() + (size_t)i * p, b.data() + (size_t)i * p, p);
@@ -412,10 +432,17 @@ int paraqaoa_features(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int32_
 }
 
 int paraqaoa_solve_learned(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int32_t* ids, int32_t count,
-                           paraqaoa_mlp* q, int32_t fallback_steps, double* gamma_out, double* beta_out,
+                           paraqaoa_mlp* q, int32_t fallback_steps, double tol, double* gamma_out, double* beta_out,
                            double* value_out, int32_t* fallback_out) {
-  if (!ctx || !part || !ids || count < 1 || !q || q->ctx != ctx || fallback_steps < 0 || !gamma_out || !beta_out)
+  if (!ctx || !part || !ids || count < 1 || !q || q->ctx != ctx || fallback_steps < 0 || !gamma_out || !beta_out ||
+      !(tol >= 0.0))
     return PARAQAOA_E_INVAL;
+  int32_t M = 0;
+  LQ_RC(paraqaoa_part_info(part, &M, nullptr, nullptr, nullptr, nullptr));
+  std::vector<int64_t> weight(M);
+  LQ_RC(paraqaoa_part_info(part, &M, nullptr, nullptr, nullptr, weight.data()));
+  for (int i = 0; i < count; ++i)
+    if (ids[i] < 0 || ids[i] >= M) return PARAQAOA_E_INVAL;
   const int p = q->p;
   std::vector<float> X((size_t)count * kFeatures);
   LQ_RC(paraqaoa_features(ctx, part, ids, count, X.data()));
@@ -434,15 +461,26 @@ int paraqaoa_solve_learned(paraqaoa_ctx* ctx, const paraqaoa_part* part, const i
       b2[(size_t)(count + i) * p + l] = q->ref[p + l];
     }
   }
-  LQ_RC(paraqaoa_simulate_batch(ctx, part, ids2.data(), 2 * count, p, g2.data(), b2.data(), PARAQAOA_SIM_EXPECT));
-  LQ_RC(paraqaoa_expect(ctx, 2 * count, ex.data()));
+  LQ_RC(expect_chunked(ctx, part, ids2.data(), 2 * count, p, g2.data(), b2.data(), ex.data()));
   std::vector<int32_t> rej;
   std::vector<double> val(count);
   for (int i = 0; i < count; ++i) {
     val[i] = ex[i];
-    const bool ok = ex[i] >= ex[count + i];
-    if (!ok) rej.push_back(i);
-    if (fallback_out) fallback_out[i] = ok ? 0 : 1;
+    int verdict = 0;                                  // keep the prediction
+    if (ex[i] < ex[count + i]) {
+      if (ex[i] >= ex[count + i] - tol * (double)std::max<int64_t>(weight[ids[i]], 1)) {
+        verdict = 2;                                  // the reference is better by less than tol W: take it
+        val[i] = ex[count + i];
+        for (int l = 0; l < p; ++l) {
+          g[(size_t)i * p + l] = q->ref[l];
+          b[(size_t)i * p + l] = q->ref[p + l];
+        }
+      } else {
+        verdict = 1;                                  // the network missed: plain form
+        rej.push_back(i);
+      }
+    }
+    if (fallback_out) fallback_out[i] = verdict;
   }
   if (!rej.empty()) {
     std::vector<int32_t> rid(rej.size());

@@ -154,6 +154,18 @@ cudaError_t launch_adam_raw(float* w, const float* g, float* m, float* v, int64_
                             cudaStream_t st);
 cudaError_t launch_split_angles(const float* Y, int rows, int p, double* gamma, double* beta, cudaStream_t st);
 
+// Split-precision tensor-core mixer variant (tc_mixer.cu).
+cudaError_t launch_mixer_tc(int kb, bool fp16, const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n,
+                            int32_t q0, int32_t layer, float2* states, float scale, int* err, int num_sms,
+                            cudaStream_t st);
+cudaError_t launch_tc_phase(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n, int32_t layer,
+                            int32_t init, const float2* tables, const uint16_t* cuts, int64_t cut_stride,
+                            float2* states, cudaStream_t st);
+int tc_finish_blocks(int32_t n);
+cudaError_t launch_tc_finish(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n, const uint16_t* cuts,
+                             int64_t cut_stride, float2* states, double* partials, int32_t keep, double* expect,
+                             cudaStream_t st);
+
 // Context internals the learned-angle entry points share (capi.cpp).
 cudaStream_t ctx_stream(paraqaoa_ctx* c);
 int ctx_device(paraqaoa_ctx* c);

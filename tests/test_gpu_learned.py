@@ -184,7 +184,8 @@ def test_learned_angles_gain_over_plain_and_constant(api, orc):
         losses = capi.paraqaoa_mlp_train(net, Xtr, T, epochs, 128, 1e-3, synth.epoch_orders(ntr, epochs, 1))
         assert losses[-1] < 0.1 * losses[0]
         gp, bp, vp = capi.paraqaoa_solve_plain(ctx, pte, ite, p, steps)
-        gq, bq, vq, fb = capi.paraqaoa_solve_learned(ctx, pte, ite, net, p, steps)
+        gq, bq, vq, fb = capi.paraqaoa_solve_learned(ctx, pte, ite, net, p, steps, 0.0)
+        gt, bt, vt, fbt = capi.paraqaoa_solve_learned(ctx, pte, ite, net, p, steps, 1e-3)
 
         def value_at(g, b):
             capi.paraqaoa_simulate_batch(ctx, pte, ite, p, g, b)
@@ -219,5 +220,13 @@ def test_learned_angles_gain_over_plain_and_constant(api, orc):
     o_ref = orc.expect_batch(batch, ite, np.tile(rg, (nte, 1)), np.tile(rb, (nte, 1)))
     decided = np.abs(o_pred - o_ref) > 1e-5 * W
     assert np.array_equal(fb[decided] == 0, (o_pred >= o_ref)[decided])
+    assert set(np.unique(fb)) <= {0, 1}  # tol = 0: no reference verdicts
     kept = fb == 0
     np.testing.assert_allclose(gq[kept], g0[kept]), np.testing.assert_allclose(bq[kept], b0[kept])
+    # tol = 1e-3: reference angles where the prediction loses by less than 1e-3 W
+    thr = o_ref - 1e-3 * W
+    decided = decided & (np.abs(o_pred - thr) > 1e-5 * W)
+    want = np.where(o_pred >= o_ref, 0, np.where(o_pred >= thr, 2, 1))
+    assert np.array_equal(fbt[decided], want[decided])
+    ref_taken = fbt == 2
+    assert np.allclose(gt[ref_taken], rg) and np.allclose(bt[ref_taken], rb)
