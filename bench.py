@@ -181,7 +181,7 @@ def run_layer_case(args):
     ids = np.repeat(np.arange(M, dtype=np.int32), 8)
     gam, bet = synth.random_angles(len(ids), 2, 3)
     capi.paraqaoa_part_upload(ctx, part)
-    tuned = {20: (None, None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
+    tuned = {20: (None, None, None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
     for it in range(args.iters):
         if it == args.iters - 1:
             capi.paraqaoa_profile_enable(ctx, True)
@@ -191,6 +191,7 @@ def run_layer_case(args):
     peak, kind = read_peaks()
     print(json.dumps({"case": "layer_pass", "instances": int(len(ids)), "qubits": 20, "p": 2,
                       "tile_bits": tuned[20][0], "reg_bits": tuned[20][1], "min_run_qubits": tuned[20][2],
+                      "split": tuned[20][3],
                       "launches": n_l, "ms": ms, "algorithmic_bytes": by,
                       "achieved_gbs": by / (ms / 1e3) / 1e9, "peak_gbs": peak,
                       "frac": by / (ms / 1e3) / 1e9 / peak}), flush=True)
@@ -199,7 +200,7 @@ def run_layer_case(args):
 
 
 LARGE_N, LARGE_P_EDGE, LARGE_M, LARGE_K, LARGE_BEAM, LARGE_DEPTH = 16000, 0.01, 640, 32, 64, 2
-LARGE_JUDGE_TOL = 1e-3
+LARGE_JUDGE_TOL = 1e-2
 
 
 def train_large_model(capi, ctx, depth=LARGE_DEPTH, count=2048, epochs=100, seed=7):
@@ -259,6 +260,7 @@ def run_large_case(args):
         print(json.dumps(out), flush=True)
     if "plain" in out:
         out["cut_ratio"] = out["learned"]["cut"] / out["plain"]["cut"]
+        out["expect_ratio"] = out["learned"]["mean_expect"] / out["plain"]["mean_expect"]
         out["speedup"] = out["plain"]["time_to_cut_s"] / out["learned"]["time_to_cut_s"]
     capi.paraqaoa_mlp_free(net)
     solver.close()
@@ -382,8 +384,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(total_launches),
             "clocks": clk,
-            "autotune": {str(n): {"tile_bits": tb, "reg_bits": rb, "min_run_qubits": cm}
-                         for n, (tb, rb, cm) in tuned.items() if n == 20},
+            "autotune": {str(n): {"tile_bits": tb, "reg_bits": rb, "min_run_qubits": cm, "split": sp}
+                         for n, (tb, rb, cm, sp) in tuned.items() if n == 20},
             "cpu_baseline": cb,
         }
         print(json.dumps(line), flush=True)

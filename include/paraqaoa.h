@@ -215,13 +215,16 @@ int paraqaoa_topk_noalloc(const float *state_dev, int32_t n, int32_t K, uint32_t
 
 #define PARAQAOA_FEATURES 64
 
-/* The 64 features of each part in ids (count x 64 floats, row-major):
- * [0] n/32, [1] edge density, [2]/[3] mean/std edge weight over 16,
- * [4..8) mean/std/max/min degree over n, [8..24) degree histogram (bin
- * min(deg, 15)) over n, [24..40) weight histogram (bin min(w, 16) - 1) over
- * |E|, [40..56) weighted-degree histogram (bin min(15, floor(16 D / (max D +
- * 1)))) over n, [56] triangles / C(n,3), [57] total weight / (10 C(n,2)),
- * [58..64) zero. Parts must have at most 32 vertices. Synchronises. */
+/* The 64 features of each part in ids (count x 64 floats, row-major),
+ * computed over the m vertices that have at least one edge (an isolated
+ * vertex changes neither <C> nor the best angles; all features are 0 when
+ * m = 0): [0] m/32, [1] edge density |E| / C(m,2), [2]/[3] mean/std edge
+ * weight over 16, [4..8) mean/std/max/min degree over m, [8..24) degree
+ * histogram (bin min(deg, 15)) over m, [24..40) weight histogram (bin
+ * min(w, 16) - 1) over |E|, [40..56) weighted-degree histogram (bin
+ * min(15, floor(16 D / (max D + 1)))) over m, [56] triangles / C(m,3),
+ * [57] total weight / (10 C(m,2)), [58..64) zero. Parts must have at most
+ * 32 vertices. Synchronises. */
 int paraqaoa_features(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count,
                       float *out_host);
 
@@ -310,15 +313,26 @@ int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
 
 /* Autotuner for the HBM-streaming layer passes (no counterpart in the paper,
  * which runs a fixed solver per subgraph). For every qubit count n >= 15
- * present in `part`, times the candidate tile shapes (2^12 amplitudes per CTA
- * as 32 or 16 registers per thread, or 2^13 as 32) and minimum
- * contiguous-qubit runs (2..4) on copies of one part of that size at depth p,
- * and keeps the fastest for ctx. Choices that give the same pass schedule are
- * timed once. Optional outputs (31 entries each, indexed by n): chosen tile
- * bits, register bits per thread and minimum run. Without a call the context
- * uses the 2^12 x 16-register shape unless 2^13 needs fewer passes. */
-int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p,
-                      int32_t *out_tile_bits, int32_t *out_reg_bits, int32_t *out_c_min);
+ * present in `part`, times the candidate schedules on copies of one part of
+ * that size at depth p and keeps the fastest for ctx: tile shapes (2^12
+ * amplitudes per CTA as 32 or 16 registers per thread, or 2^13 as 32),
+ * minimum contiguous-qubit runs of the higher groups (2..4), and classic or
+ * split schedules (classic: the low group is the tile's 2^12 or 2^13
+ * contiguous qubits, mixed in up to three register rounds; split: the low
+ * group is the 2R lowest qubits, mixed in two rounds with one transpose).
+ * Choices that give the same pass schedule are timed once. Optional outputs
+ * (31 entries each, indexed by n): chosen tile bits, register bits per
+ * thread, minimum run, split flag. Without a call the context uses the
+ * classic 2^12 x 16-register schedule unless 2^13 needs fewer passes. */
+int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, int32_t *out_tile_bits,
+                      int32_t *out_reg_bits, int32_t *out_c_min, int32_t *out_split);
+
+/* Set the layer-pass schedule of n-qubit parts by hand (the choice the
+ * autotuner makes): tile bits and register bits per thread (one of the
+ * shapes 12/5, 12/4, 13/5), minimum contiguous run c_min of the higher groups
+ * and split (0 classic, 1 split). Affects later simulate calls of ctx. */
+int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
+                          int32_t split);
 
 /* Per-kernel device time recorded with CUDA events on the context stream.
  * enable != 0 starts recording (and clears the counters). */

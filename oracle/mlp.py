@@ -32,16 +32,22 @@ HID = 256       # hidden width
 
 # ------------------------------------------------------------------ features
 def features(n: int, eu, ev, ew) -> np.ndarray:
-    """64 features of one subgraph with n vertices and edge list (eu, ev, ew):
+    """64 features of one subgraph with n vertices and edge list (eu, ev, ew).
 
-      [0] n / 32                 [1] |E| / C(n,2)            [2] mean w / 16
-      [3] std w / 16 (population) [4] mean degree / n        [5] std degree / n
-      [6] max degree / n         [7] min degree / n
-      [8..24)  degree histogram, bin min(deg, 15), counts / n
-      [24..40) weight histogram, bin min(w, 16) - 1, counts / max(|E|, 1)
-      [40..56) weighted-degree histogram, bin min(15, floor(16 D_u / (max_v D_v + 1))), counts / n
-      [56] triangles / C(n,3)    [57] total weight / (10 C(n,2))    [58..64) 0
+    Isolated vertices are left out first: a vertex without edges contributes
+    nothing to C(z), its qubit's mixer commutes with everything else and the
+    phase, and so neither <C> nor the best angles depend on it. With m the
+    number of vertices that have at least one edge (all features 0 when m = 0):
 
+      [0] m / 32                 [1] |E| / C(m,2)            [2] mean w / 16
+      [3] std w / 16 (population) [4] mean degree / m        [5] std degree / m
+      [6] max degree / m         [7] min degree / m
+      [8..24)  degree histogram, bin min(deg, 15), counts / m
+      [24..40) weight histogram, bin min(w, 16) - 1, counts / |E|
+      [40..56) weighted-degree histogram, bin min(15, floor(16 D_u / (max_v D_v + 1))), counts / m
+      [56] triangles / C(m,3)    [57] total weight / (10 C(m,2))    [58..64) 0
+
+    Degrees and weighted degrees D run over the m non-isolated vertices.
     C(k, j) is the binomial coefficient (0 when k < j, and then the feature is 0).
     """
     eu = np.asarray(eu, np.int64)
@@ -59,35 +65,39 @@ def features(n: int, eu, ev, ew) -> np.ndarray:
         wdeg[b] += w
         adj[a].add(int(b))
         adj[b].add(int(a))
-    pairs = n * (n - 1) / 2.0
-    triples = n * (n - 1) * (n - 2) / 6.0
-    f[0] = n / 32.0
-    f[1] = E / pairs if pairs > 0 else 0.0
-    if E > 0:
-        mw = ew.mean()
-        f[2] = mw / 16.0
-        f[3] = np.sqrt(max((ew.astype(np.float64) ** 2).mean() - mw * mw, 0.0)) / 16.0
+    keep = deg > 0
+    m = int(keep.sum())
+    if m == 0:
+        return f
+    deg, wdeg = deg[keep], wdeg[keep]
+    pairs = m * (m - 1) / 2.0
+    triples = m * (m - 1) * (m - 2) / 6.0
+    f[0] = m / 32.0
+    f[1] = E / pairs
+    mw = ew.mean()
+    f[2] = mw / 16.0
+    f[3] = np.sqrt(max((ew.astype(np.float64) ** 2).mean() - mw * mw, 0.0)) / 16.0
     md = deg.mean()
-    f[4] = md / n
-    f[5] = np.sqrt(max((deg.astype(np.float64) ** 2).mean() - md * md, 0.0)) / n
-    f[6] = deg.max() / n
-    f[7] = deg.min() / n
+    f[4] = md / m
+    f[5] = np.sqrt(max((deg.astype(np.float64) ** 2).mean() - md * md, 0.0)) / m
+    f[6] = deg.max() / m
+    f[7] = deg.min() / m
     for d in deg:
         f[8 + min(int(d), 15)] += 1.0
-    f[8:24] /= n
+    f[8:24] /= m
     for w in ew:
         f[24 + min(int(w), 16) - 1] += 1.0
-    f[24:40] /= max(E, 1)
+    f[24:40] /= E
     dmax = int(wdeg.max())
     for d in wdeg:
         f[40 + min(15, (16 * int(d)) // (dmax + 1))] += 1.0
-    f[40:56] /= n
+    f[40:56] /= m
     tri = 0
     for a, b in zip(eu, ev):
         tri += len(adj[int(a)] & adj[int(b)])
     tri //= 3
     f[56] = tri / triples if triples > 0 else 0.0
-    f[57] = ew.sum() / (10.0 * pairs) if pairs > 0 else 0.0
+    f[57] = ew.sum() / (10.0 * pairs)
     return f
 
 

@@ -106,8 +106,8 @@ struct paraqaoa_ctx {
   // low qubits a high-group tile carries (heuristic, or measured by autotune)
   int8_t tile_kind[PARAQAOA_MAX_QUBITS + 1] = {};  // index into kTileShapes
   int8_t c_min[PARAQAOA_MAX_QUBITS + 1] = {};
-  // L2-prefetch distance of the layer passes, in waves of resident CTAs (0: off)
-  int8_t pf_waves[PARAQAOA_MAX_QUBITS + 1] = {};
+  // split schedule (the low group is 2R qubits, one transpose per pass) per n
+  int8_t split[PARAQAOA_MAX_QUBITS + 1] = {};
   int num_sms = 0;
   // partition on the device
   uint64_t part_serial = 0;
@@ -345,12 +345,10 @@ int plan_run(paraqaoa_ctx* c) {
   for (auto& kv : pl.hbm) {
     const int n = kv.first;
     const int kind = c->tile_kind[n], tb = kTileShapes[kind].tb;
-    const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want);
+    const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[kind].r : 0);
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
     PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * cut_consts_elems(kind, kv.second.second)));
-    const int pf = c->pf_waves[n] * c->num_sms * layer_resident_per_sm(kind);
-    for (PassDesc pd : sched) {
-      pd.pf = pf;
+    for (const PassDesc& pd : sched) {
       if (pd.layerP >= 0 || pd.expect) {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
         PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
@@ -392,24 +390,30 @@ int ctx_part_device(paraqaoa_ctx* c, const paraqaoa_part* pt, const SubDev** sub
 // for even l and decreasing for odd l, so the last group of layer l is the
 // first of layer l+1 and one pass can finish layer l, apply the phase of
 // l+1 and start its mixer: 1 + p (G - 1) passes in all.
-int schedule_groups(int n, int tb, int c_min) {
+// Split schedules (split_r = R > 0) give group 0 only the 2R lowest qubits,
+// which a pass mixes in two register rounds with a single transpose; the
+// tile still loads 2^tb contiguous amplitudes, and qubits [2R, n) form the
+// higher groups.
+int schedule_groups(int n, int tb, int c_min, int split_r) {
   const int gmax = tb - std::max(0, std::min(c_min, tb - 1));
-  return 1 + (n - tb + gmax - 1) / gmax;
+  const int low = split_r > 0 ? 2 * split_r : tb;
+  return 1 + (n - low + gmax - 1) / gmax;
 }
 
-std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect) {
+std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect, int split_r) {
   const int TB = tb;
   struct Grp {
-    int c, s, mix_lo;
+    int c, s, mix_lo, split;
   };
   std::vector<Grp> grp;
-  grp.push_back({TB, TB, 0});
-  const int rest = n - TB;
-  const int H = schedule_groups(n, tb, c_min) - 1;
-  int s = TB;
+  const int low = split_r > 0 ? 2 * split_r : TB;
+  grp.push_back({TB, TB, 0, split_r > 0 ? 1 : 0});
+  const int rest = n - low;
+  const int H = schedule_groups(n, tb, c_min, split_r) - 1;
+  int s = low;
   for (int h = 0; h < H; ++h) {
     const int g = rest / H + (h < rest % H ? 1 : 0);
-    grp.push_back({TB - g, s, TB - g});
+    grp.push_back({TB - g, s, TB - g, 0});
     s += g;
   }
   const int G = (int)grp.size();
@@ -419,6 +423,7 @@ std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, 
     d.c = grp[gi].c;
     d.s = grp[gi].s;
     d.mix_lo = grp[gi].mix_lo;
+    d.split = grp[gi].split;
     d.layerA = d.layerP = d.layerB = -1;
     return d;
   };
@@ -500,7 +505,7 @@ int paraqaoa_create(paraqaoa_ctx** out, int device, size_t hbm_budget) {
     // default: the 2^12 tile with 16 registers per thread (highest occupancy)
     // unless the 2^13 tile needs fewer passes
     c->c_min[n] = 3;
-    c->tile_kind[n] = (n >= kMaxTileBits && schedule_groups(n, kMinTileBits, 3) > schedule_groups(n, kMaxTileBits, 3))
+    c->tile_kind[n] = (n >= kMaxTileBits && schedule_groups(n, kMinTileBits, 3, 0) > schedule_groups(n, kMaxTileBits, 3, 0))
                           ? 2 : 1;
   }
   *out = c;
@@ -1186,8 +1191,24 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   return PARAQAOA_OK;
 }
 
+int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
+                          int32_t split) {
+  if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || (split != 0 && split != 1))
+    return PARAQAOA_E_INVAL;
+  for (int kind = 0; kind < kTileKinds; ++kind)
+    if (kTileShapes[kind].tb == tile_bits && kTileShapes[kind].r == reg_bits) {
+      if (n < tile_bits || (split && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
+      c->tile_kind[n] = (int8_t)kind;
+      c->c_min[n] = (int8_t)c_min;
+      c->split[n] = (int8_t)split;
+      c->plan.valid = false;
+      return PARAQAOA_OK;
+    }
+  return PARAQAOA_E_INVAL;
+}
+
 int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32_t* out_tile_bits,
-                      int32_t* out_reg_bits, int32_t* out_c_min) {
+                      int32_t* out_reg_bits, int32_t* out_c_min, int32_t* out_split) {
   if (!c || !pt || p < 1 || p > PARAQAOA_MAX_P) return PARAQAOA_E_INVAL;
   PQ_CUDA(cudaSetDevice(c->device));
   int rc = upload_part(c, pt, false);
@@ -1205,19 +1226,21 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
     std::vector<int32_t> ids(copies, rep);
     std::vector<double> ang(copies * p, 0.5);
     float best_ms = 1e30f;
-    int best_kind = c->tile_kind[n], best_cm = c->c_min[n];
-    std::vector<std::pair<int, int>> seen;  // (kind and groups, carried bits) already timed
+    int best_kind = c->tile_kind[n], best_cm = c->c_min[n], best_split = c->split[n];
+    std::vector<std::pair<int, int>> seen;  // (kind, groups, split; carried bits) already timed
     for (int kind = 0; kind < kTileKinds; ++kind) {
-      const int tb = kTileShapes[kind].tb;
+      const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
       if (n < tb) continue;
+      for (int sp = 0; sp <= 1; ++sp)
       for (int cm = 2; cm <= 4; ++cm) {
-        const int G = schedule_groups(n, tb, cm);
-        const auto sched = make_schedule(n, p, tb, cm, false, true);
-        const std::pair<int, int> key(G * 100 + kind, sched.size() > 1 ? sched[1].c : 0);
+        const int G = schedule_groups(n, tb, cm, sp ? r : 0);
+        const auto sched = make_schedule(n, p, tb, cm, false, true, sp ? r : 0);
+        const std::pair<int, int> key(G * 1000 + kind * 10 + sp, sched.size() > 1 ? sched[1].c : 0);
         if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
         seen.push_back(key);
         c->tile_kind[n] = (int8_t)kind;
         c->c_min[n] = (int8_t)cm;
+        c->split[n] = (int8_t)sp;
         rc = plan_build(c, pt, ids.data(), (int32_t)copies, p, PARAQAOA_SIM_EXPECT);
         if (rc == PARAQAOA_E_ADMISSION) continue;
         if (rc) break;
@@ -1235,12 +1258,14 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
           best_ms = ms;
           best_kind = kind;
           best_cm = cm;
+          best_split = sp;
         }
       }
       if (rc) break;
     }
     c->tile_kind[n] = (int8_t)best_kind;
     c->c_min[n] = (int8_t)best_cm;
+    c->split[n] = (int8_t)best_split;
     if (rc) break;
   }
   c->pool.push_back(e0);
@@ -1252,6 +1277,7 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
     if (out_tile_bits) out_tile_bits[n] = kTileShapes[c->tile_kind[n]].tb;
     if (out_reg_bits) out_reg_bits[n] = kTileShapes[c->tile_kind[n]].r;
     if (out_c_min) out_c_min[n] = c->c_min[n];
+    if (out_split) out_split[n] = c->split[n];
   }
   return PARAQAOA_OK;
 }

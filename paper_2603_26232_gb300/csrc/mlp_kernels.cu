@@ -14,15 +14,19 @@
 namespace pq {
 
 // ---------------------------------------------------------------------------
-// Features of one subgraph (kFeatures floats), from its adjacency bit-planes:
-//   [0] n / 32           [1] |E| / C(n,2)        [2] mean w / 16    [3] std w / 16
-//   [4] mean degree / n  [5] std degree / n      [6] max degree / n [7] min degree / n
-//   [8..24)  degree histogram, bin min(deg, 15), counts / n
-//   [24..40) weight histogram, bin min(w, 16) - 1, counts / max(|E|, 1)
-//   [40..56) weighted-degree histogram, bin min(15, floor(16 D_u / (max D + 1))), counts / n
-//   [56] triangles / C(n,3)   [57] total weight / (10 C(n,2))   [58..64) 0
-// One warp per subgraph, lane u owns vertex u; histogram bins are integer
-// counts from warp ballots, so every entry is one FP32 division.
+// Features of one subgraph (kFeatures floats), from its adjacency bit-planes.
+// Isolated vertices are left out (they change neither C(z)'s dependence on the
+// other qubits nor <C>, so neither the best angles); m = number of vertices
+// with at least one edge, all features 0 when m = 0:
+//   [0] m / 32           [1] |E| / C(m,2)        [2] mean w / 16    [3] std w / 16
+//   [4] mean degree / m  [5] std degree / m      [6] max degree / m [7] min degree / m
+//   [8..24)  degree histogram, bin min(deg, 15), counts / m
+//   [24..40) weight histogram, bin min(w, 16) - 1, counts / |E|
+//   [40..56) weighted-degree histogram, bin min(15, floor(16 D_u / (max D + 1))), counts / m
+//   [56] triangles / C(m,3)   [57] total weight / (10 C(m,2))   [58..64) 0
+// (degrees over the m non-isolated vertices). One warp per subgraph, lane u
+// owns vertex u; histogram bins are integer counts from warp ballots, so every
+// entry is one FP32 division.
 __global__ void k_features(const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes,
                            const int32_t* __restrict__ ids, int32_t count, float* __restrict__ out) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -31,12 +35,11 @@ __global__ void k_features(const SubDev* __restrict__ subs, const uint32_t* __re
   const SubDev S = subs[ids[w]];
   const uint32_t* pl = planes + S.plane_off;
   const int n = S.n, P = S.P;
-  const bool own = lane < n;
   int deg = 0, wdeg = 0, esum = 0, esq = 0, ecnt = 0, tri = 0;
   int whist_lane[16];
 #pragma unroll
   for (int b = 0; b < 16; ++b) whist_lane[b] = 0;
-  if (own) {
+  if (lane < n) {
     uint32_t any = 0;
     for (int b = 0; b < P; ++b) any |= pl[lane * P + b];
     deg = __popc(any);
@@ -58,6 +61,8 @@ __global__ void k_features(const SubDev* __restrict__ subs, const uint32_t* __re
       tri += __popc(any & anyv & ~((2u << v) - 1u));  // triangles u < v < x
     }
   }
+  const bool own = lane < n && deg > 0;  // a non-isolated vertex
+  const int m = __popc(__ballot_sync(0xffffffffu, own));
   auto wsum = [](int x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -74,9 +79,14 @@ __global__ void k_features(const SubDev* __restrict__ subs, const uint32_t* __re
   }
   const int dbin = min(deg, 15);
   const int wdbin = min(15, (16 * wdeg) / (wdmax + 1));
-  const float fn = (float)n, pairs = 0.5f * fn * (fn - 1.f);
-  const float triples = fn * (fn - 1.f) * (fn - 2.f) / 6.f;
   float* f = out + (int64_t)w * kFeatures;
+  if (m == 0) {  // edgeless: every feature 0
+    f[lane] = 0.f;
+    f[32 + lane] = 0.f;
+    return;
+  }
+  const float fm = (float)m, pairs = 0.5f * fm * (fm - 1.f);
+  const float triples = fm * (fm - 1.f) * (fm - 2.f) / 6.f;
   // lane b < 16 writes the three histograms' bin b; the others the scalars and zeros
   int hd = 0, hw = 0, hwd = 0;
 #pragma unroll
@@ -91,23 +101,23 @@ __global__ void k_features(const SubDev* __restrict__ subs, const uint32_t* __re
     }
   }
   if (lane < 16) {
-    f[8 + lane] = (float)hd / fn;
-    f[24 + lane] = (float)hw / (float)max(E, 1);
-    f[40 + lane] = (float)hwd / fn;
+    f[8 + lane] = (float)hd / fm;
+    f[24 + lane] = (float)hw / (float)E;
+    f[40 + lane] = (float)hwd / fm;
   } else if (lane == 16) {
-    f[0] = fn / 32.f;
-    f[1] = pairs > 0.f ? (float)E / pairs : 0.f;
-    const float mw = E > 0 ? (float)Wt / (float)E : 0.f;
+    f[0] = fm / 32.f;
+    f[1] = (float)E / pairs;
+    const float mw = (float)Wt / (float)E;
     f[2] = mw / 16.f;
-    f[3] = E > 0 ? sqrtf(fmaxf((float)Wsq / (float)E - mw * mw, 0.f)) / 16.f : 0.f;
-    const float md = (float)dsum / fn;
-    f[4] = md / fn;
-    f[5] = sqrtf(fmaxf((float)dsq / fn - md * md, 0.f)) / fn;
-    f[6] = (float)dmax / fn;
-    f[7] = (float)dmin / fn;
+    f[3] = sqrtf(fmaxf((float)Wsq / (float)E - mw * mw, 0.f)) / 16.f;
+    const float md = (float)dsum / fm;
+    f[4] = md / fm;
+    f[5] = sqrtf(fmaxf((float)dsq / fm - md * md, 0.f)) / fm;
+    f[6] = (float)dmax / fm;
+    f[7] = (float)dmin / fm;
   } else if (lane == 17) {
     f[56] = triples > 0.f ? (float)T / triples : 0.f;
-    f[57] = pairs > 0.f ? (float)Wt / (10.f * pairs) : 0.f;
+    f[57] = (float)Wt / (10.f * pairs);
   } else if (lane < 24) {
     f[58 + (lane - 18)] = 0.f;
   }

@@ -60,7 +60,7 @@ struct PassDesc {
   int32_t store;    // write the tile back
   int32_t expect;   // reduce sum |psi|^2 C into the tile partial
   int32_t last;     // the final pass (stores apply lambda_p)
-  int32_t pf;       // L2-prefetch the tile this many CTAs ahead (0: off)
+  int32_t split;    // low-group pass of a split schedule: mix local bits [0, 2R) in two rounds
 };
 
 // Kernel launchers (sim_kernels.cu). All enqueue on `st` and return the
@@ -172,7 +172,7 @@ int ctx_device(paraqaoa_ctx* c);
 int ctx_part_device(paraqaoa_ctx* c, const paraqaoa_part* pt, const SubDev** subs, const uint32_t** planes);
 
 // Pass schedule for an n-qubit instance group (layer_pass.cu host helper).
-std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect);
-int schedule_groups(int n, int tb, int c_min);
+std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect, int split_r);
+int schedule_groups(int n, int tb, int c_min, int split_r);
 
 }  // namespace pq

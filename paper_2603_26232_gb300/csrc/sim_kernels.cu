@@ -112,10 +112,24 @@ __device__ __forceinline__ uint32_t lir(uint32_t tid, uint32_t k) {
   }
 }
 
-// Local bit that thread-index bit b occupies in layout RHO (inverse of lir's thread part).
-template <int TB, int R, int RHO>
-__host__ __device__ constexpr int thread_bit_local(int b) {
-  return RHO == 0 ? b : (RHO == 1 ? (b < TB - 2 * R ? b : b + R) : b + R);
+// The same layouts named by their register-bit offset O: registers hold local
+// bits [O, O + R); thread bits fill [0, O) and [O + R, TB) in increasing order,
+// so lanes stay on the lowest local bits (coalesced HBM access) whenever O >= 5.
+// RHO 0, 1, 2 are O = TB - R, TB - 2R, 0.
+template <int TB, int R, int O>
+__device__ __forceinline__ uint32_t lir_o(uint32_t tid, uint32_t k) {
+  return (tid & ((1u << O) - 1u)) | (k << O) | ((tid >> O) << (O + R));
+}
+// Local bit that thread-index bit b occupies in the layout of offset O.
+template <int R, int O>
+__host__ __device__ constexpr int thread_bit_local_o(int b) { return b < O ? b : b + R; }
+
+// Layout offsets of the layer passes. Classic passes mix up to three rounds
+// through layouts O = TB - R, TB - 2R, 0. Split passes (the low qubit group of
+// 2R qubits) mix local bits [R, 2R) and [0, R) in two rounds with a single
+// transpose, loading and storing in O = R.
+__host__ __device__ constexpr int lay_off(int TB, int R, bool split, int rho) {
+  return split ? (rho == 0 ? R : 0) : (rho == 0 ? TB - R : (rho == 1 ? TB - 2 * R : 0));
 }
 
 __host__ __device__ __forceinline__ int slot_lbr(int TB, int R, int rho, int j) {
@@ -131,6 +145,18 @@ __device__ __forceinline__ void transposer(float2 (&a)[1 << R], float2* sm, uint
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < (1 << R); ++k) a[k] = pt[padr<R>(lir<TB, R, TO>(0, k))];
+  __syncthreads();
+}
+
+template <int TB, int R, int OF, int OT>
+__device__ __forceinline__ void transposer_o(float2 (&a)[1 << R], float2* sm, uint32_t tid) {
+  float2* pf = sm + padr<R>(lir_o<TB, R, OF>(tid, 0));
+  float2* pt = sm + padr<R>(lir_o<TB, R, OT>(tid, 0));
+#pragma unroll
+  for (int k = 0; k < (1 << R); ++k) pf[padr<R>(lir_o<TB, R, OF>(0, k))] = a[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < (1 << R); ++k) a[k] = pt[padr<R>(lir_o<TB, R, OT>(0, k))];
   __syncthreads();
 }
 
@@ -542,10 +568,10 @@ __host__ __device__ constexpr int gray_bit(int i) { return i & 1 ? 0 : (i & 2 ? 
 // Entries per instance of the k_cut_consts output: 2^R (Q_K table) + (1 + R) per thread.
 __host__ __device__ constexpr int cut_consts_stride(int tb, int r) { return (1 << r) + (1 + r) * (1 << (tb - r)); }
 
-// Per-instance cut constants of one pass, for the cut layout RC:
+// Per-instance cut constants of one pass, for the cut layout of offset OC:
 // out[0..2^R) = -2 Q_K(k); out[2^R + t] = -2 Q_J(z_J(t)); out[2^R + (1+j) NT + t] =
 // B_u(t) of register slot j.
-template <int TB, int R, int RC>
+template <int TB, int R, int OC>
 __global__ void __launch_bounds__(1 << (TB - R))
     k_cut_consts(PassDesc pd, int32_t n, const InstDev* __restrict__ inst_all,
                  const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
@@ -563,16 +589,16 @@ __global__ void __launch_bounds__(1 << (TB - R))
   if (tid < (uint32_t)KQ) {
     uint32_t zk = 0;
     for (int j = 0; j < R; ++j)
-      if ((tid >> j) & 1u) zk |= 1u << qubit_of(slot_lbr(TB, R, RC, j), c, s);
+      if ((tid >> j) & 1u) zk |= 1u << qubit_of(OC + j, c, s);
     int acc = 0;
     for (int j = 0; j < R; ++j) {
       if (!((tid >> j) & 1u)) continue;
-      const uint32_t* row = pl + qubit_of(slot_lbr(TB, R, RC, j), c, s) * P;
+      const uint32_t* row = pl + qubit_of(OC + j, c, s) * P;
       for (int b = 0; b < P; ++b) acc += __popc(row[b] & zk) << b;
     }
     o[tid] = -acc;  // each pair of set K qubits counted from both ends
   }
-  const uint32_t li0 = lir<TB, R, RC>(tid, 0);
+  const uint32_t li0 = lir_o<TB, R, OC>(tid, 0);
   uint32_t zJ = 0;
   for (int lb = 0; lb < TB; ++lb)
     if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
@@ -584,7 +610,7 @@ __global__ void __launch_bounds__(1 << (TB - R))
   }
   o[KQ + tid] = -acc;
   for (int j = 0; j < R; ++j) {
-    const uint32_t* row = pl + qubit_of(slot_lbr(TB, R, RC, j), c, s) * P;
+    const uint32_t* row = pl + qubit_of(OC + j, c, s) * P;
     int bj = 0;
     for (int b = 0; b < P; ++b) bj += __popc(row[b] & zJ) << b;
     o[KQ + (1 + j) * NT + tid] = -2 * bj;
@@ -596,7 +622,7 @@ __global__ void __launch_bounds__(1 << (TB - R))
 // four CTAs of 256 threads).
 __host__ __device__ constexpr int layer_min_blocks(int tb, int r) { return r == 4 ? 4 : (tb >= 13 ? 2 : 4); }
 
-template <int TB, int R, int NR>
+template <int TB, int R, int NR, bool SPLIT>
 __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
     k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
                  const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
@@ -605,13 +631,16 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
                  const int32_t* __restrict__ consts, uint32_t mm0, uint32_t mm1, uint32_t mm2) {
   constexpr uint32_t NT = 1u << (TB - R);
   constexpr int KQ = 1 << R;  // registers per thread
-  constexpr int RC = NR - 1;  // layout of the cut step (phase / <C>)
+  constexpr int O0 = lay_off(TB, R, SPLIT, 0), O1 = lay_off(TB, R, SPLIT, 1), O2 = lay_off(TB, R, SPLIT, 2);
+  constexpr int OC = lay_off(TB, R, SPLIT, NR - 1);  // layout of the cut step (phase / <C>)
+  static_assert(!SPLIT || NR == 2, "split passes mix two rounds");
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* tab = reinterpret_cast<float2*>(smraw);
   float2* sm = tab + tabcap;
   int* qk = reinterpret_cast<int*>(sm + padded_r<TB, R>());  // 2^R entries (<= 32)
   TileConst* tc = reinterpret_cast<TileConst*>(qk + 32);
-  double* red = reinterpret_cast<double*>(tc + 1);
+  uint32_t* pls = reinterpret_cast<uint32_t*>(tc + 1);  // the instance's bit-planes
+  double* red = reinterpret_cast<double*>(pls + PARAQAOA_MAX_QUBITS * kMaxPlanes);
   const uint32_t tid = threadIdx.x;
   const int c = pd.c, s = pd.s, g = TB - c;
   const uint32_t lowt = (uint32_t)(s - c);
@@ -623,58 +652,37 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   const bool need_cut = pd.layerP >= 0 || pd.expect;
   const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
 
-  // ---- set-up: phase table, Q_K table, tile constants (warp 0)
+  // ---- set-up. One round of global loads, all issued before the first
+  // barrier (the state loads below too): the phase table, the instance's
+  // adjacency bit-planes, the Q_K table and this thread's cut constants.
+  // After the barrier warp 0 derives the tile constants from the planes in
+  // shared memory.
   if (pd.layerP >= 0) {
     const float2* tl = tables + Ip->table_off + (int64_t)pd.layerP * (W + 1);
     for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
   }
   const int32_t* cc_inst = consts + (int64_t)li_idx * cut_consts_stride(TB, R);
-  if (need_cut && tid < 32) {
-    if (tid < (uint32_t)KQ) qk[tid] = cc_inst[tid];
-    // lane u < n: contribution of vertex u to C(z_F); lane u < TB: lam of local bit u
-    int cfu = 0;
-    if ((int)tid < n && ((zbase >> tid) & 1u)) {
-      const uint32_t* row = pl + tid * P;
-      for (int b = 0; b < P; ++b) cfu += __popc(row[b] & ~zbase) << b;
-    }
+  int ccJ = 0, ccB[R];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cfu += __shfl_xor_sync(0xffffffffu, cfu, o);
-    if (tid < (uint32_t)TB) {
-      const uint32_t* row = pl + qubit_of(tid, c, s) * P;
-      int d = 0, a = 0;
-      for (int b = 0; b < P; ++b) {
-        d += __popc(row[b]) << b;
-        a += __popc(row[b] & zbase) << b;
-      }
-      tc->lam[tid] = d - 2 * a;
-    }
-    if (tid == 0) tc->cf = cfu;
+  for (int j = 0; j < R; ++j) ccB[j] = 0;
+  if (need_cut) {
+    for (int q = tid; q < n * P; q += NT) pls[q] = pl[q];
+    if (tid < (uint32_t)KQ) qk[tid] = cc_inst[tid];
+    ccJ = cc_inst[KQ + tid];
+#pragma unroll
+    for (int j = 0; j < R; ++j) ccB[j] = cc_inst[KQ + (1 + j) * NT + tid];
   }
   // Local index -> qubit offset: local bits [0, c) are qubits [0, c), bits
   // [c, TB) move up by s - c (a monotone bit map, so it keeps popcounts).
   const uint32_t lowm = (1u << c) - 1u;
   const int sh = s - c;
   auto zmap = [&](uint32_t li) -> uint32_t { return (li & lowm) | ((li & ~lowm) << sh); };
-  // load/store layout: thread bits are local bits [0, TB - R), registers the rest
-  float2* base = states + Ip->state_off + (zbase | zmap(tid));
-
-  // L2 prefetch of the tile pd.pf CTAs ahead (the block scheduler starts CTAs
-  // in index order, so that tile is processed about pd.pf / resident CTA
-  // lifetimes from now): its 2^(TB-c) runs of 2^c contiguous amplitudes.
-  if (pd.pf > 0 && !pd.init) {
-    const uint32_t t2 = blockIdx.x + (uint32_t)pd.pf;
-    if (t2 < gridDim.x) {
-      const uint32_t tile2 = t2 & ((1u << tiles_log2) - 1u);
-      const uint32_t zb2 = ((tile2 & ((1u << lowt) - 1u)) << c) | ((tile2 >> lowt) << (s + g));
-      const float2* p2 = states + inst_all[list[t2 >> tiles_log2]].state_off + zb2;
-      for (uint32_t r = tid; r < (1u << g); r += NT)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p2 + ((size_t)r << s)), "r"(8u << c)
-                     : "memory");
-    }
-  }
+  // load/store layout O0: this thread's amplitude offsets are zmap(lt | register bits)
+  const uint32_t lt = lir_o<TB, R, O0>(tid, 0);
+  float2* base = states + Ip->state_off + (zbase | zmap(lt));
 
   float2 a[KQ];
-  const uint32_t li0 = lir<TB, R, RC>(tid, 0);
+  const uint32_t li0 = lir_o<TB, R, OC>(tid, 0);
   if (pd.init) {  // s_z = i^popcount(z), z = tile base | thread qubits | register qubits
     const int r = __popc(zbase | zmap(li0));
     const float sg = (r & 2) ? -1.f : 1.f;
@@ -684,7 +692,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   } else {
     uint32_t e[R];  // qubit offsets of the register slots
 #pragma unroll
-    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (TB - R + j));
+    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (O0 + j));
     uint32_t off = 0;
     a[0] = base[0];
 #pragma unroll
@@ -694,29 +702,50 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
       a[k] = base[off];
     }
   }
-  __syncthreads();  // phase table, Q_K and tile constants visible
+  __syncthreads();  // phase table, planes and Q_K visible
   int A = 0, kap[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) kap[j] = 0;
   if (need_cut) {
-    A = tc->cf + cc_inst[KQ + tid];
+    if (tid < 32) {
+      // lane u < n: contribution of vertex u to C(z_F); lane u < TB: lam of local bit u
+      int cfu = 0;
+      if ((int)tid < n && ((zbase >> tid) & 1u)) {
+        const uint32_t* row = pls + tid * P;
+        for (int b = 0; b < P; ++b) cfu += __popc(row[b] & ~zbase) << b;
+      }
 #pragma unroll
-    for (int b = 0; b < TB - R; ++b) A += ((tid >> b) & 1u) ? tc->lam[thread_bit_local<TB, R, RC>(b)] : 0;
+      for (int o = 16; o > 0; o >>= 1) cfu += __shfl_xor_sync(0xffffffffu, cfu, o);
+      if (tid < (uint32_t)TB) {
+        const uint32_t* row = pls + qubit_of(tid, c, s) * P;
+        int d = 0, aa = 0;
+        for (int b = 0; b < P; ++b) {
+          d += __popc(row[b]) << b;
+          aa += __popc(row[b] & zbase) << b;
+        }
+        tc->lam[tid] = d - 2 * aa;
+      }
+      if (tid == 0) tc->cf = cfu;
+    }
+    __syncthreads();  // tile constants visible
+    A = tc->cf + ccJ;
 #pragma unroll
-    for (int j = 0; j < R; ++j) kap[j] = tc->lam[slot_lbr(TB, R, RC, j)] + cc_inst[KQ + (1 + j) * NT + tid];
+    for (int b = 0; b < TB - R; ++b) A += ((tid >> b) & 1u) ? tc->lam[thread_bit_local_o<R, OC>(b)] : 0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) kap[j] = tc->lam[OC + j] + ccB[j];
   }
   // round 2 (layout 2) only ever mixes slots below TB - 2R (the others repeat layout 1's)
   constexpr uint32_t kAll = (1u << R) - 1u;
-  constexpr uint32_t kLow2 = (TB - 2 * R) >= R ? kAll : ((1u << (TB - 2 * R > 0 ? TB - 2 * R : 0)) - 1u);
+  constexpr uint32_t kLow2 = SPLIT || (TB - 2 * R) >= R ? kAll : ((1u << (TB - 2 * R > 0 ? TB - 2 * R : 0)) - 1u);
   if (pd.layerA >= 0) {
     const float muA = Ip->mu[pd.layerA];
     mix_regs_sel<R, kAll>(a, muA, mm0);
     if constexpr (NR > 1) {
-      transposer<TB, R, 0, 1>(a, sm, tid);
+      transposer_o<TB, R, O0, O1>(a, sm, tid);
       mix_regs_sel<R, kAll>(a, muA, mm1);
     }
     if constexpr (NR > 2) {
-      transposer<TB, R, 1, 2>(a, sm, tid);
+      transposer_o<TB, R, O1, O2>(a, sm, tid);
       mix_regs_sel<R, kLow2>(a, muA, mm2);
     }
   }
@@ -734,11 +763,11 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
     const float muB = Ip->mu[pd.layerB];
     if constexpr (NR > 2) {
       mix_regs_sel<R, kLow2>(a, muB, mm2);
-      transposer<TB, R, 2, 1>(a, sm, tid);
+      transposer_o<TB, R, O2, O1>(a, sm, tid);
     }
     if constexpr (NR > 1) {
       mix_regs_sel<R, kAll>(a, muB, mm1);
-      transposer<TB, R, 1, 0>(a, sm, tid);
+      transposer_o<TB, R, O1, O0>(a, sm, tid);
     }
     mix_regs_sel<R, kAll>(a, muB, mm0);
   }
@@ -759,17 +788,17 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   }
   if (pd.store) {
     if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
-      if constexpr (NR == 3) transposer<TB, R, 2, 0>(a, sm, tid);
-      if constexpr (NR == 2) transposer<TB, R, 1, 0>(a, sm, tid);
+      if constexpr (NR == 3) transposer_o<TB, R, O2, O0>(a, sm, tid);
+      if constexpr (NR == 2) transposer_o<TB, R, O1, O0>(a, sm, tid);
     }
     if (pd.last) {  // back from the gauge, times lambda_p
-      const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zmap(tid)));
+      const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zmap(lt)));
 #pragma unroll
       for (int k = 0; k < KQ; ++k) a[k] = cmul(a[k], rot_i(fs, -popc_c(k)));
     }
     uint32_t e[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (TB - R + j));
+    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (O0 + j));
     uint32_t off = 0;
     base[0] = a[0];
 #pragma unroll
@@ -785,7 +814,7 @@ size_t layer_pass_smem(int kind, int tabcap) {
   const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
   const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - r));
   return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
-         16 * sizeof(double);
+         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 16 * sizeof(double);
 }
 
 int layer_resident_per_sm(int kind) { return layer_min_blocks(kTileShapes[kind].tb, kTileShapes[kind].r); }
@@ -795,14 +824,15 @@ int64_t cut_consts_elems(int kind, int32_t nlist) {
 }
 
 static int pass_rounds(int tb, int r, const PassDesc& pd) {
+  if (pd.split) return 2;
   return 1 + (pd.mix_lo < tb - r) + (pd.mix_lo < tb - 2 * r);
 }
 
-template <int TB, int R, int RC>
+template <int TB, int R, int OC>
 static cudaError_t launch_cc_t(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                                int32_t nlist, const SubDev* subs, const uint32_t* planes,
                                int32_t* consts, cudaStream_t st) {
-  k_cut_consts<TB, R, RC><<<nlist, 1 << (TB - R), 0, st>>>(pd, n, inst, list, subs, planes, consts);
+  k_cut_consts<TB, R, OC><<<nlist, 1 << (TB - R), 0, st>>>(pd, n, inst, list, subs, planes, consts);
   return cudaGetLastError();
 }
 
@@ -815,9 +845,10 @@ cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev
 #define PQ_CC(TBV, RV) \
   do { \
     if (tb == TBV && r == RV) { \
-      if (rc == 0) return launch_cc_t<TBV, RV, 0>(n, pd, inst, list, nlist, subs, planes, consts, st); \
-      if (rc == 1) return launch_cc_t<TBV, RV, 1>(n, pd, inst, list, nlist, subs, planes, consts, st); \
-      return launch_cc_t<TBV, RV, 2>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      if (pd.split) return launch_cc_t<TBV, RV, lay_off(TBV, RV, true, 1)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      if (rc == 0) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 0)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      if (rc == 1) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 1)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 2)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
     } \
   } while (0)
   PQ_CC(12, 5);
@@ -827,13 +858,13 @@ cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev
   return cudaErrorInvalidValue;
 }
 
-template <int TB, int R, int NR>
+template <int TB, int R, int NR, bool SPLIT>
 static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const InstDev* inst,
                                   const int32_t* list, int32_t nlist, const SubDev* subs,
                                   const uint32_t* planes, const float2* tables, float2* states,
                                   double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
   const size_t smem = layer_pass_smem(kind, tabcap);
-  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, R, NR>,
+  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, R, NR, SPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles_log2 = n - TB;
@@ -842,11 +873,11 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
   // register slots each round mixes (mm0: layout 0, mm1: layout 1, mm2: layout 2)
   uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
   for (int j = 0; j < R; ++j) {
-    if (TB - R + j >= pd.mix_lo) mm0 |= 1u << j;
-    if (TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
-    if (j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
+    if (SPLIT || TB - R + j >= pd.mix_lo) mm0 |= 1u << j;
+    if (SPLIT || TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
+    if (!SPLIT && j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
   }
-  k_layer_pass<TB, R, NR><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
+  k_layer_pass<TB, R, NR, SPLIT><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
       pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts, mm0, mm1, mm2);
   return cudaGetLastError();
 }
@@ -863,9 +894,10 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
 #define PQ_LAUNCH(TBV, RV) \
   do { \
     if (tb == TBV && r == RV) { \
-      if (nr == 1) return launch_layer_t<TBV, RV, 1>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
-      if (nr == 2) return launch_layer_t<TBV, RV, 2>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
-      return launch_layer_t<TBV, RV, 3>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      if (pd.split) return launch_layer_t<TBV, RV, 2, true>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      if (nr == 1) return launch_layer_t<TBV, RV, 1, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      if (nr == 2) return launch_layer_t<TBV, RV, 2, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      return launch_layer_t<TBV, RV, 3, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
     } \
   } while (0)
   PQ_LAUNCH(12, 5);

@@ -357,8 +357,8 @@ def test_autotune_choices_keep_parity(api, orc):
     try:
         choice = capi.paraqaoa_autotune(ctx, part, 2)
         for n in sizes:
-            tb, rb, cm = choice[n]
-            assert (tb, rb) in ((12, 5), (12, 4), (13, 5)) and cm in (2, 3, 4)
+            tb, rb, cm, sp = choice[n]
+            assert (tb, rb) in ((12, 5), (12, 4), (13, 5)) and cm in (2, 3, 4) and sp in (0, 1)
         subs = oracle_parts(orc, g, sizes)
         ids = np.arange(len(sizes), dtype=np.int32)
         gam, bet = synth.random_angles(len(sizes), 2, 99)
@@ -369,4 +369,34 @@ def test_autotune_choices_keep_parity(api, orc):
             assert np.max(np.abs(capi.paraqaoa_state(ctx, i, s.n) - ref)) <= AMP_TOL
             assert abs(ex[i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL
     finally:
+        capi.paraqaoa_part_free(part)
+
+
+@pytest.mark.parametrize("tb,rb,split", [(12, 5, 0), (12, 4, 0), (13, 5, 0), (12, 5, 1), (12, 4, 1), (13, 5, 1)])
+def test_every_schedule_matches_oracle(api, orc, tb, rb, split):
+    """Every tile shape in classic and split schedules, on parts of 15..24
+    qubits (two and three qubit groups), depth 3, states kept."""
+    capi, ctx = api
+    sizes = [15, 16, 19, 20, 21, 23, 24]
+    g = chain_graph(sizes, 0.3, 40 + tb + rb + split, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        for n in sizes:
+            capi.paraqaoa_set_schedule(ctx, n, tb, rb, 3, split)
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), 3, 123 + split)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+        ex = capi.paraqaoa_expect(ctx, len(ids))
+        for i, s in enumerate(subs):
+            ref = orc.simulate(s, gam[i], bet[i])
+            assert np.max(np.abs(capi.paraqaoa_state(ctx, i, s.n) - ref)) <= AMP_TOL, (s.n,)
+            assert abs(ex[i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL, (s.n,)
+        # <C> without kept states takes the expect-only last pass
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+        ex2 = capi.paraqaoa_expect(ctx, len(ids))
+        assert np.all(np.abs(ex2 - ex) <= 1e-9 * np.abs(ex))
+    finally:
+        for n in sizes:
+            capi.paraqaoa_set_schedule(ctx, n, 12, 4, 3, 0)
         capi.paraqaoa_part_free(part)

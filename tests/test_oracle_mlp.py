@@ -93,33 +93,30 @@ def test_bf16_forward_close_to_fp64_forward():
 
 def test_features_against_networkx():
     nx = pytest.importorskip("networkx")
-    for seed, (n, pe, wmax) in enumerate([(12, 0.3, 10), (9, 0.8, 3), (15, 0.1, 1), (6, 0.0, 1)]):
+    for seed, (n, pe, wmax) in enumerate([(12, 0.3, 10), (9, 0.8, 3), (15, 0.1, 1), (20, 0.05, 1)]):
         g = synth.erdos_renyi(n, pe, seed, wmax=wmax)
         f = mlp.features(n, g.eu, g.ev, g.ew)
         G = nx.Graph()
-        G.add_nodes_from(range(n))
         for a, b, w in zip(g.eu, g.ev, g.ew):
-            G.add_edge(int(a), int(b), weight=int(w))
-        deg = np.array([G.degree(v) for v in range(n)])
-        wdeg = np.array([G.degree(v, weight="weight") for v in range(n)])
-        assert f[0] == n / 32
+            G.add_edge(int(a), int(b), weight=int(w))   # only vertices with edges
+        m = G.number_of_nodes()
+        assert m > 0
+        deg = np.array([d for _, d in G.degree()])
+        wdeg = np.array([d for _, d in G.degree(weight="weight")])
+        ws = np.array([w for _, _, w in G.edges(data="weight")])
+        assert f[0] == m / 32
         assert np.isclose(f[1], nx.density(G))
-        assert np.isclose(f[4], deg.mean() / n) and np.isclose(f[5], deg.std() / n)
-        assert f[6] == deg.max() / n and f[7] == deg.min() / n
-        assert np.isclose(f[8:24].sum(), 1.0)
+        assert np.isclose(f[2], ws.mean() / 16) and np.isclose(f[3], ws.std() / 16)
+        assert np.isclose(f[4], deg.mean() / m) and np.isclose(f[5], deg.std() / m)
+        assert f[6] == deg.max() / m and f[7] == deg.min() / m
+        assert np.isclose(f[8:24].sum(), 1.0) and f[8] == 0.0
         for b in range(16):
-            want = np.sum(np.minimum(deg, 15) == b) / n
-            assert np.isclose(f[8 + b], want)
-        for b in range(16):
-            want = np.sum(np.minimum(wdeg * 16 // (wdeg.max() + 1), 15) == b) / n
-            assert np.isclose(f[40 + b], want)
+            assert np.isclose(f[8 + b], np.sum(np.minimum(deg, 15) == b) / m)
+            assert np.isclose(f[40 + b], np.sum(np.minimum(wdeg * 16 // (wdeg.max() + 1), 15) == b) / m)
+        assert np.isclose(f[24:40].sum(), 1.0)
         tri = sum(nx.triangles(G).values()) // 3
-        assert np.isclose(f[56], tri / (n * (n - 1) * (n - 2) / 6))
-        if g.num_edges:
-            ws = np.array([w for _, _, w in G.edges(data="weight")])
-            assert np.isclose(f[2], ws.mean() / 16) and np.isclose(f[3], ws.std() / 16)
-            assert np.isclose(f[24:40].sum(), 1.0)
-            assert np.isclose(f[57], ws.sum() / (10 * n * (n - 1) / 2))
+        assert np.isclose(f[56], tri / (m * (m - 1) * (m - 2) / 6) if m > 2 else 0.0)
+        assert np.isclose(f[57], ws.sum() / (10 * m * (m - 1) / 2))
         assert np.all(f[58:] == 0)
 
 
@@ -131,10 +128,20 @@ def test_features_closed_forms():
     f = mlp.features(n, g.eu, g.ev, g.ew)
     assert f[1] == 1.0 and f[56] == 1.0 and f[8 + n - 1] == 1.0
     assert np.isclose(f[2], 1 / 16) and f[3] == 0.0 and f[24] == 1.0
-    # edgeless graph: all zero except n / 32 and the zero-degree bins
-    f0 = mlp.features(5, [], [], [])
-    assert f0[0] == 5 / 32 and f0[8] == 1.0 and f0[40] == 1.0
-    assert np.count_nonzero(f0) == 3
+    # a single edge: m = 2, density 1, both degrees 1
+    f1 = mlp.features(5, [1], [3], [4])
+    assert f1[0] == 2 / 32 and f1[1] == 1.0 and f1[9] == 1.0 and f1[24 + 3] == 1.0
+    # edgeless graph: all zero
+    assert np.count_nonzero(mlp.features(5, [], [], [])) == 0
+
+
+def test_features_ignore_isolated_vertices():
+    # isolated vertices change neither <C> nor the best angles, nor the features
+    g = synth.erdos_renyi(10, 0.4, 3, wmax=10)
+    f = mlp.features(10, g.eu, g.ev, g.ew)
+    perm = np.array([0, 3, 5, 7, 11, 12, 14, 17, 20, 23])   # spread over 26 vertices
+    f2 = mlp.features(26, perm[g.eu], perm[g.ev], g.ew)
+    np.testing.assert_array_equal(f, f2)
 
 
 def test_chain_of_graphs_parts_are_the_graphs():
