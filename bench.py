@@ -181,7 +181,12 @@ def run_layer_case(args):
     ids = np.repeat(np.arange(M, dtype=np.int32), 8)
     gam, bet = synth.random_angles(len(ids), 2, 3)
     capi.paraqaoa_part_upload(ctx, part)
-    tuned = {20: (None, None, None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
+    if args.sched:
+        tb, rb, cm, sp = (int(x) for x in args.sched.split(","))
+        capi.paraqaoa_set_schedule(ctx, 20, tb, rb, cm, sp)
+        tuned = {20: (tb, rb, cm, sp)}
+    else:
+        tuned = {20: (None, None, None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
     for it in range(args.iters):
         if it == args.iters - 1:
             capi.paraqaoa_profile_enable(ctx, True)
@@ -220,6 +225,34 @@ def train_large_model(capi, ctx, depth=LARGE_DEPTH, count=2048, epochs=100, seed
     net = capi.paraqaoa_mlp_create(ctx, depth, synth.mlp_init(depth, seed))
     losses = capi.paraqaoa_mlp_train(net, X, T, epochs, 128, 1e-3, synth.epoch_orders(count, epochs, seed))
     return net, time.perf_counter() - t0, float(losses[-1])
+
+
+def large_learned(capi, pkg):
+    """16,000-vertex time-to-cut of the learned form (network trained first,
+    outside the clock); the plain form's time on the same workload takes
+    minutes and is measured by --case large."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    solver = pkg.Solver(device=torch.cuda.current_device(), hbm_budget=int(0.6 * free))
+    g = synth.erdos_renyi(LARGE_N, LARGE_P_EDGE, 0, wmax=1)
+    G = capi.Graph.of(g)
+    net, train_s, _ = train_large_model(capi, solver.ctx)
+    cfg = pkg.SolveConfig(M=LARGE_M, K=LARGE_K, p=LARGE_DEPTH, beam=LARGE_BEAM, mlp=net,
+                          fallback_steps=STEPS_ADAM, judge_tol=LARGE_JUDGE_TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = solver.solve(G, cfg)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    capi.paraqaoa_mlp_free(net)
+    solver.close()
+    return {"workload": f"G({LARGE_N},{LARGE_P_EDGE}) unit weights, seed 0; {LARGE_M} parts of 25-26 qubits; "
+                        f"p={LARGE_DEPTH}; top-{LARGE_K}; beam-{LARGE_BEAM}",
+            "form": "learned angles + judge + plain fallback", "time_to_cut_s": dt, "cut": int(r.cut),
+            "train_s": train_s, "verdicts": {"network": int(np.sum(r.fallback == 0)),
+                                             "plain_fallback": int(np.sum(r.fallback == 1)),
+                                             "reference": int(np.sum(r.fallback == 2))},
+            "plain_form": "measured by bench.py --case large"}
 
 
 def run_large_case(args):
@@ -279,6 +312,9 @@ def main():
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--sched", default="", help="fixed schedule of the 20-qubit parts instead of the autotuner: "
+                                                "tile_bits,reg_bits,c_min,split")
+    ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex learned-form time-to-cut")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the context's default tile choice (fixed launch sequence for ncu)")
     args = ap.parse_args()
@@ -313,10 +349,15 @@ def main():
     cfg = pkg.SolveConfig(M=M, K=K, p=P_FINAL, grid_points=GRID, adam_steps=STEPS_ADAM, beam=BEAM)
     # tile size per qubit count, measured once on this GPU (outside the timed region)
     tuned = {}
-    for G in Gs:
-        part = capi.paraqaoa_partition(G, M)
-        tuned = capi.paraqaoa_autotune(solver.ctx, part, P_FINAL)
-        capi.paraqaoa_part_free(part)
+    if args.sched:  # a fixed schedule (e.g. to repeat a tuned run's launches under a profiler)
+        tb, rb, cm, sp = (int(x) for x in args.sched.split(","))
+        capi.paraqaoa_set_schedule(solver.ctx, 20, tb, rb, cm, sp)
+        tuned = {20: (tb, rb, cm, sp)}
+    else:
+        for G in Gs:
+            part = capi.paraqaoa_partition(G, M)
+            tuned = capi.paraqaoa_autotune(solver.ctx, part, P_FINAL)
+            capi.paraqaoa_part_free(part)
 
     def step():
         return [solver.solve(G, cfg) for G in Gs]
@@ -355,6 +396,9 @@ def main():
         t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms, e2e_s = float(t[0]), float(t[1])
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_learned(capi, pkg)
     amps_step = amp_layers_per_graph() * len(graphs)
     value = amps_step * args.steps * world / (ms / 1e3)
     e2e_value = amps_step * args.steps * world / e2e_s
@@ -387,6 +431,7 @@ def main():
             "autotune": {str(n): {"tile_bits": tb, "reg_bits": rb, "min_run_qubits": cm, "split": sp}
                          for n, (tb, rb, cm, sp) in tuned.items() if n == 20},
             "cpu_baseline": cb,
+            "time_to_cut_16k": large,
         }
         print(json.dumps(line), flush=True)
     solver.close()
