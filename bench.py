@@ -255,6 +255,121 @@ def large_learned(capi, pkg):
             "plain_form": "measured by bench.py --case large"}
 
 
+def run_sweep_case(args):
+    """Amplitude-layer sweep over qubit counts: for n = 14..26, a batch of
+    parts of n vertices (G(*, 0.3) chain, weights 1..10) with sum 2^n >= 2^28
+    amplitudes, p = 2, <C> only, schedule chosen by the autotuner; reports
+    amplitude-layers/s and the layer passes' achieved bandwidth against the
+    measured HBM peak (n <= 14 stays on chip and has no HBM roofline)."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    ctx = capi.paraqaoa_create(0)
+    peak, kind = read_peaks()
+    for n in range(args.sweep_lo, args.sweep_hi + 1):
+        count = max(1, (1 << 28) >> n)
+        sizes = [n] * min(count, 64)
+        nv = int(sum(sizes) - (len(sizes) - 1))
+        g = synth.erdos_renyi(nv, 0.3 if n < 24 else 0.2, 7, wmax=10)
+        part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+        ids = np.resize(np.arange(len(sizes), dtype=np.int32), count)
+        gam, bet = synth.random_angles(count, 2, 11)
+        tuned = capi.paraqaoa_autotune(ctx, part, 2).get(n) if n >= 15 else None
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)  # warm-up
+        capi.paraqaoa_expect(ctx, count)
+        capi.paraqaoa_profile_enable(ctx, True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+            capi.paraqaoa_expect(ctx, count)
+        dt = time.perf_counter() - t0
+        lp = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
+        sm = capi.paraqaoa_profile_read(ctx, capi.KCLASS_SMEM_SIM)
+        dev_ms = sum(capi.paraqaoa_profile_read(ctx, k)[1] for k in range(6))
+        capi.paraqaoa_profile_enable(ctx, False)
+        amp_layers = reps * count * (1 << n) * 2
+        rate = amp_layers / (dev_ms / 1e3)
+        line = {"case": "sweep", "qubits": n, "instances": count, "p": 2,
+                "amp_layers_per_s": rate, "wall_amp_layers_per_s": amp_layers / dt,
+                "roofline_frac_16B": rate * 16 / (peak * 1e9), "schedule": tuned}
+        if lp[0]:
+            gbs = lp[2] / (lp[1] / 1e3) / 1e9
+            line.update({"layer_passes": int(lp[0] // reps), "layer_pass_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                         "hbm_bytes_per_amp_layer": lp[2] / amp_layers})
+        else:
+            line.update({"on_chip_ms": sm[1] / reps})
+        print(json.dumps(line), flush=True)
+        capi.paraqaoa_part_free(part)
+    capi.paraqaoa_destroy(ctx)
+
+
+def run_learned_case(args):
+    """Learned-angle configuration: random subgraphs of 12..20 vertices from
+    G(n, P), P in [0.05, 0.5], weights in {1..10} (and the same with unit
+    weights), labelled by the plain form at p = 1..3; the 64-256-256-2p
+    network trained on the GPU; on held-out subgraphs the <C> sum ratio to the
+    plain form's angles of the prediction alone, of the best constant
+    prediction (mean label) and of the judged learned form."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    solver = pkg.Solver()
+    ctx = solver.ctx
+    ntr, nte, epochs = args.train_count, args.test_count, 60
+    out = {"case": "learned", "train": ntr, "held_out": nte, "epochs": epochs, "results": []}
+    for wmax in (10, 1):
+        def make(count, seed):
+            specs = synth.graph_specs(count, 12, 20, 0.05, 0.5, seed)
+            G, sizes = synth.chain_of_graphs(specs, wmax=wmax)
+            part = capi.paraqaoa_partition(capi.Graph.of(G), len(sizes), capi.PART_SIZES, sizes)
+            return part, np.arange(len(sizes), dtype=np.int32)
+        ptr, itr = make(ntr, 1)
+        pte, ite = make(nte, 100000)
+        Xtr = capi.paraqaoa_features(ctx, ptr, itr)
+        Xte = capi.paraqaoa_features(ctx, pte, ite)
+        for p in (1, 2, 3):
+            t0 = time.perf_counter()
+            gl, bl, _ = capi.paraqaoa_solve_plain(ctx, ptr, itr, p, STEPS_ADAM)
+            t_label = time.perf_counter() - t0
+            T = np.concatenate([gl, bl], axis=1).astype(np.float32)
+            net = capi.paraqaoa_mlp_create(ctx, p, synth.mlp_init(p, 0))
+            t0 = time.perf_counter()
+            losses = capi.paraqaoa_mlp_train(net, Xtr, T, epochs, 256, 1e-3, synth.epoch_orders(ntr, epochs, 1))
+            t_train = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gp, bp, vp = capi.paraqaoa_solve_plain(ctx, pte, ite, p, STEPS_ADAM)
+            t_plain = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            gq, bq, vq, fb = capi.paraqaoa_solve_learned(ctx, pte, ite, net, p, STEPS_ADAM, 0.0)
+            t_learned = time.perf_counter() - t0
+            g0, b0 = capi.paraqaoa_mlp_predict(net, p, Xte)
+            capi.paraqaoa_simulate_batch(ctx, pte, ite, p, g0, b0)
+            v0 = capi.paraqaoa_expect(ctx, nte)
+            rg, rb = capi.paraqaoa_mlp_reference(net, p)
+            capi.paraqaoa_simulate_batch(ctx, pte, ite, p, np.tile(rg, (nte, 1)), np.tile(rb, (nte, 1)))
+            vr = capi.paraqaoa_expect(ctx, nte)
+            capi.paraqaoa_mlp_free(net)
+            m = vp > 0
+            r = {"weights": f"1..{wmax}", "p": p, "label_s": t_label, "train_s": t_train, "final_loss": float(losses[-1]),
+                 "ratio_prediction": float(v0[m].sum() / vp[m].sum()),
+                 "ratio_mean_label": float(vr[m].sum() / vp[m].sum()),
+                 "ratio_learned_form": float(vq[m].sum() / vp[m].sum()),
+                 "fallback_frac": float(np.mean(fb == 1)), "plain_s": t_plain, "learned_s": t_learned}
+            out["results"].append(r)
+            print(json.dumps(r), flush=True)
+        capi.paraqaoa_part_free(ptr)
+        capi.paraqaoa_part_free(pte)
+    solver.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_large_case(args):
     """16,000-vertex time-to-cut: G(16000, 0.01), unit weights, 640 parts of
     25-26 qubits (complex64 states of 256-512 MB, batched by the device-memory
@@ -308,7 +423,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-only", action="store_true", help="large case: skip the plain form")
-    ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large"],
+    ap.add_argument("--train-count", type=int, default=20000, help="learned case: training subgraphs")
+    ap.add_argument("--test-count", type=int, default=2000, help="learned case: held-out subgraphs")
+    ap.add_argument("--sweep-lo", type=int, default=14)
+    ap.add_argument("--sweep-hi", type=int, default=26)
+    ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large", "learned", "sweep"],
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
@@ -327,6 +446,10 @@ def main():
         return run_layer_case(args)
     if args.case == "large":
         return run_large_case(args)
+    if args.case == "learned":
+        return run_learned_case(args)
+    if args.case == "sweep":
+        return run_sweep_case(args)
 
     import torch
     import paper_2603_26232_gb300 as pkg
