@@ -471,19 +471,24 @@ def main():
     Gs = [capi.Graph.of(g) for g in graphs]
     cfg = pkg.SolveConfig(M=M, K=K, p=P_FINAL, grid_points=GRID, adam_steps=STEPS_ADAM, beam=BEAM)
     # tile size per qubit count, measured once on this GPU (outside the timed region)
-    tuned = {}
-    if args.sched:  # a fixed schedule (e.g. to repeat a tuned run's launches under a profiler)
-        tb, rb, cm, sp = (int(x) for x in args.sched.split(","))
-        capi.paraqaoa_set_schedule(solver.ctx, 20, tb, rb, cm, sp)
-        tuned = {20: (tb, rb, cm, sp)}
-    else:
-        for G in Gs:
+    # schedule of the 20-qubit parts per graph (the two densities have different
+    # phase-table sizes and cut structure), measured once on this GPU outside
+    # the timed region, or fixed (e.g. to repeat a tuned run's launches under a profiler)
+    sched = []
+    for G in Gs:
+        if args.sched:
+            sched.append(tuple(int(x) for x in args.sched.split(",")))
+        else:
             part = capi.paraqaoa_partition(G, M)
-            tuned = capi.paraqaoa_autotune(solver.ctx, part, P_FINAL)
+            sched.append(capi.paraqaoa_autotune(solver.ctx, part, P_FINAL)[20])
             capi.paraqaoa_part_free(part)
 
     def step():
-        return [solver.solve(G, cfg) for G in Gs]
+        out = []
+        for G, sc in zip(Gs, sched):
+            capi.paraqaoa_set_schedule(solver.ctx, 20, *sc)
+            out.append(solver.solve(G, cfg))
+        return out
 
     for _ in range(max(3, args.warmup)):
         res = step()
@@ -551,8 +556,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(total_launches),
             "clocks": clk,
-            "autotune": {str(n): {"tile_bits": tb, "reg_bits": rb, "min_run_qubits": cm, "split": sp}
-                         for n, (tb, rb, cm, sp) in tuned.items() if n == 20},
+            "schedule_20_qubits": [{"graph": f"G({NV},{pe})", "tile_bits": sc[0], "reg_bits": sc[1],
+                                    "min_run_qubits": sc[2], "split": sc[3]} for pe, sc in zip(DENSITIES, sched)],
             "cpu_baseline": cb,
             "time_to_cut_16k": large,
         }

@@ -125,6 +125,8 @@ struct paraqaoa_ctx {
   DevBuf o_vals, o_best, o_theta, o_m, o_v, o_w, o_g2, o_b2;
   // tensor-core variant: device error flag of its bounded waits
   DevBuf d_tc_err;
+  // Adam step counter on the device (read by the update kernel)
+  DevBuf o_step;
   // profiling
   bool prof = false;
   std::vector<ProfRec> pending;
@@ -528,7 +530,7 @@ void paraqaoa_destroy(paraqaoa_ctx* c) {
                     &c->m_key, &c->m_path, &c->m_sides[0], &c->m_sides[1], &c->m_score[0],
                     &c->m_score[1], &c->m_rank[0], &c->m_rank[1], &c->m_r2s[0], &c->m_r2s[1],
                     &c->m_keys, &c->m_nb, &c->o_vals, &c->o_best, &c->o_theta, &c->o_m, &c->o_v,
-                    &c->o_w, &c->o_g2, &c->o_b2, &c->d_consts, &c->d_tc_err};
+                    &c->o_w, &c->o_g2, &c->o_b2, &c->d_consts, &c->d_tc_err, &c->o_step};
   for (DevBuf* b : bufs) b->release();
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
@@ -1027,6 +1029,7 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
   PQ_CUDA(c->o_m.ensure(sizeof(double) * count * D));
   PQ_CUDA(c->o_v.ensure(sizeof(double) * count * D));
   PQ_CUDA(c->o_w.ensure(sizeof(double) * count));
+  PQ_CUDA(c->o_step.ensure(sizeof(int32_t)));
   PQ_CUDA(cudaMemcpyAsync(c->o_theta.p, theta.data(), sizeof(double) * count * D, cudaMemcpyHostToDevice, c->stream));
   PQ_CUDA(cudaMemcpyAsync(c->o_w.p, wsum.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
   PQ_CUDA(cudaMemsetAsync(c->o_m.p, 0, sizeof(double) * count * D, c->stream));
@@ -1049,15 +1052,43 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
     double* mm = c->o_m.as<double>() + (size_t)s0 * D;
     double* vv = c->o_v.as<double>() + (size_t)s0 * D;
     const double* ww = c->o_w.as<double>() + s0;
-    for (int32_t t = 1; t <= steps; ++t) {
+    int32_t* step = c->o_step.as<int32_t>();
+    PQ_CUDA(cudaMemsetAsync(step, 0, sizeof(int32_t), c->stream));
+    // one Adam step: shifted angles (and the step counter), the batch, the update
+    auto one_step = [&]() -> int {
       {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-        PQ_CUDA(launch_adam_shifts(th, ns, p, h, c->d_gamma.as<double>(), c->d_beta.as<double>(), c->stream));
+        PQ_CUDA(launch_adam_shifts(th, ns, p, h, c->d_gamma.as<double>(), c->d_beta.as<double>(), step, c->stream));
       }
-      rc = plan_run(c);
-      if (rc) return rc;
+      int r = plan_run(c);
+      if (r) return r;
       ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-      PQ_CUDA(launch_adam_update(c->d_expect.as<double>(), ww, ns, p, h, lr, t, th, mm, vv, c->stream));
+      PQ_CUDA(launch_adam_update(c->d_expect.as<double>(), ww, ns, p, h, lr, step, th, mm, vv, c->stream));
+      return PARAQAOA_OK;
+    };
+    if ((rc = one_step())) return rc;  // the first step also sizes every buffer
+    if (steps > 1 && !c->prof) {
+      // the remaining steps replay one captured step as a CUDA graph (the
+      // launches depend only on device data: angles, counter, moments)
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      PQ_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+      rc = one_step();
+      cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      PQ_CUDA(ce);
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      PQ_CUDA(ce);
+      for (int32_t t = 2; t <= steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec, c->stream);
+      cudaGraphExecDestroy(exec);
+      PQ_CUDA(ce);
+    } else {
+      for (int32_t t = 2; t <= steps; ++t)
+        if ((rc = one_step())) return rc;
     }
     s0 += ns;
   }
@@ -1217,13 +1248,14 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
   const bool prof = c->prof;
   c->prof = false;
   for (int n = kSmemMaxQubits + 1; n <= PARAQAOA_MAX_QUBITS; ++n) {
-    int32_t rep = -1;
-    for (int32_t i = 0; i < pt->M && rep < 0; ++i)
-      if (pt->size[i] == n && pt->weight[i] <= PARAQAOA_MAX_SUBGRAPH_WEIGHT) rep = i;
-    if (rep < 0) continue;
-    // enough copies of one part that the batch streams >= 1 GB (well past L2)
+    std::vector<int32_t> reps;  // every part of this size (their phase tables and cut structure differ)
+    for (int32_t i = 0; i < pt->M; ++i)
+      if (pt->size[i] == n && pt->weight[i] <= PARAQAOA_MAX_SUBGRAPH_WEIGHT) reps.push_back(i);
+    if (reps.empty()) continue;
+    // the parts cycled until the batch streams >= 1 GB (well past L2)
     const int64_t copies = std::max<int64_t>(1, std::min<int64_t>(256, (int64_t(1) << 30) / (int64_t(8) << n)));
-    std::vector<int32_t> ids(copies, rep);
+    std::vector<int32_t> ids(copies);
+    for (int64_t k = 0; k < copies; ++k) ids[k] = reps[k % reps.size()];
     std::vector<double> ang(copies * p, 0.5);
     struct Cand {
       int kind, cm, sp;

@@ -34,9 +34,12 @@ __global__ void k_grid_argmax(const double* __restrict__ vals, int32_t S, int32_
 
 // Angles of the 4p shifted evaluations per subgraph: theta +- h e_k, in the
 // order (k = 0, +), (k = 0, -), (k = 1, +), ... ; theta = (gamma_0..p-1, beta_0..p-1).
+// Also advances the Adam step counter *step (read by k_adam_update), so that
+// one captured step can be replayed as a CUDA graph.
 __global__ void k_adam_shifts(const double* __restrict__ theta, int32_t S, int32_t p, double h,
-                              double* __restrict__ gamma, double* __restrict__ beta) {
+                              double* __restrict__ gamma, double* __restrict__ beta, int32_t* __restrict__ step) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *step += 1;
   const int E = 4 * p;
   if (t >= (int64_t)S * E) return;
   const int s = (int)(t / E), e = (int)(t % E);
@@ -50,10 +53,11 @@ __global__ void k_adam_shifts(const double* __restrict__ theta, int32_t S, int32
 }
 
 __global__ void k_adam_update(const double* __restrict__ expect, const double* __restrict__ wsum,
-                              int32_t S, int32_t p, double h, double lr, int32_t t,
+                              int32_t S, int32_t p, double h, double lr, const int32_t* __restrict__ step,
                               double* __restrict__ theta, double* __restrict__ m,
                               double* __restrict__ v) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = *step;
   const int D = 2 * p;
   if (q >= (int64_t)S * D) return;
   const int s = (int)(q / D), k = (int)(q % D);
@@ -90,15 +94,15 @@ cudaError_t launch_grid_argmax(const double* vals, int32_t S, int32_t points, do
 }
 
 cudaError_t launch_adam_shifts(const double* theta, int32_t S, int32_t p, double h, double* gamma,
-                               double* beta, cudaStream_t st) {
-  k_adam_shifts<<<nblk((int64_t)S * 4 * p, 128), 128, 0, st>>>(theta, S, p, h, gamma, beta);
+                               double* beta, int32_t* step, cudaStream_t st) {
+  k_adam_shifts<<<nblk((int64_t)S * 4 * p, 128), 128, 0, st>>>(theta, S, p, h, gamma, beta, step);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adam_update(const double* expect, const double* wsum, int32_t S, int32_t p,
-                               double h, double lr, int32_t t, double* theta, double* m, double* v,
+                               double h, double lr, const int32_t* step, double* theta, double* m, double* v,
                                cudaStream_t st) {
-  k_adam_update<<<nblk((int64_t)S * 2 * p, 128), 128, 0, st>>>(expect, wsum, S, p, h, lr, t, theta, m, v);
+  k_adam_update<<<nblk((int64_t)S * 2 * p, 128), 128, 0, st>>>(expect, wsum, S, p, h, lr, step, theta, m, v);
   return cudaGetLastError();
 }
 

@@ -127,9 +127,9 @@ cudaError_t launch_beam_level(const MergeDev& md, int32_t l, int32_t nb, int64_t
 cudaError_t launch_grid_argmax(const double* vals, int32_t S, int32_t points, double* gamma,
                                double* beta, double* best, cudaStream_t st);
 cudaError_t launch_adam_shifts(const double* theta, int32_t S, int32_t p, double h,
-                               double* gamma, double* beta, cudaStream_t st);
+                               double* gamma, double* beta, int32_t* step, cudaStream_t st);
 cudaError_t launch_adam_update(const double* expect, const double* wsum, int32_t S, int32_t p,
-                               double h, double lr, int32_t t, double* theta, double* m, double* v,
+                               double h, double lr, const int32_t* step, double* theta, double* m, double* v,
                                cudaStream_t st);
 cudaError_t launch_theta_split(const double* theta, int32_t S, int32_t p, double* gamma,
                                double* beta, cudaStream_t st);

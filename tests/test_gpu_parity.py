@@ -400,3 +400,59 @@ def test_every_schedule_matches_oracle(api, orc, tb, rb, split):
         for n in sizes:
             capi.paraqaoa_set_schedule(ctx, n, 12, 4, 3, 0)
         capi.paraqaoa_part_free(part)
+
+
+def test_large_parts_full_size(api, orc):
+    """Parts of 25 and 26 qubits (the 16,000-vertex workload's sizes, 256 and
+    512 MB complex64 states), p = 2, in the split schedule the autotuner picks
+    there (three qubit groups, five passes) and in a classic one: <C>, 4096
+    sampled amplitudes plus the top-32 entries, and the top-32 lists."""
+    capi, ctx = api
+    sizes = [25, 26]
+    g = chain_graph(sizes, 0.15, 77, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), 2, capi.PART_SIZES, sizes)
+    subs = oracle_parts(orc, g, sizes)
+    gam, bet = synth.random_angles(2, 2, 2526)
+    refs = [orc.simulate(s, gam[i], bet[i]) for i, s in enumerate(subs)]
+    oex = [orc.expect_state(s, r) for s, r in zip(subs, refs)]
+    rng = np.random.default_rng(5)
+    try:
+        for sched in [(12, 5, 2, 1), (13, 5, 2, 0)]:
+            for n in sizes:
+                capi.paraqaoa_set_schedule(ctx, n, *sched)
+            ids = np.arange(2, dtype=np.int32)
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+            ex = capi.paraqaoa_expect(ctx, 2)
+            z, pr = capi.paraqaoa_topk(ctx, 2, 32)
+            for i, s in enumerate(subs):
+                assert abs(ex[i] - oex[i]) / s.total_weight <= EXP_TOL, (sched, s.n)
+                ours = capi.paraqaoa_state(ctx, i, s.n)
+                idx = np.concatenate([rng.integers(0, 1 << s.n, 4096), z[i].astype(np.int64)])
+                assert np.max(np.abs(ours[idx] - refs[i][idx])) <= AMP_TOL, (sched, s.n)
+                del ours
+                _check_topk(orc, s, refs[i], z[i], pr[i], 32)
+    finally:
+        for n in sizes:
+            capi.paraqaoa_set_schedule(ctx, n, 12, 4, 3, 0)
+        capi.paraqaoa_part_free(part)
+
+
+def test_optimize_graph_replay_matches_direct_launches(api):
+    """With per-kernel profiling off, Adam steps 2.. replay one captured step
+    as a CUDA graph; with profiling on, every step is launched directly. Both
+    must give identical angles and <C> (the kernels are deterministic)."""
+    capi, ctx = api
+    g = synth.erdos_renyi(60, 0.3, 4, wmax=10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), 4)
+    try:
+        ids = np.arange(4, dtype=np.int32)
+        g0, b0 = synth.random_angles(4, 2, 8)
+        out = []
+        for prof in (False, True):
+            capi.paraqaoa_profile_enable(ctx, prof)
+            out.append(capi.paraqaoa_optimize(ctx, part, ids, 2, g0, b0, 6))
+        capi.paraqaoa_profile_enable(ctx, False)
+    finally:
+        capi.paraqaoa_part_free(part)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
