@@ -182,11 +182,12 @@ def run_layer_case(args):
     gam, bet = synth.random_angles(len(ids), 2, 3)
     capi.paraqaoa_part_upload(ctx, part)
     if args.sched:
-        tb, rb, cm, sp = (int(x) for x in args.sched.split(","))
-        capi.paraqaoa_set_schedule(ctx, 20, tb, rb, cm, sp)
-        tuned = {20: (tb, rb, cm, sp)}
+        sc = tuple(int(x) for x in args.sched.split(","))
+        sc = sc + (0,) * (5 - len(sc))
+        capi.paraqaoa_set_schedule(ctx, 20, *sc)
+        tuned = {20: sc}
     else:
-        tuned = {20: (None, None, None, None)} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
+        tuned = {20: (None,) * 5} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
     for it in range(args.iters):
         if it == args.iters - 1:
             capi.paraqaoa_profile_enable(ctx, True)
@@ -196,7 +197,7 @@ def run_layer_case(args):
     peak, kind = read_peaks()
     print(json.dumps({"case": "layer_pass", "instances": int(len(ids)), "qubits": 20, "p": 2,
                       "tile_bits": tuned[20][0], "reg_bits": tuned[20][1], "min_run_qubits": tuned[20][2],
-                      "split": tuned[20][3],
+                      "split": tuned[20][3], "tiles_per_cta_log2": tuned[20][4],
                       "launches": n_l, "ms": ms, "algorithmic_bytes": by,
                       "achieved_gbs": by / (ms / 1e3) / 1e9, "peak_gbs": peak,
                       "frac": by / (ms / 1e3) / 1e9 / peak}), flush=True)
@@ -432,7 +433,7 @@ def main():
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--sched", default="", help="fixed schedule of the 20-qubit parts instead of the autotuner: "
-                                                "tile_bits,reg_bits,c_min,split")
+                                                "tile_bits,reg_bits,c_min,split[,tiles_per_cta_log2]")
     ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex learned-form time-to-cut")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the context's default tile choice (fixed launch sequence for ncu)")
@@ -477,7 +478,8 @@ def main():
     sched = []
     for G in Gs:
         if args.sched:
-            sched.append(tuple(int(x) for x in args.sched.split(",")))
+            sc = tuple(int(x) for x in args.sched.split(","))
+            sched.append(sc + (0,) * (5 - len(sc)))
         else:
             part = capi.paraqaoa_partition(G, M)
             sched.append(capi.paraqaoa_autotune(solver.ctx, part, P_FINAL)[20])
@@ -557,7 +559,8 @@ def main():
             "gpu_launches": int(total_launches),
             "clocks": clk,
             "schedule_20_qubits": [{"graph": f"G({NV},{pe})", "tile_bits": sc[0], "reg_bits": sc[1],
-                                    "min_run_qubits": sc[2], "split": sc[3]} for pe, sc in zip(DENSITIES, sched)],
+                                    "min_run_qubits": sc[2], "split": sc[3], "tiles_per_cta_log2": sc[4]}
+                                   for pe, sc in zip(DENSITIES, sched)],
             "cpu_baseline": cb,
             "time_to_cut_16k": large,
         }

@@ -320,20 +320,24 @@ int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
  * minimum contiguous-qubit runs of the higher groups (2..4), and classic or
  * split schedules (classic: the low group is the tile's 2^12 or 2^13
  * contiguous qubits, mixed in up to three register rounds; split: the low
- * group is the 2R lowest qubits, mixed in two rounds with one transpose).
- * Choices that give the same pass schedule are timed once. Optional outputs
- * (31 entries each, indexed by n): chosen tile bits, register bits per
- * thread, minimum run, split flag. Without a call the context uses the
- * classic 2^12 x 16-register schedule unless 2^13 needs fewer passes. */
+ * group is the 2R lowest qubits, mixed in two rounds with one transpose),
+ * and for the 16-register shape 1, 2, 4 or 8 tiles per CTA (sharing the
+ * per-instance set-up loads). Choices that give the same pass schedule are
+ * timed once. Optional outputs (31 entries each, indexed by n): chosen tile
+ * bits, register bits per thread, minimum run, split flag, log2 tiles per
+ * CTA. Without a call the context uses the classic 2^12 x 16-register
+ * schedule, one tile per CTA, unless 2^13 needs fewer passes. */
 int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, int32_t *out_tile_bits,
-                      int32_t *out_reg_bits, int32_t *out_c_min, int32_t *out_split);
+                      int32_t *out_reg_bits, int32_t *out_c_min, int32_t *out_split,
+                      int32_t *out_tiles_per_cta_log2);
 
 /* Set the layer-pass schedule of n-qubit parts by hand (the choice the
  * autotuner makes): tile bits and register bits per thread (one of the
- * shapes 12/5, 12/4, 13/5), minimum contiguous run c_min of the higher groups
- * and split (0 classic, 1 split). Affects later simulate calls of ctx. */
+ * shapes 12/5, 12/4, 13/5), minimum contiguous run c_min of the higher groups,
+ * split (0 classic, 1 split) and log2 of the tiles each CTA walks (0..8;
+ * above 0 only for the 12/4 shape). Affects later simulate calls of ctx. */
 int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
-                          int32_t split);
+                          int32_t split, int32_t tiles_per_cta_log2);
 
 /* Per-kernel device time recorded with CUDA events on the context stream.
  * enable != 0 starts recording (and clears the counters). */

@@ -61,9 +61,9 @@ _SIGS = {
     "paraqaoa_grid_search": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P, P], ctypes.c_int),
     "paraqaoa_optimize": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                            ctypes.c_double, P, P, P], ctypes.c_int),
-    "paraqaoa_autotune": ([P, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
-    "paraqaoa_set_schedule": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
-                              ctypes.c_int),
+    "paraqaoa_autotune": ([P, P, ctypes.c_int32, P, P, P, P, P], ctypes.c_int),
+    "paraqaoa_set_schedule": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_int32], ctypes.c_int),
     "paraqaoa_profile_enable": ([P, ctypes.c_int32], ctypes.c_int),
     "paraqaoa_profile_read": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -261,14 +261,15 @@ def paraqaoa_optimize(ctx, part, ids, p: int, gamma0, beta0, steps: int = 32, lr
 
 def paraqaoa_autotune(ctx, part, p: int = 2):
     """Time the layer-pass schedule candidates per qubit count; returns
-    {n: (tile_bits, register_bits, min_contiguous_qubits, split)} for n >= 15."""
+    {n: (tile_bits, register_bits, min_contiguous_qubits, split, tiles_per_cta_log2)} for n >= 15."""
     tb = np.zeros(31, np.int32)
     rb = np.zeros(31, np.int32)
     cm = np.zeros(31, np.int32)
     sp = np.zeros(31, np.int32)
-    _check(load().paraqaoa_autotune(ctx, part, int(p), _ptr(tb), _ptr(rb), _ptr(cm), _ptr(sp)),
+    tp = np.zeros(31, np.int32)
+    _check(load().paraqaoa_autotune(ctx, part, int(p), _ptr(tb), _ptr(rb), _ptr(cm), _ptr(sp), _ptr(tp)),
            "paraqaoa_autotune")
-    return {n: (int(tb[n]), int(rb[n]), int(cm[n]), int(sp[n])) for n in range(15, 31)}
+    return {n: (int(tb[n]), int(rb[n]), int(cm[n]), int(sp[n]), int(tp[n])) for n in range(15, 31)}
 
 
 def paraqaoa_profile_enable(ctx, enable: bool = True):
@@ -393,6 +394,7 @@ def paraqaoa_simulate_tc(ctx, part, ids, p: int, gamma, beta, flags: int = SIM_E
                                        int(precision), int(block_qubits)), "paraqaoa_simulate_tc")
 
 
-def paraqaoa_set_schedule(ctx, n: int, tile_bits: int, reg_bits: int, c_min: int = 3, split: int = 0):
-    _check(load().paraqaoa_set_schedule(ctx, int(n), int(tile_bits), int(reg_bits), int(c_min), int(split)),
-           "paraqaoa_set_schedule")
+def paraqaoa_set_schedule(ctx, n: int, tile_bits: int, reg_bits: int, c_min: int = 3, split: int = 0,
+                          tiles_per_cta_log2: int = 0):
+    _check(load().paraqaoa_set_schedule(ctx, int(n), int(tile_bits), int(reg_bits), int(c_min), int(split),
+                                        int(tiles_per_cta_log2)), "paraqaoa_set_schedule")

@@ -108,6 +108,8 @@ struct paraqaoa_ctx {
   int8_t c_min[PARAQAOA_MAX_QUBITS + 1] = {};
   // split schedule (the low group is 2R qubits, one transpose per pass) per n
   int8_t split[PARAQAOA_MAX_QUBITS + 1] = {};
+  // tiles per CTA of the layer passes (log2) per n
+  int8_t tpc_log2[PARAQAOA_MAX_QUBITS + 1] = {};
   int num_sms = 0;
   // partition on the device
   uint64_t part_serial = 0;
@@ -350,7 +352,8 @@ int plan_run(paraqaoa_ctx* c) {
     const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[kind].r : 0);
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
     PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * cut_consts_elems(kind, kv.second.second)));
-    for (const PassDesc& pd : sched) {
+    for (PassDesc pd : sched) {
+      pd.tpc_log2 = std::min<int>(c->tpc_log2[n], n - tb);
       if (pd.layerP >= 0 || pd.expect) {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
         PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
@@ -1223,15 +1226,18 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
 }
 
 int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
-                          int32_t split) {
-  if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || (split != 0 && split != 1))
+                          int32_t split, int32_t tiles_per_cta_log2) {
+  if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || (split != 0 && split != 1) ||
+      tiles_per_cta_log2 < 0 || tiles_per_cta_log2 > 8)
     return PARAQAOA_E_INVAL;
   for (int kind = 0; kind < kTileKinds; ++kind)
     if (kTileShapes[kind].tb == tile_bits && kTileShapes[kind].r == reg_bits) {
       if (n < tile_bits || (split && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
+      if (tiles_per_cta_log2 > 0 && !layer_kind_multi_tile(kind)) return PARAQAOA_E_INVAL;
       c->tile_kind[n] = (int8_t)kind;
       c->c_min[n] = (int8_t)c_min;
       c->split[n] = (int8_t)split;
+      c->tpc_log2[n] = (int8_t)tiles_per_cta_log2;
       c->plan.valid = false;
       return PARAQAOA_OK;
     }
@@ -1239,7 +1245,7 @@ int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t
 }
 
 int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32_t* out_tile_bits,
-                      int32_t* out_reg_bits, int32_t* out_c_min, int32_t* out_split) {
+                      int32_t* out_reg_bits, int32_t* out_c_min, int32_t* out_split, int32_t* out_tiles_per_cta_log2) {
   if (!c || !pt || p < 1 || p > PARAQAOA_MAX_P) return PARAQAOA_E_INVAL;
   PQ_CUDA(cudaSetDevice(c->device));
   int rc = upload_part(c, pt, false);
@@ -1258,7 +1264,7 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
     for (int64_t k = 0; k < copies; ++k) ids[k] = reps[k % reps.size()];
     std::vector<double> ang(copies * p, 0.5);
     struct Cand {
-      int kind, cm, sp;
+      int kind, cm, sp, tpc;
       float ms;
     };
     std::vector<Cand> cands;
@@ -1273,7 +1279,8 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
           const std::pair<int, int> key(G * 1000 + kind * 10 + sp, sched.size() > 1 ? sched[1].c : 0);
           if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
           seen.push_back(key);
-          cands.push_back({kind, cm, sp, 1e30f});
+          for (int tpc = 0; tpc <= (layer_kind_multi_tile(kind) ? 3 : 0) && tpc <= n - tb; ++tpc)
+            cands.push_back({kind, cm, sp, tpc, 1e30f});
         }
     }
     // three rounds over all candidates, each keeping its fastest round: the
@@ -1284,6 +1291,7 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
         c->tile_kind[n] = (int8_t)cd.kind;
         c->c_min[n] = (int8_t)cd.cm;
         c->split[n] = (int8_t)cd.sp;
+        c->tpc_log2[n] = (int8_t)cd.tpc;
         rc = plan_build(c, pt, ids.data(), (int32_t)copies, p, PARAQAOA_SIM_EXPECT);
         if (rc == PARAQAOA_E_ADMISSION) {
           rc = PARAQAOA_OK;
@@ -1303,12 +1311,13 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
         cd.ms = std::min(cd.ms, ms);
       }
     if (rc) break;
-    Cand best{c->tile_kind[n], c->c_min[n], c->split[n], 1e30f};
+    Cand best{c->tile_kind[n], c->c_min[n], c->split[n], c->tpc_log2[n], 1e30f};
     for (const Cand& cd : cands)
       if (cd.ms < best.ms) best = cd;
     c->tile_kind[n] = (int8_t)best.kind;
     c->c_min[n] = (int8_t)best.cm;
     c->split[n] = (int8_t)best.sp;
+    c->tpc_log2[n] = (int8_t)best.tpc;
   }
   c->pool.push_back(e0);
   c->pool.push_back(e1);
@@ -1320,6 +1329,7 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
     if (out_reg_bits) out_reg_bits[n] = kTileShapes[c->tile_kind[n]].r;
     if (out_c_min) out_c_min[n] = c->c_min[n];
     if (out_split) out_split[n] = c->split[n];
+    if (out_tiles_per_cta_log2) out_tiles_per_cta_log2[n] = c->tpc_log2[n];
   }
   return PARAQAOA_OK;
 }

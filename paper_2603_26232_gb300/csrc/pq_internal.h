@@ -61,6 +61,7 @@ struct PassDesc {
   int32_t expect;   // reduce sum |psi|^2 C into the tile partial
   int32_t last;     // the final pass (stores apply lambda_p)
   int32_t split;    // low-group pass of a split schedule: mix local bits [0, 2R) in two rounds
+  int32_t tpc_log2; // each CTA processes 2^tpc_log2 consecutive tiles of one instance
 };
 
 // Kernel launchers (sim_kernels.cu). All enqueue on `st` and return the
@@ -82,6 +83,7 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
 int64_t cut_consts_elems(int kind, int32_t nlist);
 int layer_resident_per_sm(int kind);  // occupancy target of a tile shape (CTAs per SM)
+bool layer_kind_multi_tile(int kind);  // may the shape's CTAs walk several tiles
 cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
                               int32_t* consts, cudaStream_t st);

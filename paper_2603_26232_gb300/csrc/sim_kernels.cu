@@ -617,6 +617,10 @@ __global__ void __launch_bounds__(1 << (TB - R))
   }
 }
 
+// Shapes whose CTAs may walk 2^tpc_log2 consecutive tiles (sharing the
+// per-instance set-up loads).
+__host__ __device__ constexpr bool layer_multi_tile(int tb, int r) { return r == 4; }
+
 // Occupancy target of a tile shape: resident CTAs per SM. The 16-register
 // shape fits 64 registers per thread (four CTAs of 256 threads); the 2^12 x 32
 // shape is held to 96 registers for five CTAs of 128 threads (a few bytes of
@@ -645,13 +649,13 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   const uint32_t tid = threadIdx.x;
   const int c = pd.c, s = pd.s, g = TB - c;
   const uint32_t lowt = (uint32_t)(s - c);
-  const int li_idx = (int)(blockIdx.x >> tiles_log2);
-  const uint32_t tile = blockIdx.x & ((1u << tiles_log2) - 1u);
+  // this CTA's 2^tpc_log2 consecutive tiles, all of one instance
+  const uint32_t tile0 = blockIdx.x << pd.tpc_log2;
+  const int li_idx = (int)(tile0 >> tiles_log2);
   const InstDev* Ip = inst_all + list[li_idx];
   const int P = Ip->P, W = Ip->W;
   const uint32_t* pl = planes_all + subs[Ip->sub].plane_off;
   const bool need_cut = pd.layerP >= 0 || pd.expect;
-  const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
 
   // ---- set-up. One round of global loads, all issued before the first
   // barrier (the state loads below too): the phase table, the instance's
@@ -680,6 +684,16 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   auto zmap = [&](uint32_t li) -> uint32_t { return (li & lowm) | ((li & ~lowm) << sh); };
   // load/store layout O0: this thread's amplitude offsets are zmap(lt | register bits)
   const uint32_t lt = lir_o<TB, R, O0>(tid, 0);
+  // Tiles of one CTA share the set-up above. Across iterations the barriers
+  // below order every reuse of shared memory: warp 0 rewrites the tile
+  // constants only after the first barrier of the next tile, which every
+  // thread reaches after its last read of them.
+  // (Only the 16-register shape walks several tiles: the 32-register shapes
+  // keep one tile per CTA, where the loop's live set would spill.)
+  const uint32_t ntiles = layer_multi_tile(TB, R) ? (1u << pd.tpc_log2) : 1u;
+  for (uint32_t tt = 0; tt < ntiles; ++tt) {
+  const uint32_t tile = (tile0 + tt) & ((1u << tiles_log2) - 1u);
+  const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
   float2* base = states + Ip->state_off + (zbase | zmap(lt));
 
   float2 a[KQ];
@@ -809,6 +823,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
       base[off] = a[k];
     }
   }
+  }  // tiles of this CTA
 }
 
 size_t layer_pass_smem(int kind, int tabcap) {
@@ -817,6 +832,8 @@ size_t layer_pass_smem(int kind, int tabcap) {
   return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
          PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 16 * sizeof(double);
 }
+
+bool layer_kind_multi_tile(int kind) { return layer_multi_tile(kTileShapes[kind].tb, kTileShapes[kind].r); }
 
 int layer_resident_per_sm(int kind) { return layer_min_blocks(kTileShapes[kind].tb, kTileShapes[kind].r); }
 
@@ -869,7 +886,9 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles_log2 = n - TB;
-  const int64_t blocks = (int64_t)nlist << tiles_log2;
+  const int tpc = layer_multi_tile(TB, R) ? pd.tpc_log2 : 0;
+  if (tpc < 0 || tpc > tiles_log2) return cudaErrorInvalidValue;
+  const int64_t blocks = (int64_t)nlist << (tiles_log2 - tpc);
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
   // register slots each round mixes (mm0: layout 0, mm1: layout 1, mm2: layout 2)
   uint32_t mm0 = 0, mm1 = 0, mm2 = 0;

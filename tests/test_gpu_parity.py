@@ -357,8 +357,8 @@ def test_autotune_choices_keep_parity(api, orc):
     try:
         choice = capi.paraqaoa_autotune(ctx, part, 2)
         for n in sizes:
-            tb, rb, cm, sp = choice[n]
-            assert (tb, rb) in ((12, 5), (12, 4), (13, 5)) and cm in (2, 3, 4) and sp in (0, 1)
+            tb, rb, cm, sp, tp = choice[n]
+            assert (tb, rb) in ((12, 5), (12, 4), (13, 5)) and cm in (2, 3, 4) and sp in (0, 1) and 0 <= tp <= 3
         subs = oracle_parts(orc, g, sizes)
         ids = np.arange(len(sizes), dtype=np.int32)
         gam, bet = synth.random_angles(len(sizes), 2, 99)
@@ -372,17 +372,19 @@ def test_autotune_choices_keep_parity(api, orc):
         capi.paraqaoa_part_free(part)
 
 
-@pytest.mark.parametrize("tb,rb,split", [(12, 5, 0), (12, 4, 0), (13, 5, 0), (12, 5, 1), (12, 4, 1), (13, 5, 1)])
-def test_every_schedule_matches_oracle(api, orc, tb, rb, split):
-    """Every tile shape in classic and split schedules, on parts of 15..24
-    qubits (two and three qubit groups), depth 3, states kept."""
+@pytest.mark.parametrize("tb,rb,split,tpc", [(12, 5, 0, 0), (12, 4, 0, 0), (13, 5, 0, 0), (12, 5, 1, 0), (12, 4, 1, 0),
+                                             (13, 5, 1, 0), (12, 4, 0, 3), (12, 4, 1, 2)])
+def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
+    """Every tile shape in classic and split schedules, one or several tiles
+    per CTA, on parts of 15..24 qubits (two and three qubit groups), depth 3,
+    states kept."""
     capi, ctx = api
     sizes = [15, 16, 19, 20, 21, 23, 24]
-    g = chain_graph(sizes, 0.3, 40 + tb + rb + split, 10)
+    g = chain_graph(sizes, 0.3, 40 + tb + rb + split + tpc, 10)
     part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
     try:
         for n in sizes:
-            capi.paraqaoa_set_schedule(ctx, n, tb, rb, 3, split)
+            capi.paraqaoa_set_schedule(ctx, n, tb, rb, 3, split, tpc)
         subs = oracle_parts(orc, g, sizes)
         ids = np.arange(len(sizes), dtype=np.int32)
         gam, bet = synth.random_angles(len(sizes), 3, 123 + split)
