@@ -256,6 +256,45 @@ def large_learned(capi, pkg):
             "plain_form": "measured by bench.py --case large"}
 
 
+def run_batching_case(args):
+    """Batching configuration: G(2000, 0.05), unit weights, uneven parts of
+    12..24 vertices (about 120), p = 3, random angles, <C> of every part in one
+    simulate call; amplitude-layers/s with the size classes on side streams
+    (profiling off) and in order (profiling on, per-class device times)."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    ctx = capi.paraqaoa_create(0)
+    g = synth.erdos_renyi(2000, 0.05, 0, wmax=1)
+    sizes = synth.uneven_sizes(2000, 12, 24, 1)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    ids = np.arange(len(sizes), dtype=np.int32)
+    gam, bet = synth.random_angles(len(sizes), 3, 3)
+    capi.paraqaoa_autotune(ctx, part, 3)
+    amp_layers = float(np.sum(np.left_shift(1, sizes.astype(np.int64)))) * 3
+    out = {"case": "batching", "workload": "G(2000,0.05) unit weights, seed 0; uneven parts of 12..24 vertices; p=3",
+           "parts": int(len(sizes)), "amplitude_layers": amp_layers}
+    for name, prof in (("side_streams", False), ("serial", True)):
+        capi.paraqaoa_profile_enable(ctx, prof)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+        capi.paraqaoa_expect(ctx, len(ids))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 5
+        for _ in range(reps):
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+            ex = capi.paraqaoa_expect(ctx, len(ids))
+        dt = (time.perf_counter() - t0) / reps
+        out[name] = {"s_per_batch": dt, "amp_layers_per_s": amp_layers / dt}
+    capi.paraqaoa_profile_enable(ctx, False)
+    out["mean_expect"] = float(np.mean(ex))
+    capi.paraqaoa_part_free(part)
+    capi.paraqaoa_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep_case(args):
     """Amplitude-layer sweep over qubit counts: for n = 14..26, a batch of
     parts of n vertices (G(*, 0.3) chain, weights 1..10) with sum 2^n >= 2^28
@@ -428,7 +467,8 @@ def main():
     ap.add_argument("--test-count", type=int, default=2000, help="learned case: held-out subgraphs")
     ap.add_argument("--sweep-lo", type=int, default=14)
     ap.add_argument("--sweep-hi", type=int, default=26)
-    ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large", "learned", "sweep"],
+    ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large", "learned", "sweep",
+                                                        "batching"],
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
@@ -451,6 +491,8 @@ def main():
         return run_learned_case(args)
     if args.case == "sweep":
         return run_sweep_case(args)
+    if args.case == "batching":
+        return run_batching_case(args)
 
     import torch
     import paper_2603_26232_gb300 as pkg

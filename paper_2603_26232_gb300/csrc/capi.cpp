@@ -98,6 +98,8 @@ struct SimPlan {
   bool valid = false;
 };
 
+constexpr int kSideStreams = 4;
+
 struct paraqaoa_ctx {
   int device = 0;
   size_t budget = 0;
@@ -129,6 +131,9 @@ struct paraqaoa_ctx {
   DevBuf d_tc_err;
   // Adam step counter on the device (read by the update kernel)
   DevBuf o_step;
+  // side streams for concurrent size classes, with their fork / join events
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
   // profiling
   bool prof = false;
   std::vector<ProfRec> pending;
@@ -240,6 +245,16 @@ int upload_part(paraqaoa_ctx* c, const paraqaoa_part* pt, bool force) {
   return PARAQAOA_OK;
 }
 
+cudaError_t ensure_side_streams(paraqaoa_ctx* c) {
+  if (c->fork_ev) return cudaSuccess;
+  for (int k = 0; k < kSideStreams; ++k) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+}
+
 // Build the plan of a batch (validation, admission, memory layout).
 int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
                int32_t p, uint32_t flags) {
@@ -336,41 +351,70 @@ int plan_run(paraqaoa_ctx* c) {
     PQ_CUDA(launch_prep_layers(inst, pl.count, p, c->d_gamma.as<double>(), c->d_beta.as<double>(),
                                tables, inst, c->stream));
   }
+  // Size classes are independent (disjoint instances, states, partials and
+  // cut-constant regions): without per-kernel profiling they run on side
+  // streams forked from and joined back to the context stream, so that small
+  // classes fill the GPU next to large ones. Stream capture follows the fork.
+  const int ncls = (pl.tiny.second > 0 ? 1 : 0) + (int)pl.smem.size() + (int)pl.hbm.size();
+  const bool fork = !c->prof && ncls > 1;
+  int used = 0;
+  if (fork) {
+    PQ_CUDA(ensure_side_streams(c));
+    PQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
+    for (int k = 0; k < kSideStreams; ++k) PQ_CUDA(cudaStreamWaitEvent(c->side[k], c->fork_ev, 0));
+  }
+  auto cls_stream = [&]() -> cudaStream_t {
+    if (!fork) return c->stream;
+    const int k = used++ % kSideStreams;
+    return c->side[k];
+  };
+  int64_t cc_total = 0;
+  for (auto& kv : pl.hbm) cc_total += cut_consts_elems(c->tile_kind[kv.first], kv.second.second);
+  PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * std::max<int64_t>(cc_total, 1)));
   if (pl.tiny.second > 0) {
+    cudaStream_t st = cls_stream();
     ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, 0);
     PQ_CUDA(launch_tiny_sim(inst, lists + pl.tiny.first, pl.tiny.second, p, subs, planes, tables,
-                            states, expect, keep, want, pl.tabcap, c->stream));
+                            states, expect, keep, want, pl.tabcap, st));
   }
   for (auto& kv : pl.smem) {
+    cudaStream_t st = cls_stream();
     ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, keep ? (double)kv.second.second * 8.0 * (1 << kv.first) : 0.0);
     PQ_CUDA(launch_smem_sim(kv.first, inst, lists + kv.second.first, kv.second.second, p, subs,
-                            planes, tables, states, expect, keep, want, pl.tabcap, c->stream));
+                            planes, tables, states, expect, keep, want, pl.tabcap, st));
   }
+  int64_t cc_off = 0;
   for (auto& kv : pl.hbm) {
+    cudaStream_t st = cls_stream();
     const int n = kv.first;
     const int kind = c->tile_kind[n], tb = kTileShapes[kind].tb;
     const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[kind].r : 0);
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
-    PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * cut_consts_elems(kind, kv.second.second)));
+    int32_t* consts = c->d_consts.as<int32_t>() + cc_off;
+    cc_off += cut_consts_elems(kind, kv.second.second);
     for (PassDesc pd : sched) {
       pd.tpc_log2 = std::min<int>(c->tpc_log2[n], n - tb);
       if (pd.layerP >= 0 || pd.expect) {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
         PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
-                                  c->d_consts.as<int32_t>(), c->stream));
+                                  consts, st));
       }
       const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
       ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
       PQ_CUDA(launch_layer_pass(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs,
-                                planes, tables, states, partials, pl.tabcap, c->d_consts.as<int32_t>(),
-                                c->stream));
+                                planes, tables, states, partials, pl.tabcap, consts, st));
     }
     if (want) {
       ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
       PQ_CUDA(launch_expect_reduce(inst, lists + kv.second.first, kv.second.second,
-                                   1 << (n - tb), partials, expect, c->stream));
+                                   1 << (n - tb), partials, expect, st));
     }
   }
+  if (fork)
+    for (int k = 0; k < kSideStreams; ++k) {
+      PQ_CUDA(cudaEventRecord(c->join_ev[k], c->side[k]));
+      PQ_CUDA(cudaStreamWaitEvent(c->stream, c->join_ev[k], 0));
+    }
   return PARAQAOA_OK;
 }
 
@@ -535,6 +579,11 @@ void paraqaoa_destroy(paraqaoa_ctx* c) {
                     &c->m_keys, &c->m_nb, &c->o_vals, &c->o_best, &c->o_theta, &c->o_m, &c->o_v,
                     &c->o_w, &c->o_g2, &c->o_b2, &c->d_consts, &c->d_tc_err, &c->o_step};
   for (DevBuf* b : bufs) b->release();
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
 }

@@ -458,3 +458,30 @@ def test_optimize_graph_replay_matches_direct_launches(api):
         capi.paraqaoa_part_free(part)
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+def test_size_classes_on_side_streams_match_serial(api, orc):
+    """Uneven parts (9..22 qubits: tiny, on-chip and streamed classes) in one
+    batch: with profiling off the size classes run concurrently on side
+    streams, with profiling on they run in order on the context stream. The
+    results must be identical, and match the oracle."""
+    capi, ctx = api
+    sizes = [9, 12, 14, 15, 17, 20, 22, 16, 13]
+    g = chain_graph(sizes, 0.3, 66, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), 3, 67)
+        out = []
+        for prof in (False, True):
+            capi.paraqaoa_profile_enable(ctx, prof)
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+            out.append(capi.paraqaoa_expect(ctx, len(ids)))
+        capi.paraqaoa_profile_enable(ctx, False)
+        assert np.array_equal(out[0], out[1])
+        subs = oracle_parts(orc, g, sizes)
+        oex = orc.expect_batch(orc.Batch(subs), ids, gam, bet)
+        W = np.array([s.total_weight for s in subs], float)
+        assert np.all(np.abs(out[0] - oex) / W <= EXP_TOL)
+    finally:
+        capi.paraqaoa_part_free(part)
