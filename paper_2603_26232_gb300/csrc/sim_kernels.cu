@@ -148,16 +148,33 @@ __device__ __forceinline__ void transposer(float2 (&a)[1 << R], float2* sm, uint
   __syncthreads();
 }
 
+// True when layouts OF and OT put the same local bits in the warp index
+// (thread bits 5 and up): a transpose between them then only moves data
+// among the lanes of one warp, through shared memory the warp alone
+// touches, and a warp barrier is enough.
+template <int TB, int R, int OF, int OT>
+__host__ __device__ constexpr bool warp_local_transpose() {
+  for (int b = 5; b < TB - R; ++b)
+    if (thread_bit_local_o<R, OF>(b) != thread_bit_local_o<R, OT>(b)) return false;
+  return true;
+}
+
+static_assert(warp_local_transpose<12, 4, 4, 0>() && warp_local_transpose<12, 5, 2, 0>() &&
+                  warp_local_transpose<13, 5, 3, 0>() && warp_local_transpose<12, 5, 5, 0>(),
+              "the second transpose of a three-round pass and the split pass's transpose stay in a warp");
+static_assert(!warp_local_transpose<12, 4, 8, 4>(), "load/store-layout transposes cross warps");
+
 template <int TB, int R, int OF, int OT>
 __device__ __forceinline__ void transposer_o(float2 (&a)[1 << R], float2* sm, uint32_t tid) {
+  constexpr bool kWarp = warp_local_transpose<TB, R, OF, OT>();
   float2* pf = sm + padr<R>(lir_o<TB, R, OF>(tid, 0));
   float2* pt = sm + padr<R>(lir_o<TB, R, OT>(tid, 0));
 #pragma unroll
   for (int k = 0; k < (1 << R); ++k) pf[padr<R>(lir_o<TB, R, OF>(0, k))] = a[k];
-  __syncthreads();
+  if constexpr (kWarp) __syncwarp(); else __syncthreads();
 #pragma unroll
   for (int k = 0; k < (1 << R); ++k) a[k] = pt[padr<R>(lir_o<TB, R, OT>(0, k))];
-  __syncthreads();
+  if constexpr (kWarp) __syncwarp(); else __syncthreads();
 }
 
 template <int R>
