@@ -295,6 +295,63 @@ def run_batching_case(args):
     print(json.dumps(out), flush=True)
 
 
+def run_tc_case(args):
+    """Split-precision tensor-core mixer on the batching configuration
+    (G(2000, 0.05), unit weights, 122 parts of 12..24 vertices, p = 3, random
+    angles): amplitude-layers/s of paraqaoa_simulate_tc (FP16 and BF16 splits,
+    blocks of up to --tc-k qubits) against the FP32 butterfly path, and the largest
+    |d<C>| / W against the FP32 path over all parts (itself within 1e-5 W of
+    the FP64 oracle) and against the FP64 oracle on the parts of <= 18 qubits."""
+    import torch
+    import oracle
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    ctx = capi.paraqaoa_create(0)
+    g = synth.erdos_renyi(2000, 0.05, 0, wmax=1)
+    sizes = synth.uneven_sizes(2000, 12, 24, 1)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    ids = np.arange(len(sizes), dtype=np.int32)
+    keep = sizes >= 12
+    ids = ids[keep]
+    gam, bet = synth.random_angles(len(ids), 3, 3)
+    W = np.array([max(int(w), 1) for w in capi.paraqaoa_part_info(part)[3][ids]], float)
+    amp_layers = float(np.sum(np.left_shift(1, sizes[keep].astype(np.int64)))) * 3
+    subs = oracle.subgraphs(g, len(sizes), 2, sizes)
+    small = [i for i, k in enumerate(ids) if sizes[k] <= 18][:24]
+    oex = oracle.expect_batch(oracle.Batch([subs[ids[i]] for i in small]), np.arange(len(small), dtype=np.int32),
+                              gam[small], bet[small])
+    out = {"case": "tc", "workload": "G(2000,0.05) unit weights, seed 0; parts of 12..24 vertices; p=3",
+           "parts": int(len(ids)), "oracle_parts": len(small), "block_qubits": args.tc_k}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ex = fn()
+        return ex, (time.perf_counter() - t0) / 3
+
+    def fp32():
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+        return capi.paraqaoa_expect(ctx, len(ids))
+    ex32, t32 = timed(fp32)
+    out["fp32"] = {"amp_layers_per_s": amp_layers / t32,
+                   "max_dC_over_W_vs_oracle": float(np.max(np.abs(ex32[small] - oex) / W[small]))}
+    for name, prec in (("fp16_split", capi.TC_FP16), ("bf16_split", capi.TC_BF16)):
+        def tc():
+            capi.paraqaoa_simulate_tc(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT, prec, args.tc_k)
+            return capi.paraqaoa_expect(ctx, len(ids))
+        ex, t = timed(tc)
+        out[name] = {"amp_layers_per_s": amp_layers / t,
+                     "max_dC_over_W_vs_fp32_path": float(np.max(np.abs(ex - ex32) / W)),
+                     "max_dC_over_W_vs_oracle": float(np.max(np.abs(ex[small] - oex) / W[small]))}
+    capi.paraqaoa_part_free(part)
+    capi.paraqaoa_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep_case(args):
     """Amplitude-layer sweep over qubit counts: for n = 14..26, a batch of
     parts of n vertices (G(*, 0.3) chain, weights 1..10) with sum 2^n >= 2^28
@@ -465,10 +522,11 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="large case: skip the plain form")
     ap.add_argument("--train-count", type=int, default=20000, help="learned case: training subgraphs")
     ap.add_argument("--test-count", type=int, default=2000, help="learned case: held-out subgraphs")
+    ap.add_argument("--tc-k", type=int, default=6, help="tc case: mixer block qubits (5..7)")
     ap.add_argument("--sweep-lo", type=int, default=14)
     ap.add_argument("--sweep-hi", type=int, default=26)
     ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large", "learned", "sweep",
-                                                        "batching"],
+                                                        "batching", "tc"],
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
@@ -493,6 +551,8 @@ def main():
         return run_sweep_case(args)
     if args.case == "batching":
         return run_batching_case(args)
+    if args.case == "tc":
+        return run_tc_case(args)
 
     import torch
     import paper_2603_26232_gb300 as pkg

@@ -1197,12 +1197,17 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   for (int32_t i = 0; i < count; ++i) by_n[pl.inst[i].n].push_back(i);
   std::vector<int32_t> lists;
   std::vector<std::pair<int, std::pair<int32_t, int32_t>>> groups;
+  // each size group gets its own cut-table and partial-sum region, so that
+  // the groups can run concurrently on side streams
   int64_t cut_elems = 0, part_elems = 0;
+  std::vector<int64_t> cut_off, part_off;
   for (auto& kv : by_n) {
     groups.push_back({kv.first, {(int32_t)lists.size(), (int32_t)kv.second.size()}});
     lists.insert(lists.end(), kv.second.begin(), kv.second.end());
-    cut_elems = std::max<int64_t>(cut_elems, (int64_t)kv.second.size() << kv.first);
-    part_elems = std::max<int64_t>(part_elems, (int64_t)kv.second.size() * tc_finish_blocks(kv.first));
+    cut_off.push_back(cut_elems);
+    part_off.push_back(part_elems);
+    cut_elems += (int64_t)kv.second.size() << kv.first;
+    part_elems += (int64_t)kv.second.size() * tc_finish_blocks(kv.first);
   }
   const double extra = (double)cut_elems * 2 + (double)part_elems * 8;
   const double need = (double)pl.state_elems * 8 + (double)pl.table_elems * 8 + extra;
@@ -1226,14 +1231,25 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   }
   const bool fp16 = precision == PARAQAOA_TC_FP16;
   float2* states = c->d_states.as<float2>();
-  for (auto& gr : groups) {
+  // size groups on side streams (as in plan_run) unless per-kernel profiling is on
+  const bool fork = !c->prof && groups.size() > 1;
+  if (fork) {
+    PQ_CUDA(ensure_side_streams(c));
+    PQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
+    for (int k = 0; k < kSideStreams; ++k) PQ_CUDA(cudaStreamWaitEvent(c->side[k], c->fork_ev, 0));
+  }
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const auto& gr = groups[gi];
+    cudaStream_t st = fork ? c->side[gi % kSideStreams] : c->stream;
     const int n = gr.first;
     const int32_t off = gr.second.first, cnt = gr.second.second;
     const int64_t stride = int64_t(1) << n;
+    uint16_t* gcuts = cuts + cut_off[gi];
+    double* gparts = c->d_partials.as<double>() + part_off[gi];
     for (int32_t j = 0; j < cnt; ++j) {
       ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)stride * 2);
       PQ_CUDA(launch_cut_table(c->d_subs.as<SubDev>() + pl.inst[lists[off + j]].sub, n, c->d_planes.as<uint32_t>(),
-                               cuts + (int64_t)j * stride, c->stream));
+                               gcuts + (int64_t)j * stride, st));
     }
     // ceil(n / block_qubits) blocks of as even sizes as possible; fewer blocks
     // (sizes up to 7) when that would leave blocks under 5 qubits. Every block
@@ -1248,20 +1264,25 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
     for (int l = 0; l < p; ++l) {
       {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)cnt * stride * (l == 0 ? 10.0 : 18.0));
-        PQ_CUDA(launch_tc_phase(inst, dl + off, cnt, n, l, l == 0, c->d_tables.as<float2>(), cuts, stride, states,
-                                c->stream));
+        PQ_CUDA(launch_tc_phase(inst, dl + off, cnt, n, l, l == 0, c->d_tables.as<float2>(), gcuts, stride, states,
+                                st));
       }
       int q0 = 0;
       for (int b : bs) {
         ProfScope ps(c, PARAQAOA_KCLASS_TC_MIXER, (double)cnt * stride * 16.0);
-        PQ_CUDA(launch_mixer_tc(b, fp16, inst, dl + off, cnt, n, q0, l, states, scale, err, c->num_sms, c->stream));
+        PQ_CUDA(launch_mixer_tc(b, fp16, inst, dl + off, cnt, n, q0, l, states, scale, err, c->num_sms, st));
         q0 += b;
       }
     }
     ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)cnt * stride * (flags & PARAQAOA_SIM_KEEP_STATE ? 18.0 : 10.0));
-    PQ_CUDA(launch_tc_finish(inst, dl + off, cnt, n, cuts, stride, states, c->d_partials.as<double>(),
-                             (flags & PARAQAOA_SIM_KEEP_STATE) ? 1 : 0, c->d_expect.as<double>(), c->stream));
+    PQ_CUDA(launch_tc_finish(inst, dl + off, cnt, n, gcuts, stride, states, gparts,
+                             (flags & PARAQAOA_SIM_KEEP_STATE) ? 1 : 0, c->d_expect.as<double>(), st));
   }
+  if (fork)
+    for (int k = 0; k < kSideStreams; ++k) {
+      PQ_CUDA(cudaEventRecord(c->join_ev[k], c->side[k]));
+      PQ_CUDA(cudaStreamWaitEvent(c->stream, c->join_ev[k], 0));
+    }
   int herr = 0;
   PQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));

@@ -16,9 +16,10 @@
 // significant bits each but have a narrow exponent range, so A is scaled by a
 // power of two (exact) before splitting and D scaled back.
 //
-// One CTA of 128 threads owns a tile of 64 amplitude groups x 2^k amplitudes
+// One CTA of 256 threads owns a tile of 64 amplitude groups x 2^k amplitudes
 // (128 rows: real parts, then imaginary parts). Per tile: coalesced FP32
-// loads, split into shared memory in the canonical no-swizzle K-major layout,
+// loads (all issued before the first use), split into shared memory in the
+// canonical no-swizzle K-major layout,
 // one thread issues 3 x 2^k/16 MMAs (M = 128, N = 2^k, K = 16) into 2^k TMEM
 // columns, tcgen05.commit signals an mbarrier, and the accumulators come back
 // with tcgen05.ld, are staged through shared memory and stored coalesced.
@@ -103,8 +104,10 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
 // list (all with n qubits), in place on the interleaved complex64 states.
 // Grid: nlist x ctas_per_inst CTAs; CTA (i, j) walks tiles j, j + ctas, ...
 // of instance i. err (device int) is set to 1 if an mbarrier wait gave up.
+constexpr int kThreads = 256;  // 8 warps: TMEM lane quarter w % 4, column half w / 4
+
 template <int KB, bool FP16>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, KB < 7 ? 2 : 1)
     k_mixer_tc(const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list, int32_t n, int32_t q0,
                int32_t layer, int32_t ctas_per_inst, float2* __restrict__ states, float scale,
                int* __restrict__ err) {
@@ -160,13 +163,26 @@ __global__ void __launch_bounds__(128, 1)
   bool ok = true;
 
   for (int64_t t = cta_j; t < tiles && ok; t += ctas_per_inst) {
-    // ---- load the tile, split into A_hi / A_lo: thread (u, c-pair parity)
-    const uint32_t u = tid & (kGroups - 1);
+    // ---- load the tile (every load issued first), split into A_hi / A_lo:
+    // thread (u, q) handles amplitude group u and column pairs c = 2q + 8i
+    const uint32_t u = tid & (kGroups - 1), q = tid >> 6;
     const int64_t gi = t * kGroups + u;  // amplitude-group index (hi bits, lo bits)
     const int64_t base = ((gi >> q0) << (q0 + KB)) | (gi & lomask);
-    for (int c = (int)(tid >> 6) * 2; c < K; c += 4) {
-      const float2 x0 = psi[base + ((int64_t)c << q0)];
-      const float2 x1 = psi[base + ((int64_t)(c + 1) << q0)];
+    constexpr int NP = K / 8;            // column pairs per thread
+    constexpr int NB = NP < 8 ? NP : 8;  // pairs loaded per batch (caps the registers in flight)
+#pragma unroll 1
+    for (int i0 = 0; i0 < NP; i0 += NB) {
+    float2 v[2 * NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int c = 2 * (int)q + 8 * (i0 + i);
+      v[2 * i] = psi[base + ((int64_t)c << q0)];
+      v[2 * i + 1] = psi[base + ((int64_t)(c + 1) << q0)];
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int c = 2 * (int)q + 8 * (i0 + i);
+      const float2 x0 = v[2 * i], x1 = v[2 * i + 1];
       uint16_t h0, l0, h1, l1;
       Split<FP16>::run(x0.x * scale, h0, l0);
       Split<FP16>::run(x1.x * scale, h1, l1);
@@ -176,6 +192,7 @@ __global__ void __launch_bounds__(128, 1)
       Split<FP16>::run(x1.y * scale, h1, l1);
       *reinterpret_cast<uint32_t*>(a_hi + canon_off<K>(u + kGroups, c)) = (uint32_t)h0 | ((uint32_t)h1 << 16);
       *reinterpret_cast<uint32_t*>(a_lo + canon_off<K>(u + kGroups, c)) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -224,28 +241,40 @@ __global__ void __launch_bounds__(128, 1)
     if (!ok) break;
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- accumulators -> registers -> staging (row = TMEM lane = 32 warp + lane)
-    const uint32_t row = warp * 32 + lane;
+    // ---- accumulators -> registers -> staging: warp w reads TMEM lanes
+    // 32 (w % 4) .. + 31 (rows) and columns [(w / 4) K / 2, (w / 4 + 1) K / 2)
+    const uint32_t row = (warp & 3) * 32 + lane;
+    const uint32_t lane_base = tmem + (((warp & 3) * 32u) << 16);
+    constexpr int CH = K / 2 < 32 ? K / 2 : 32;  // columns per tcgen05.ld
 #pragma unroll 1
-    for (int c0 = 0; c0 < K; c0 += 32) {
+    for (int c0 = (int)(warp >> 2) * (K / 2); c0 < (int)(warp >> 2) * (K / 2) + K / 2; c0 += CH) {
       uint32_t r[32];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(tmem + ((warp * 32u) << 16) + (uint32_t)c0));
+      if constexpr (CH == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(lane_base + (uint32_t)c0));
+      } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15])
+            : "r"(lane_base + (uint32_t)c0));
+      }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 32; ++j) stage[row * K + ((c0 + j) ^ (row & 31))] = __uint_as_float(r[j]) * inv;
+      for (int j = 0; j < CH; ++j) stage[row * K + ((c0 + j) ^ (row & 31))] = __uint_as_float(r[j]) * inv;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     // ---- coalesced stores of the tile
-    for (int c = (int)(tid >> 6); c < K; c += 2)
+    for (int c = (int)q; c < K; c += 4)
       psi[base + ((int64_t)c << q0)] =
           make_float2(stage[u * K + (c ^ (u & 31))], stage[(u + kGroups) * K + (c ^ ((u + kGroups) & 31))]);
     __syncthreads();  // staging (aliasing A) is free for the next tile's split
@@ -280,7 +309,7 @@ static cudaError_t launch_tc_t(const InstDev* inst, const int32_t* list, int32_t
   const int per = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, ((int64_t)num_sms * 2 + nlist - 1) / nlist));
   const int64_t blocks = (int64_t)nlist * per;
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-  k_mixer_tc<KB, FP16><<<(unsigned)blocks, 128, smem, st>>>(inst, list, n, q0, layer, per, states, scale, err);
+  k_mixer_tc<KB, FP16><<<(unsigned)blocks, kThreads, smem, st>>>(inst, list, n, q0, layer, per, states, scale, err);
   return cudaGetLastError();
 }
 
