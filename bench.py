@@ -39,6 +39,23 @@ DENSITIES = (0.1, 0.5)
 WMAX = 10
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks (the job takes
+    as long as its slowest rank); the values themselves when not distributed."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_value(units_per_rank_step: float, steps: int, world: int, ms: float) -> float:
+    """Whole-job throughput under weak scaling: the units every rank processed
+    over the slowest rank's time."""
+    return units_per_rank_step * steps * world / (ms / 1e3)
+
+
 def workload(rank: int):
     return [synth.erdos_renyi(NV, pe, seed=rank, wmax=WMAX) for pe in DENSITIES]
 
@@ -624,16 +641,13 @@ def main():
         step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    ms, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
     large = None
     if rank == 0 and not args.no_large:
         large = large_learned(capi, pkg)
     amps_step = amp_layers_per_graph() * len(graphs)
-    value = amps_step * args.steps * world / (ms / 1e3)
-    e2e_value = amps_step * args.steps * world / e2e_s
+    value = job_value(amps_step, args.steps, world, ms)
+    e2e_value = job_value(amps_step, args.steps, world, e2e_s * 1e3)
     launches, lp_ms, lp_bytes = prof[capi.KCLASS_LAYER_PASS]
     peak, peak_kind = read_peaks()
     achieved = (lp_bytes / (lp_ms / 1e3)) / 1e9 if lp_ms > 0 else 0.0
