@@ -293,16 +293,6 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
   }
 }
 
-// Network output rows [gamma | beta] (FP32) -> FP64 angle arrays (rows x p each).
-__global__ void k_split_angles(const float* __restrict__ Y, int rows, int p, double* __restrict__ gamma,
-                               double* __restrict__ beta) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows * 2 * p) return;
-  const int r = i / (2 * p), c = i % (2 * p);
-  if (c < p) gamma[(int64_t)r * p + c] = (double)Y[i];
-  else beta[(int64_t)r * p + (c - p)] = (double)Y[i];
-}
-
 cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* y, int64_t n, cudaStream_t st) {
   k_to_bf16<<<nblk(n), 256, 0, st>>>(x, y, n);
   return cudaGetLastError();
@@ -330,11 +320,6 @@ cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n,
   const float b1 = 0.9f, b2 = 0.999f;
   k_adam<<<nblk(n), 256, 0, st>>>(w, g, m, v, n, lr, b1, b2, 1e-8f, 1.f - powf(b1, (float)t),
                                   1.f - powf(b2, (float)t), wb);
-  return cudaGetLastError();
-}
-cudaError_t launch_split_angles(const float* Y, int rows, int p, double* gamma, double* beta, cudaStream_t st) {
-  if (rows <= 0) return cudaSuccess;
-  k_split_angles<<<(rows * 2 * p + 255) / 256, 256, 0, st>>>(Y, rows, p, gamma, beta);
   return cudaGetLastError();
 }
 

@@ -82,7 +82,6 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
 int64_t cut_consts_elems(int kind, int32_t nlist);
-int layer_resident_per_sm(int kind);  // occupancy target of a tile shape (CTAs per SM)
 bool layer_kind_multi_tile(int kind);  // may the shape's CTAs walk several tiles
 cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
@@ -154,7 +153,6 @@ cudaError_t launch_relu_back_raw(float* dH, const float* Z, int64_t n, bf16_t* d
 cudaError_t launch_colsum(const float* dZ, int rows, int cols, float* db, cudaStream_t st);
 cudaError_t launch_adam_raw(float* w, const float* g, float* m, float* v, int64_t n, float lr, int t, bf16_t* wb,
                             cudaStream_t st);
-cudaError_t launch_split_angles(const float* Y, int rows, int p, double* gamma, double* beta, cudaStream_t st);
 
 // Split-precision tensor-core mixer variant (tc_mixer.cu).
 cudaError_t launch_mixer_tc(int kb, bool fp16, const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n,

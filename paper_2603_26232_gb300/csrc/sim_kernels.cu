@@ -852,7 +852,6 @@ size_t layer_pass_smem(int kind, int tabcap) {
 
 bool layer_kind_multi_tile(int kind) { return layer_multi_tile(kTileShapes[kind].tb, kTileShapes[kind].r); }
 
-int layer_resident_per_sm(int kind) { return layer_min_blocks(kTileShapes[kind].tb, kTileShapes[kind].r); }
 
 int64_t cut_consts_elems(int kind, int32_t nlist) {
   return (int64_t)nlist * cut_consts_stride(kTileShapes[kind].tb, kTileShapes[kind].r);
