@@ -120,7 +120,8 @@ int paraqaoa_cut_table(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t id,
 /* Sec. 2.2 / Sec. 3.3: simulate `count` QAOA instances. Instance i runs on
  * part ids[i] with angles gamma[i*p + l], beta[i*p + l] (FP64, host), starting
  * from |+>^n; the state is complex64. With PARAQAOA_SIM_EXPECT the
- * expectation <C> is reduced (FP32 terms, FP64 sums); with
+ * expectation <C> is reduced (per-thread FP32 sums of a few hundred
+ * terms at most, FP64 across threads and tiles); with
  * PARAQAOA_SIM_KEEP_STATE the final states stay on the device for
  * paraqaoa_topk / paraqaoa_state. Results replace those of the previous
  * call. Returns PARAQAOA_E_ADMISSION if the states would exceed the budget. */
@@ -321,7 +322,7 @@ int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
  * split schedules (classic: the low group is the tile's 2^12 or 2^13
  * contiguous qubits, mixed in up to three register rounds; split: the low
  * group is the 2R lowest qubits, mixed in two rounds with one transpose),
- * and for the 16-register shape 1, 2, 4 or 8 tiles per CTA (sharing the
+ * and for the 16-register shape 1, 2, 4, 8 or 16 tiles per CTA (sharing the
  * per-instance set-up loads). Choices that give the same pass schedule are
  * timed once. Optional outputs (31 entries each, indexed by n): chosen tile
  * bits, register bits per thread, minimum run, split flag, log2 tiles per
@@ -334,7 +335,7 @@ int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, i
 /* Set the layer-pass schedule of n-qubit parts by hand (the choice the
  * autotuner makes): tile bits and register bits per thread (one of the
  * shapes 12/5, 12/4, 13/5), minimum contiguous run c_min of the higher groups,
- * split (0 classic, 1 split) and log2 of the tiles each CTA walks (0..8;
+ * split (0 classic, 1 split) and log2 of the tiles each CTA walks (0..4;
  * above 0 only for the 12/4 shape). Affects later simulate calls of ctx. */
 int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2);

@@ -1298,7 +1298,7 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
 int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2) {
   if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || (split != 0 && split != 1) ||
-      tiles_per_cta_log2 < 0 || tiles_per_cta_log2 > 8)
+      tiles_per_cta_log2 < 0 || tiles_per_cta_log2 > kMaxTpcLog2)
     return PARAQAOA_E_INVAL;
   for (int kind = 0; kind < kTileKinds; ++kind)
     if (kTileShapes[kind].tb == tile_bits && kTileShapes[kind].r == reg_bits) {
@@ -1349,7 +1349,7 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
           const std::pair<int, int> key(G * 1000 + kind * 10 + sp, sched.size() > 1 ? sched[1].c : 0);
           if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
           seen.push_back(key);
-          for (int tpc = 0; tpc <= (layer_kind_multi_tile(kind) ? 3 : 0) && tpc <= n - tb; ++tpc)
+          for (int tpc = 0; tpc <= (layer_kind_multi_tile(kind) ? kMaxTpcLog2 : 0) && tpc <= n - tb; ++tpc)
             cands.push_back({kind, cm, sp, tpc, 1e30f});
         }
     }

@@ -24,6 +24,7 @@ constexpr int kMaxTileBits = 13;
 constexpr int kSmemMaxQubits = 14;  // states of <= 14 qubits stay on chip
 constexpr int kTinyMaxQubits = 9;   // n <= 9: one small CTA, plain loops
 constexpr int kMaxPlanes = 16;      // weight bit-planes (weights < 2^16)
+constexpr int kMaxTpcLog2 = 4;      // a layer-pass CTA walks at most 2^4 tiles
 
 // One subgraph on the device. Adjacency is stored as bit-planes: bit v of
 // planes[u*P + b] is bit b of w_uv (0 when u, v are not adjacent), so the
@@ -61,7 +62,7 @@ struct PassDesc {
   int32_t expect;   // reduce sum |psi|^2 C into the tile partial
   int32_t last;     // the final pass (stores apply lambda_p)
   int32_t split;    // low-group pass of a split schedule: mix local bits [0, 2R) in two rounds
-  int32_t tpc_log2; // each CTA processes 2^tpc_log2 consecutive tiles of one instance
+  int32_t tpc_log2; // each CTA processes 2^tpc_log2 tiles of one instance (strided by the CTAs per instance)
 };
 
 // Kernel launchers (sim_kernels.cu). All enqueue on `st` and return the

@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(1 << (TB - R))
   }
 }
 
-// Shapes whose CTAs may walk 2^tpc_log2 consecutive tiles (sharing the
+// Shapes whose CTAs may walk 2^tpc_log2 tiles of one instance (sharing the
 // per-instance set-up loads).
 __host__ __device__ constexpr bool layer_multi_tile(int tb, int r) { return r == 4; }
 
@@ -666,9 +666,13 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   const uint32_t tid = threadIdx.x;
   const int c = pd.c, s = pd.s, g = TB - c;
   const uint32_t lowt = (uint32_t)(s - c);
-  // this CTA's 2^tpc_log2 consecutive tiles, all of one instance
-  const uint32_t tile0 = blockIdx.x << pd.tpc_log2;
-  const int li_idx = (int)(tile0 >> tiles_log2);
+  // this CTA's 2^tpc_log2 tiles, all of one instance, strided by the
+  // instance's CTA count: CTAs that run side by side then cover consecutive
+  // tiles, which keeps the DRAM pages of a pass with short contiguous runs
+  // (a high qubit group) busy together
+  const uint32_t per = (uint32_t)(tiles_log2 - pd.tpc_log2);
+  const int li_idx = (int)(blockIdx.x >> per);
+  const uint32_t tj = blockIdx.x & ((1u << per) - 1u);
   const InstDev* Ip = inst_all + list[li_idx];
   const int P = Ip->P, W = Ip->W;
   const uint32_t* pl = planes_all + subs[Ip->sub].plane_off;
@@ -708,8 +712,13 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   // (Only the 16-register shape walks several tiles: the 32-register shapes
   // keep one tile per CTA, where the loop's live set would spill.)
   const uint32_t ntiles = layer_multi_tile(TB, R) ? (1u << pd.tpc_log2) : 1u;
+  // this thread's <C> terms over the CTA's tiles, summed in FP32 in two
+  // levels (2^R positive terms per tile, then at most 2^kMaxTpcLog2 tile
+  // sums: relative error below 48 x 2^-24, about 3e-6), FP64 from the block
+  // reduction on
+  float acc_cta = 0.f;
   for (uint32_t tt = 0; tt < ntiles; ++tt) {
-  const uint32_t tile = (tile0 + tt) & ((1u << tiles_log2) - 1u);
+  const uint32_t tile = tj | (tt << per);
   const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
   float2* base = states + Ip->state_off + (zbase | zmap(lt));
 
@@ -815,8 +824,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
       }
       acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)(S + qk[k]), acc);
     }
-    const double sum = block_sum((double)acc, red, tid, NT);
-    if (tid == 0) partials[Ip->part_off + tile] = sum;
+    acc_cta += acc;
   }
   if (pd.store) {
     if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
@@ -841,6 +849,17 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
     }
   }
   }  // tiles of this CTA
+  // One block reduction per CTA (the FP64 pipe is narrow and the reduction
+  // serialises the CTA): the sum goes to the partial slot of the CTA's first
+  // tile and its other tiles' slots get 0, so the per-instance reduction
+  // over tile slots is unchanged.
+  if (pd.expect) {
+    const double sum = block_sum((double)acc_cta, red, tid, NT);
+    if (tid == 0) {
+      partials[Ip->part_off + tj] = sum;
+      for (uint32_t tt = 1; tt < ntiles; ++tt) partials[Ip->part_off + (tj | (tt << per))] = 0.0;
+    }
+  }
 }
 
 size_t layer_pass_smem(int kind, int tabcap) {
@@ -903,7 +922,7 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
   if (e != cudaSuccess) return e;
   const int tiles_log2 = n - TB;
   const int tpc = layer_multi_tile(TB, R) ? pd.tpc_log2 : 0;
-  if (tpc < 0 || tpc > tiles_log2) return cudaErrorInvalidValue;
+  if (tpc < 0 || tpc > tiles_log2 || tpc > kMaxTpcLog2) return cudaErrorInvalidValue;
   const int64_t blocks = (int64_t)nlist << (tiles_log2 - tpc);
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
   // register slots each round mixes (mm0: layout 0, mm1: layout 1, mm2: layout 2)

@@ -404,6 +404,19 @@ def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
         capi.paraqaoa_part_free(part)
 
 
+def test_set_schedule_rejects_out_of_range(api):
+    """Host-side validation of hand-set schedules: unknown shapes, runs,
+    tiles per CTA above 2^4 or on a single-tile shape, split schedules that
+    do not fit the part."""
+    capi, ctx = api
+    for args in [(20, 12, 3, 2, 0, 0), (20, 12, 4, 9, 0, 0), (20, 12, 4, 2, 2, 0), (20, 12, 4, 2, 0, 5),
+                 (20, 12, 5, 2, 0, 1), (8, 12, 4, 2, 0, 0), (20, 14, 5, 2, 0, 0)]:
+        with pytest.raises(capi.ParaQAOAError):
+            capi.paraqaoa_set_schedule(ctx, *args)
+    capi.paraqaoa_set_schedule(ctx, 20, 12, 4, 2, 0, 4)   # the largest walk is accepted
+    capi.paraqaoa_set_schedule(ctx, 20, 12, 4, 3, 0)
+
+
 def test_large_parts_full_size(api, orc):
     """Parts of 25 and 26 qubits (the 16,000-vertex workload's sizes, 256 and
     512 MB complex64 states), p = 2, in the split schedule the autotuner picks
