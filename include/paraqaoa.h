@@ -341,8 +341,17 @@ int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32
                           int32_t split, int32_t tiles_per_cta_log2);
 
 /* Per-kernel device time recorded with CUDA events on the context stream.
- * enable != 0 starts recording (and clears the counters). */
+ * enable != 0 starts recording (and clears the counters). While it is on,
+ * size classes run in order on the context stream and Adam steps are
+ * launched one by one (no side streams, no graph replay), so that every
+ * launch can be bracketed. */
 int paraqaoa_profile_enable(paraqaoa_ctx *ctx, int32_t enable);
+/* Restrict the event brackets to the kernel classes whose bit is set in
+ * mask (bit k = PARAQAOA_KCLASS k; the default is every class). Launches
+ * and algorithmic bytes are still counted for every class; the device
+ * milliseconds of an unbracketed class read as 0. Fewer brackets leave
+ * fewer gaps between launches. */
+int paraqaoa_profile_classes(paraqaoa_ctx *ctx, uint32_t mask);
 /* Read one counter set: kernel class `which` (see PARAQAOA_KCLASS_*):
  * launches, summed device milliseconds and algorithmic bytes moved. */
 int paraqaoa_profile_read(paraqaoa_ctx *ctx, int32_t which, int64_t *launches, double *ms,

@@ -65,6 +65,7 @@ _SIGS = {
     "paraqaoa_set_schedule": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                ctypes.c_int32], ctypes.c_int),
     "paraqaoa_profile_enable": ([P, ctypes.c_int32], ctypes.c_int),
+    "paraqaoa_profile_classes": ([P, ctypes.c_uint32], ctypes.c_int),
     "paraqaoa_profile_read": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "paraqaoa_topk_noalloc": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, P, P, P], ctypes.c_int),
@@ -274,6 +275,11 @@ def paraqaoa_autotune(ctx, part, p: int = 2):
 
 def paraqaoa_profile_enable(ctx, enable: bool = True):
     _check(load().paraqaoa_profile_enable(ctx, 1 if enable else 0), "paraqaoa_profile_enable")
+
+
+def paraqaoa_profile_classes(ctx, mask: int):
+    """Bracket only the kernel classes whose bit is set (bit k = KCLASS k)."""
+    _check(load().paraqaoa_profile_classes(ctx, int(mask) & 0xFFFFFFFF), "paraqaoa_profile_classes")
 
 
 def paraqaoa_profile_read(ctx, which: int):

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -67,8 +68,6 @@ int bitlen(int64_t x) {
 struct ProfRec {
   int cls;
   cudaEvent_t a, b;
-  double bytes;
-  int kernels;
 };
 
 }  // namespace
@@ -93,9 +92,15 @@ struct SimPlan {
   std::vector<int32_t> lists;                   // concatenated instance lists
   std::pair<int32_t, int32_t> tiny{0, 0};       // offset, length into lists
   std::map<int, std::pair<int32_t, int32_t>> smem, hbm;  // n -> (offset, length)
+  // n -> (offset, length) into lists: one instance per distinct part of the
+  // class (the instances of a part share their cut constants)
+  std::map<int, std::pair<int32_t, int32_t>> hbm_reps;
   int64_t table_elems = 0, state_elems = 0, partial_elems = 0;
   int32_t tabcap = 1;  // largest W + 1 of the batch (phase-table entries on chip)
   bool valid = false;
+  // the layer passes' cut constants (functions of the parts and the pass
+  // layouts only) are on the device from an earlier run of this plan
+  bool cc_ready = false;
 };
 
 constexpr int kSideStreams = 4;
@@ -119,7 +124,7 @@ struct paraqaoa_ctx {
   // simulate
   SimPlan plan;
   DevBuf d_inst, d_lists, d_gamma, d_beta, d_tables, d_states, d_partials, d_expect;
-  DevBuf d_consts;  // per-instance cut constants of the current layer pass
+  DevBuf d_consts;  // cut constants of the current plan's layer passes (the tensor-core variant: its lists)
   // top-K
   DevBuf d_chunk_off, d_topk_scratch, d_topk_z, d_topk_p;
   // merge
@@ -136,6 +141,7 @@ struct paraqaoa_ctx {
   cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
   // profiling
   bool prof = false;
+  uint32_t prof_mask = ~0u;  // classes bracketed by events while profiling
   std::vector<ProfRec> pending;
   std::vector<cudaEvent_t> pool;
   int64_t launches[PARAQAOA_KCLASS_COUNT] = {};
@@ -155,6 +161,13 @@ cudaEvent_t get_event(paraqaoa_ctx* c) {
   return e;
 }
 
+void prof_flush(paraqaoa_ctx* c);
+
+// Records kept unread before a flush; the event pool is filled to cover them
+// when profiling is switched on, so a profiled run neither synchronises nor
+// creates events in the middle of a call.
+constexpr size_t kProfPendingMax = 16384;
+
 struct ProfScope {
   paraqaoa_ctx* c;
   int cls;
@@ -164,15 +177,20 @@ struct ProfScope {
   ProfScope(paraqaoa_ctx* c_, int cls_, double bytes_, int kernels_ = 1)
       : c(c_), cls(cls_), bytes(bytes_), kernels(kernels_) {
     if (c->prof) {
-      a = get_event(c);
-      cudaEventRecord(a, c->stream);
+      c->launches[cls] += kernels;
+      c->bytes[cls] += bytes;
+      if ((c->prof_mask >> cls) & 1u) {
+        a = get_event(c);
+        cudaEventRecord(a, c->stream);
+      }
     }
   }
   ~ProfScope() {
     if (c->prof && a) {
       cudaEvent_t b = get_event(c);
       cudaEventRecord(b, c->stream);
-      c->pending.push_back({cls, a, b, bytes, kernels});
+      c->pending.push_back({cls, a, b});
+      if (c->pending.size() >= kProfPendingMax) prof_flush(c);
     }
   }
 };
@@ -183,9 +201,7 @@ void prof_flush(paraqaoa_ctx* c) {
   for (auto& r : c->pending) {
     float t = 0.f;
     cudaEventElapsedTime(&t, r.a, r.b);
-    c->launches[r.cls] += r.kernels;
     c->ms[r.cls] += t;
-    c->bytes[r.cls] += r.bytes;
     c->pool.push_back(r.a);
     c->pool.push_back(r.b);
   }
@@ -310,6 +326,19 @@ int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int
   pl.tiny = t;
   for (auto& kv : smem) pl.smem[kv.first] = add(kv.second);
   for (auto& kv : hbm) pl.hbm[kv.first] = add(kv.second);
+  for (auto& kv : hbm) {
+    std::map<int32_t, int32_t> slot;  // part -> slot, in order of first appearance
+    std::vector<int32_t> reps;
+    for (int32_t i : kv.second) {
+      auto it = slot.find(pl.inst[i].sub);
+      if (it == slot.end()) {
+        it = slot.emplace(pl.inst[i].sub, (int32_t)reps.size()).first;
+        reps.push_back(i);
+      }
+      pl.inst[i].cc_slot = it->second;
+    }
+    pl.hbm_reps[kv.first] = add(reps);
+  }
   // admission: every byte this batch puts on the device
   const double need = (double)pl.state_elems * 8 + (double)pl.table_elems * 8 +
                       (double)pl.partial_elems * 8 + (double)count * (sizeof(InstDev) + 8 + 16 * p) +
@@ -368,9 +397,41 @@ int plan_run(paraqaoa_ctx* c) {
     const int k = used++ % kSideStreams;
     return c->side[k];
   };
+  // Cut constants: one array per size class and distinct cut layout of its
+  // schedule (a layout is fixed by the pass's qubit group and round count),
+  // computed by the first run of the plan and reused by the later ones (Adam
+  // steps, replayed graphs, the autotuner's timed runs).
+  struct ClassSched {
+    int kind, tb;
+    std::vector<PassDesc> sched;
+    std::vector<int> set;  // per pass: index of its cut layout (-1: no cut)
+    int nsets = 0;
+    int64_t off = 0, elems = 0;
+  };
+  std::map<int, ClassSched> cs;
   int64_t cc_total = 0;
-  for (auto& kv : pl.hbm) cc_total += cut_consts_elems(c->tile_kind[kv.first], kv.second.second);
-  PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * std::max<int64_t>(cc_total, 1)));
+  for (auto& kv : pl.hbm) {
+    const int n = kv.first;
+    ClassSched& q = cs[n];
+    q.kind = c->tile_kind[n];
+    q.tb = kTileShapes[q.kind].tb;
+    q.sched = make_schedule(n, p, q.tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[q.kind].r : 0);
+    std::vector<std::array<int, 4>> keys;
+    for (const PassDesc& pd : q.sched) {
+      int k = -1;
+      if (pd.layerP >= 0 || pd.expect) {
+        const std::array<int, 4> key{pd.c, pd.s, pd.split, pd.mix_lo};
+        k = (int)(std::find(keys.begin(), keys.end(), key) - keys.begin());
+        if (k == (int)keys.size()) keys.push_back(key);
+      }
+      q.set.push_back(k);
+    }
+    q.nsets = (int)keys.size();
+    q.elems = cut_consts_elems(q.kind, pl.hbm_reps[n].second);
+    q.off = cc_total;
+    cc_total += q.nsets * q.elems;
+  }
+  if (!pl.cc_ready) PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * std::max<int64_t>(cc_total, 1)));
   if (pl.tiny.second > 0) {
     cudaStream_t st = cls_stream();
     ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, 0);
@@ -383,21 +444,23 @@ int plan_run(paraqaoa_ctx* c) {
     PQ_CUDA(launch_smem_sim(kv.first, inst, lists + kv.second.first, kv.second.second, p, subs,
                             planes, tables, states, expect, keep, want, pl.tabcap, st));
   }
-  int64_t cc_off = 0;
   for (auto& kv : pl.hbm) {
     cudaStream_t st = cls_stream();
     const int n = kv.first;
-    const int kind = c->tile_kind[n], tb = kTileShapes[kind].tb;
-    const auto sched = make_schedule(n, p, tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[kind].r : 0);
+    const ClassSched& q = cs[n];
+    const int kind = q.kind, tb = q.tb;
     const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
-    int32_t* consts = c->d_consts.as<int32_t>() + cc_off;
-    cc_off += cut_consts_elems(kind, kv.second.second);
-    for (PassDesc pd : sched) {
+    const auto reps = pl.hbm_reps[n];
+    std::vector<char> done(q.nsets, pl.cc_ready ? 1 : 0);
+    for (size_t ip = 0; ip < q.sched.size(); ++ip) {
+      PassDesc pd = q.sched[ip];
       pd.tpc_log2 = std::min<int>(c->tpc_log2[n], n - tb);
-      if (pd.layerP >= 0 || pd.expect) {
+      const int k = q.set[ip];
+      int32_t* consts = c->d_consts.as<int32_t>() + q.off + (int64_t)std::max(k, 0) * q.elems;
+      if (k >= 0 && !done[k]) {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-        PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs, planes,
-                                  consts, st));
+        PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + reps.first, reps.second, subs, planes, consts, st));
+        done[k] = 1;
       }
       const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
       ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
@@ -415,6 +478,7 @@ int plan_run(paraqaoa_ctx* c) {
       PQ_CUDA(cudaEventRecord(c->join_ev[k], c->side[k]));
       PQ_CUDA(cudaStreamWaitEvent(c->stream, c->join_ev[k], 0));
     }
+  pl.cc_ready = true;
   return PARAQAOA_OK;
 }
 
@@ -782,7 +846,6 @@ int paraqaoa_expect(paraqaoa_ctx* c, int32_t count, double* out_host) {
   PQ_CUDA(cudaSetDevice(c->device));
   PQ_CUDA(cudaMemcpyAsync(out_host, c->d_expect.p, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
-  prof_flush(c);
   return PARAQAOA_OK;
 }
 
@@ -815,7 +878,6 @@ int paraqaoa_topk(paraqaoa_ctx* c, int32_t count, int32_t K, uint32_t* out_z, fl
   PQ_CUDA(cudaMemcpyAsync(out_z, c->d_topk_z.p, sizeof(uint32_t) * count * K, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaMemcpyAsync(out_p, c->d_topk_p.p, sizeof(float) * count * K, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
-  prof_flush(c);
   return PARAQAOA_OK;
 }
 
@@ -956,7 +1018,6 @@ int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* 
     const uint8_t flip = side[0];
     for (int32_t v = 0; v < nv; ++v) out_side[v] = side[v] ^ flip;
     *out_cut = (int64_t)(key >> 32);
-    prof_flush(c);
     return PARAQAOA_OK;
   }
   // beam reading
@@ -997,7 +1058,6 @@ int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* 
   const uint8_t flip = (uint8_t)(packed[0] & 1u);
   for (int32_t v = 0; v < nv; ++v) out_side[v] = (uint8_t)(((packed[v >> 5] >> (v & 31)) & 1u) ^ flip);
   *out_cut = best;
-  prof_flush(c);
   return PARAQAOA_OK;
 }
 
@@ -1054,7 +1114,6 @@ int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
     PQ_CUDA(cudaMemcpyAsync(out_values, c->o_vals.p, sizeof(double) * total, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
   c->plan.valid = false;
-  prof_flush(c);
   return PARAQAOA_OK;
 }
 
@@ -1170,7 +1229,6 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
     PQ_CUDA(cudaStreamSynchronize(c->stream));
     s0 += ns;
   }
-  prof_flush(c);
   return PARAQAOA_OK;
 }
 
@@ -1286,7 +1344,6 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   int herr = 0;
   PQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
-  prof_flush(c);
   if (herr) {
     pl.valid = false;
     return PARAQAOA_E_TIMEOUT;
@@ -1408,11 +1465,25 @@ int paraqaoa_profile_enable(paraqaoa_ctx* c, int32_t enable) {
   if (!c) return PARAQAOA_E_INVAL;
   prof_flush(c);
   c->prof = enable != 0;
+  // Event records are read back only by paraqaoa_profile_read (or when
+  // kProfPendingMax records are waiting), so that API calls return without
+  // a pass over their events while the GPU idles.
+  while (c->prof && c->pool.size() < 2 * kProfPendingMax) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) break;
+    c->pool.push_back(e);
+  }
   for (int k = 0; k < PARAQAOA_KCLASS_COUNT; ++k) {
     c->launches[k] = 0;
     c->ms[k] = 0;
     c->bytes[k] = 0;
   }
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_profile_classes(paraqaoa_ctx* c, uint32_t mask) {
+  if (!c) return PARAQAOA_E_INVAL;
+  c->prof_mask = mask;
   return PARAQAOA_OK;
 }
 

@@ -70,8 +70,20 @@ __global__ void k_adam_update(const double* __restrict__ expect, const double* _
   const double vv = b2 * v[q] + (1.0 - b2) * g * g;
   m[q] = mm;
   v[q] = vv;
-  const double mh = mm / (1.0 - pow(b1, (double)t));
-  const double vh = vv / (1.0 - pow(b2, (double)t));
+  // bias corrections b^t by binary powering: t is the step count, and a
+  // chain of a few FP64 multiplies is far shorter than pow() on the narrow
+  // FP64 pipe (relative difference ~1e-15)
+  double p1 = 1.0, p2 = 1.0, q1 = b1, q2 = b2;
+  for (int e = t; e > 0; e >>= 1) {
+    if (e & 1) {
+      p1 *= q1;
+      p2 *= q2;
+    }
+    q1 *= q1;
+    q2 *= q2;
+  }
+  const double mh = mm / (1.0 - p1);
+  const double vh = vv / (1.0 - p2);
   theta[q] -= lr * mh / (sqrt(vh) + eps);
 }
 

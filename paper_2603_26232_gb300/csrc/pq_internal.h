@@ -46,7 +46,7 @@ struct InstDev {
   float mu[PARAQAOA_MAX_P];  // mixer butterfly coefficient per layer
   float2 final_scale;        // lambda_p: scalar the last mixer left out
   float final_scale2;        // |lambda_p|^2
-  int32_t pad;
+  int32_t cc_slot;           // its part's slot in the layer passes' cut-constant arrays
 };
 
 // One layer pass over every tile of a group of same-size instances.
@@ -84,6 +84,7 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
 int64_t cut_consts_elems(int kind, int32_t nlist);
 bool layer_kind_multi_tile(int kind);  // may the shape's CTAs walk several tiles
+// `list`: one instance per distinct part, in cc_slot order
 cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
                               int32_t* consts, cudaStream_t st);

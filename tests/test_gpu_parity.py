@@ -473,6 +473,33 @@ def test_optimize_graph_replay_matches_direct_launches(api):
         assert np.array_equal(a, b)
 
 
+def test_profile_classes_mask(api):
+    """With the event brackets restricted to the layer passes, every class
+    still counts its launches and bytes, only the layer passes get device
+    time, and the results equal those of an unprofiled run."""
+    capi, ctx = api
+    g = synth.erdos_renyi(60, 0.3, 5, wmax=10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), 3)
+    try:
+        ids = np.arange(3, dtype=np.int32)
+        gam, bet = synth.random_angles(3, 2, 9)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+        ref = capi.paraqaoa_expect(ctx, 3)
+        capi.paraqaoa_profile_enable(ctx, True)
+        capi.paraqaoa_profile_classes(ctx, 1 << capi.KCLASS_LAYER_PASS)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+        ex = capi.paraqaoa_expect(ctx, 3)
+        lp = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
+        other = capi.paraqaoa_profile_read(ctx, capi.KCLASS_OTHER)
+    finally:
+        capi.paraqaoa_profile_enable(ctx, False)
+        capi.paraqaoa_profile_classes(ctx, 0xFFFFFFFF)
+        capi.paraqaoa_part_free(part)
+    assert np.array_equal(ex, ref)
+    assert lp[0] > 0 and lp[1] > 0 and lp[2] > 0
+    assert other[0] > 0 and other[1] == 0.0
+
+
 def test_size_classes_on_side_streams_match_serial(api, orc):
     """Uneven parts (9..22 qubits: tiny, on-chip and streamed classes) in one
     batch: with profiling off the size classes run concurrently on side
