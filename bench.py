@@ -86,16 +86,28 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_for(kernel_src: str, alg_bytes_per_launch: float):
+LAYER_PASS_SOURCES = [os.path.join(ROOT, "paper_2603_26232_gb300", "csrc", f)
+                      for f in ("layer_pass.cu", "sim_common.cuh")]
+
+
+def kernel_sources_sha256(paths) -> str:
+    """sha256 over the concatenated sources of a kernel (the layer pass and
+    the device helpers it includes)."""
+    h = hashlib.sha256()
+    for path in paths:
+        h.update(open(path, "rb").read())
+    return h.hexdigest()
+
+
+def traffic_for(kernel_srcs, alg_bytes_per_launch: float):
     """DRAM bytes per layer-pass launch: the ncu-measured DRAM/algorithmic ratio
     of profiles/layer_pass_traffic.json times this run's algorithmic bytes per
-    launch; None when the kernel source changed since that capture."""
+    launch; None when the kernel sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "layer_pass_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    if rec.get("source_sha256") != h:
+    if rec.get("source_sha256") != kernel_sources_sha256(kernel_srcs):
         return None
     return rec["dram_over_algorithmic"] * alg_bytes_per_launch
 
@@ -656,8 +668,7 @@ def main():
     launches, lp_ms, lp_bytes = prof[capi.KCLASS_LAYER_PASS]
     peak, peak_kind = read_peaks()
     achieved = (lp_bytes / (lp_ms / 1e3)) / 1e9 if lp_ms > 0 else 0.0
-    traffic = traffic_for(os.path.join(ROOT, "paper_2603_26232_gb300", "csrc", "sim_kernels.cu"),
-                          lp_bytes / max(launches, 1))
+    traffic = traffic_for(LAYER_PASS_SOURCES, lp_bytes / max(launches, 1))
     total_launches = sum(v[0] for v in prof.values())
     h2d = sum(int(G.row_ptr.nbytes + G.col.nbytes + G.w.nbytes) for G in Gs)
     d2h = len(Gs) * (M * K * 8 + NV + M * 8 * 3)

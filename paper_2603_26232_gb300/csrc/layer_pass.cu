@@ -1,0 +1,421 @@
+// The HBM-streaming layer pass (Sec. 2.2, Sec. 3.3): one pass over every
+// tile of a batch of same-size QAOA states finishes one layer's mixer on a
+// qubit group, applies the next cost phase and starts the next mixer, or
+// reduces <C>. The state representation (gauge, mixer arithmetic, cut
+// values) is described in sim_common.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "sim_common.cuh"
+
+namespace pq {
+
+// Cut values. With T the tile's qubits, F the fixed ones, J the qubits of the
+// thread index and K the 5 register qubits of the layout where the cut is
+// needed, C(z) = sum_u d_u z_u - 2 sum_{u<v} w_uv z_u z_v splits into
+//   C = C(z_F)                          per tile (z_T = 0)
+//     + sum_{u in J} lam_u z_u          lam_u = d_u - 2 sum_{v in F} w_uv z_v, per tile
+//     - 2 Q_J(z_J)                      per thread and instance (k_cut_consts)
+//     + sum_{u in K} z_u (lam_u + B_u)  B_u = -2 sum_{v in J} w_uv z_v, per thread (k_cut_consts)
+//     - 2 Q_K(z_K)                      32-entry table per instance (k_cut_consts)
+// so a cut value costs a broadcast load and a few integer adds.
+struct TileConst {
+  int cf;        // C(z_F)
+  int lam[16];   // lam_u per local bit
+  int pad[3];    // keeps what follows in shared memory 16-byte aligned
+};
+static_assert(sizeof(TileConst) % 16 == 0, "shared-memory carve-up needs 16-byte multiples");
+
+__host__ __device__ __forceinline__ uint32_t qubit_of(int lb, int c, int s) {
+  return lb < c ? (uint32_t)lb : (uint32_t)(s + (lb - c));
+}
+
+// Visit the 32 registers in Gray-code order so that consecutive registers
+// differ in one bit: per-register offsets then cost one add each.
+__host__ __device__ constexpr int gray(int i) { return i ^ (i >> 1); }
+__host__ __device__ constexpr int gray_bit(int i) { return i & 1 ? 0 : (i & 2 ? 1 : (i & 4 ? 2 : (i & 8 ? 3 : 4))); }
+
+// Entries per instance of the k_cut_consts output: 2^R (Q_K table) + (1 + R) per thread.
+__host__ __device__ constexpr int cut_consts_stride(int tb, int r) { return (1 << r) + (1 + r) * (1 << (tb - r)); }
+
+// Cut constants of one pass for the part of each listed instance (one CTA
+// per distinct part; the layer pass finds them by the instance's cc_slot),
+// for the cut layout of offset OC, at out + blockIdx.x * stride:
+// out[0..2^R) = -2 Q_K(k); out[2^R + t] = -2 Q_J(z_J(t)); out[2^R + (1+j) NT + t] =
+// B_u(t) of register slot j.
+template <int TB, int R, int OC>
+__global__ void __launch_bounds__(1 << (TB - R))
+    k_cut_consts(PassDesc pd, int32_t n, const InstDev* __restrict__ inst_all,
+                 const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
+                 const uint32_t* __restrict__ planes_all, int32_t* __restrict__ out) {
+  constexpr uint32_t NT = 1u << (TB - R);
+  constexpr int KQ = 1 << R;
+  __shared__ uint32_t pl[PARAQAOA_MAX_QUBITS * kMaxPlanes];
+  const uint32_t tid = threadIdx.x;
+  const InstDev* Ip = inst_all + list[blockIdx.x];
+  const SubDev S = subs[Ip->sub];
+  const int P = Ip->P, c = pd.c, s = pd.s;
+  for (uint32_t q = tid; q < (uint32_t)(n * P); q += NT) pl[q] = planes_all[S.plane_off + q];
+  __syncthreads();
+  int32_t* o = out + (int64_t)blockIdx.x * cut_consts_stride(TB, R);
+  if (tid < (uint32_t)KQ) {
+    uint32_t zk = 0;
+    for (int j = 0; j < R; ++j)
+      if ((tid >> j) & 1u) zk |= 1u << qubit_of(OC + j, c, s);
+    int acc = 0;
+    for (int j = 0; j < R; ++j) {
+      if (!((tid >> j) & 1u)) continue;
+      const uint32_t* row = pl + qubit_of(OC + j, c, s) * P;
+      for (int b = 0; b < P; ++b) acc += __popc(row[b] & zk) << b;
+    }
+    o[tid] = -acc;  // each pair of set K qubits counted from both ends
+  }
+  const uint32_t li0 = lir_o<TB, R, OC>(tid, 0);
+  uint32_t zJ = 0;
+  for (int lb = 0; lb < TB; ++lb)
+    if ((li0 >> lb) & 1u) zJ |= 1u << qubit_of(lb, c, s);
+  int acc = 0;
+  for (int u = 0; u < n; ++u) {
+    if (!((zJ >> u) & 1u)) continue;
+    const uint32_t* row = pl + u * P;
+    for (int b = 0; b < P; ++b) acc += __popc(row[b] & zJ) << b;
+  }
+  o[KQ + tid] = -acc;
+  for (int j = 0; j < R; ++j) {
+    const uint32_t* row = pl + qubit_of(OC + j, c, s) * P;
+    int bj = 0;
+    for (int b = 0; b < P; ++b) bj += __popc(row[b] & zJ) << b;
+    o[KQ + (1 + j) * NT + tid] = -2 * bj;
+  }
+}
+
+// Shapes whose CTAs may walk 2^tpc_log2 tiles of one instance (sharing the
+// per-instance set-up loads).
+__host__ __device__ constexpr bool layer_multi_tile(int tb, int r) { return r == 4; }
+
+// Occupancy target of a tile shape: resident CTAs per SM. The 16-register
+// shape fits 64 registers per thread (four CTAs of 256 threads); the 2^12 x 32
+// shape is held to 96 registers for five CTAs of 128 threads (a few bytes of
+// spills, measured 3% faster than four CTAs at 128 registers).
+__host__ __device__ constexpr int layer_min_blocks(int tb, int r) { return r == 4 ? 4 : (tb >= 13 ? 2 : 5); }
+
+template <int TB, int R, int NR, bool SPLIT>
+__global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
+    k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
+                 const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
+                 const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
+                 float2* __restrict__ states, double* __restrict__ partials, int32_t tabcap,
+                 const int32_t* __restrict__ consts, uint32_t mm0, uint32_t mm1, uint32_t mm2) {
+  constexpr uint32_t NT = 1u << (TB - R);
+  constexpr int KQ = 1 << R;  // registers per thread
+  constexpr int O0 = lay_off(TB, R, SPLIT, 0), O1 = lay_off(TB, R, SPLIT, 1), O2 = lay_off(TB, R, SPLIT, 2);
+  constexpr int OC = lay_off(TB, R, SPLIT, NR - 1);  // layout of the cut step (phase / <C>)
+  static_assert(!SPLIT || NR == 2, "split passes mix two rounds");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* tab = reinterpret_cast<float2*>(smraw);
+  float2* sm = tab + tabcap;
+  int* qk = reinterpret_cast<int*>(sm + padded_r<TB, R>());  // 2^R entries (<= 32)
+  TileConst* tc = reinterpret_cast<TileConst*>(qk + 32);
+  uint32_t* pls = reinterpret_cast<uint32_t*>(tc + 1);  // the instance's bit-planes
+  double* red = reinterpret_cast<double*>(pls + PARAQAOA_MAX_QUBITS * kMaxPlanes);
+  const uint32_t tid = threadIdx.x;
+  const int c = pd.c, s = pd.s, g = TB - c;
+  const uint32_t lowt = (uint32_t)(s - c);
+  // this CTA's 2^tpc_log2 tiles, all of one instance, strided by the
+  // instance's CTA count: CTAs that run side by side then cover consecutive
+  // tiles, which keeps the DRAM pages of a pass with short contiguous runs
+  // (a high qubit group) busy together
+  const uint32_t per = (uint32_t)(tiles_log2 - pd.tpc_log2);
+  const int li_idx = (int)(blockIdx.x >> per);
+  const uint32_t tj = blockIdx.x & ((1u << per) - 1u);
+  const InstDev* Ip = inst_all + list[li_idx];
+  const int P = Ip->P, W = Ip->W;
+  const uint32_t* pl = planes_all + subs[Ip->sub].plane_off;
+  const bool need_cut = pd.layerP >= 0 || pd.expect;
+
+  // ---- set-up. One round of global loads, all issued before the first
+  // barrier (the state loads below too): the phase table, the instance's
+  // adjacency bit-planes, the Q_K table and this thread's cut constants.
+  // After the barrier warp 0 derives the tile constants from the planes in
+  // shared memory.
+  if (pd.layerP >= 0) {
+    const float2* tl = tables + Ip->table_off + (int64_t)pd.layerP * (W + 1);
+    for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
+  }
+  const int32_t* cc_inst = consts + (int64_t)Ip->cc_slot * cut_consts_stride(TB, R);
+  int ccJ = 0, ccB[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) ccB[j] = 0;
+  if (need_cut) {
+    for (int q = tid; q < n * P; q += NT) pls[q] = pl[q];
+    if (tid < (uint32_t)KQ) qk[tid] = cc_inst[tid];
+    ccJ = cc_inst[KQ + tid];
+#pragma unroll
+    for (int j = 0; j < R; ++j) ccB[j] = cc_inst[KQ + (1 + j) * NT + tid];
+  }
+  // Local index -> qubit offset: local bits [0, c) are qubits [0, c), bits
+  // [c, TB) move up by s - c (a monotone bit map, so it keeps popcounts).
+  const uint32_t lowm = (1u << c) - 1u;
+  const int sh = s - c;
+  auto zmap = [&](uint32_t li) -> uint32_t { return (li & lowm) | ((li & ~lowm) << sh); };
+  // load/store layout O0: this thread's amplitude offsets are zmap(lt | register bits)
+  const uint32_t lt = lir_o<TB, R, O0>(tid, 0);
+  // Tiles of one CTA share the set-up above. Across iterations the barriers
+  // below order every reuse of shared memory: warp 0 rewrites the tile
+  // constants only after the first barrier of the next tile, which every
+  // thread reaches after its last read of them.
+  // (Only the 16-register shape walks several tiles: the 32-register shapes
+  // keep one tile per CTA, where the loop's live set would spill.)
+  const uint32_t ntiles = layer_multi_tile(TB, R) ? (1u << pd.tpc_log2) : 1u;
+  // this thread's <C> terms over the CTA's tiles, summed in FP32 in two
+  // levels (2^R positive terms per tile, then at most 2^kMaxTpcLog2 tile
+  // sums: relative error below 48 x 2^-24, about 3e-6), FP64 from the block
+  // reduction on
+  float acc_cta = 0.f;
+  for (uint32_t tt = 0; tt < ntiles; ++tt) {
+  const uint32_t tile = tj | (tt << per);
+  const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
+  float2* base = states + Ip->state_off + (zbase | zmap(lt));
+
+  float2 a[KQ];
+  const uint32_t li0 = lir_o<TB, R, OC>(tid, 0);
+  if (pd.init) {  // s_z = i^popcount(z), z = tile base | thread qubits | register qubits
+    const int r = __popc(zbase | zmap(li0));
+    const float sg = (r & 2) ? -1.f : 1.f;
+    const float2 b = (r & 1) ? make_float2(0.f, sg) : make_float2(sg, 0.f);
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) a[k] = rot_i(b, popc_c(k));
+  } else {
+    uint32_t e[R];  // qubit offsets of the register slots
+#pragma unroll
+    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (O0 + j));
+    uint32_t off = 0;
+    a[0] = base[0];
+#pragma unroll
+    for (int i = 1; i < KQ; ++i) {
+      const int k = gray(i), b = gray_bit(i);
+      off = ((k >> b) & 1) ? off + e[b] : off - e[b];
+      a[k] = base[off];
+    }
+  }
+  __syncthreads();  // phase table, planes and Q_K visible
+  int A = 0, kap[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) kap[j] = 0;
+  if (need_cut) {
+    if (tid < 32) {
+      // lane u < n: contribution of vertex u to C(z_F); lane u < TB: lam of local bit u
+      int cfu = 0;
+      if ((int)tid < n && ((zbase >> tid) & 1u)) {
+        const uint32_t* row = pls + tid * P;
+        for (int b = 0; b < P; ++b) cfu += __popc(row[b] & ~zbase) << b;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cfu += __shfl_xor_sync(0xffffffffu, cfu, o);
+      if (tid < (uint32_t)TB) {
+        const uint32_t* row = pls + qubit_of(tid, c, s) * P;
+        int d = 0, aa = 0;
+        for (int b = 0; b < P; ++b) {
+          d += __popc(row[b]) << b;
+          aa += __popc(row[b] & zbase) << b;
+        }
+        tc->lam[tid] = d - 2 * aa;
+      }
+      if (tid == 0) tc->cf = cfu;
+    }
+    __syncthreads();  // tile constants visible
+    A = tc->cf + ccJ;
+#pragma unroll
+    for (int b = 0; b < TB - R; ++b) A += ((tid >> b) & 1u) ? tc->lam[thread_bit_local_o<R, OC>(b)] : 0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) kap[j] = tc->lam[OC + j] + ccB[j];
+  }
+  // round 2 (layout 2) only ever mixes slots below TB - 2R (the others repeat layout 1's)
+  constexpr uint32_t kAll = (1u << R) - 1u;
+  constexpr uint32_t kLow2 = SPLIT || (TB - 2 * R) >= R ? kAll : ((1u << (TB - 2 * R > 0 ? TB - 2 * R : 0)) - 1u);
+  if (pd.layerA >= 0) {
+    const float muA = Ip->mu[pd.layerA];
+    mix_regs_sel<R, kAll>(a, muA, mm0);
+    if constexpr (NR > 1) {
+      transposer_o<TB, R, O0, O1>(a, sm, tid);
+      mix_regs_sel<R, kAll>(a, muA, mm1);
+    }
+    if constexpr (NR > 2) {
+      transposer_o<TB, R, O1, O2>(a, sm, tid);
+      mix_regs_sel<R, kLow2>(a, muA, mm2);
+    }
+  }
+  if (pd.layerP >= 0) {
+    int S = A;
+    a[0] = cmul(a[0], tab[tix(S + qk[0], W)]);
+#pragma unroll
+    for (int i = 1; i < KQ; ++i) {
+      const int k = gray(i), b = gray_bit(i);
+      S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
+      a[k] = cmul(a[k], tab[tix(S + qk[k], W)]);
+    }
+  }
+  if (pd.layerB >= 0) {
+    const float muB = Ip->mu[pd.layerB];
+    if constexpr (NR > 2) {
+      mix_regs_sel<R, kLow2>(a, muB, mm2);
+      transposer_o<TB, R, O2, O1>(a, sm, tid);
+    }
+    if constexpr (NR > 1) {
+      mix_regs_sel<R, kAll>(a, muB, mm1);
+      transposer_o<TB, R, O1, O0>(a, sm, tid);
+    }
+    mix_regs_sel<R, kAll>(a, muB, mm0);
+  }
+  if (pd.expect) {
+    float acc = 0.f;
+    int S = A;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) {
+      const int k = gray(i);
+      if (i > 0) {
+        const int b = gray_bit(i);
+        S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
+      }
+      acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)(S + qk[k]), acc);
+    }
+    acc_cta += acc;
+  }
+  if (pd.store) {
+    if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
+      if constexpr (NR == 3) transposer_o<TB, R, O2, O0>(a, sm, tid);
+      if constexpr (NR == 2) transposer_o<TB, R, O1, O0>(a, sm, tid);
+    }
+    if (pd.last) {  // back from the gauge, times lambda_p
+      const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zmap(lt)));
+#pragma unroll
+      for (int k = 0; k < KQ; ++k) a[k] = cmul(a[k], rot_i(fs, -popc_c(k)));
+    }
+    uint32_t e[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) e[j] = zmap(1u << (O0 + j));
+    uint32_t off = 0;
+    base[0] = a[0];
+#pragma unroll
+    for (int i = 1; i < KQ; ++i) {
+      const int k = gray(i), b = gray_bit(i);
+      off = ((k >> b) & 1) ? off + e[b] : off - e[b];
+      base[off] = a[k];
+    }
+  }
+  }  // tiles of this CTA
+  // One block reduction per CTA (the FP64 pipe is narrow and the reduction
+  // serialises the CTA): the sum goes to the partial slot of the CTA's first
+  // tile and its other tiles' slots get 0, so the per-instance reduction
+  // over tile slots is unchanged.
+  if (pd.expect) {
+    const double sum = block_sum((double)acc_cta, red, tid, NT);
+    if (tid == 0) {
+      partials[Ip->part_off + tj] = sum;
+      for (uint32_t tt = 1; tt < ntiles; ++tt) partials[Ip->part_off + (tj | (tt << per))] = 0.0;
+    }
+  }
+}
+
+size_t layer_pass_smem(int kind, int tabcap) {
+  const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
+  const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - r));
+  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
+         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 16 * sizeof(double);
+}
+
+bool layer_kind_multi_tile(int kind) { return layer_multi_tile(kTileShapes[kind].tb, kTileShapes[kind].r); }
+
+
+int64_t cut_consts_elems(int kind, int32_t nlist) {
+  return (int64_t)nlist * cut_consts_stride(kTileShapes[kind].tb, kTileShapes[kind].r);
+}
+
+static int pass_rounds(int tb, int r, const PassDesc& pd) {
+  if (pd.split) return 2;
+  return 1 + (pd.mix_lo < tb - r) + (pd.mix_lo < tb - 2 * r);
+}
+
+template <int TB, int R, int OC>
+static cudaError_t launch_cc_t(int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                               int32_t* consts, cudaStream_t st) {
+  k_cut_consts<TB, R, OC><<<nlist, 1 << (TB - R), 0, st>>>(pd, n, inst, list, subs, planes, consts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                              int32_t nlist, const SubDev* subs, const uint32_t* planes,
+                              int32_t* consts, cudaStream_t st) {
+  if (nlist <= 0 || !(pd.layerP >= 0 || pd.expect)) return cudaSuccess;
+  const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
+  const int rc = pass_rounds(tb, r, pd) - 1;
+#define PQ_CC(TBV, RV) \
+  do { \
+    if (tb == TBV && r == RV) { \
+      if (pd.split) return launch_cc_t<TBV, RV, lay_off(TBV, RV, true, 1)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      if (rc == 0) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 0)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      if (rc == 1) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 1)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 2)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+    } \
+  } while (0)
+  PQ_CC(12, 5);
+  PQ_CC(12, 4);
+  PQ_CC(13, 5);
+#undef PQ_CC
+  return cudaErrorInvalidValue;
+}
+
+template <int TB, int R, int NR, bool SPLIT>
+static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const InstDev* inst,
+                                  const int32_t* list, int32_t nlist, const SubDev* subs,
+                                  const uint32_t* planes, const float2* tables, float2* states,
+                                  double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
+  const size_t smem = layer_pass_smem(kind, tabcap);
+  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, R, NR, SPLIT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tiles_log2 = n - TB;
+  const int tpc = layer_multi_tile(TB, R) ? pd.tpc_log2 : 0;
+  if (tpc < 0 || tpc > tiles_log2 || tpc > kMaxTpcLog2) return cudaErrorInvalidValue;
+  const int64_t blocks = (int64_t)nlist << (tiles_log2 - tpc);
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  // register slots each round mixes (mm0: layout 0, mm1: layout 1, mm2: layout 2)
+  uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
+  for (int j = 0; j < R; ++j) {
+    if (SPLIT || TB - R + j >= pd.mix_lo) mm0 |= 1u << j;
+    if (SPLIT || TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
+    if (!SPLIT && j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
+  }
+  k_layer_pass<TB, R, NR, SPLIT><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
+      pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts, mm0, mm1, mm2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev* inst,
+                              const int32_t* list, int32_t nlist, const SubDev* subs,
+                              const uint32_t* planes, const float2* tables, float2* states,
+                              double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
+  if (nlist <= 0) return cudaSuccess;
+  if (kind < 0 || kind >= kTileKinds) return cudaErrorInvalidValue;
+  const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
+  if (n < tb) return cudaErrorInvalidValue;
+  const int nr = pass_rounds(tb, r, pd);
+#define PQ_LAUNCH(TBV, RV) \
+  do { \
+    if (tb == TBV && r == RV) { \
+      if (pd.split) return launch_layer_t<TBV, RV, 2, true>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      if (nr == 1) return launch_layer_t<TBV, RV, 1, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      if (nr == 2) return launch_layer_t<TBV, RV, 2, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      return launch_layer_t<TBV, RV, 3, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+    } \
+  } while (0)
+  PQ_LAUNCH(12, 5);
+  PQ_LAUNCH(12, 4);
+  PQ_LAUNCH(13, 5);
+#undef PQ_LAUNCH
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pq

@@ -32,7 +32,7 @@ def sources() -> list[str]:
 
 def _deps() -> list[str]:
     inc = os.path.join(os.path.dirname(HERE), "include", "paraqaoa.h")
-    return sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")] + [inc]
+    return sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + [inc]
 
 
 def up_to_date() -> bool:
