@@ -322,12 +322,14 @@ int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
  * split schedules (classic: the low group is the tile's 2^12 or 2^13
  * contiguous qubits, mixed in up to three register rounds; split: the low
  * group is the 2R lowest qubits, mixed in two rounds with one transpose),
- * and for the 16-register shape 1, 2, 4, 8 or 16 tiles per CTA (sharing the
- * per-instance set-up loads). Choices that give the same pass schedule are
+ * and 1, 2, 4, 8 or 16 tiles per CTA (sharing the per-instance set-up
+ * loads and the <C> reduction). Choices that give the same pass schedule are
  * timed once. Optional outputs (31 entries each, indexed by n): chosen tile
  * bits, register bits per thread, minimum run, split flag, log2 tiles per
- * CTA. Without a call the context uses the classic 2^12 x 16-register
- * schedule, one tile per CTA, unless 2^13 needs fewer passes. */
+ * CTA. Without a call the context uses the choices measured on a p = 2
+ * sweep of G(*, 0.3) parts: (12/5, run 2, split, 2 tiles per CTA) up to 18
+ * qubits, (12/4, 2, classic, 8) for 19-20, (13/5, 2, classic, 4) for 21-24
+ * and (12/5, 2, split, 4) from 25. */
 int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, int32_t *out_tile_bits,
                       int32_t *out_reg_bits, int32_t *out_c_min, int32_t *out_split,
                       int32_t *out_tiles_per_cta_log2);
@@ -335,8 +337,8 @@ int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, i
 /* Set the layer-pass schedule of n-qubit parts by hand (the choice the
  * autotuner makes): tile bits and register bits per thread (one of the
  * shapes 12/5, 12/4, 13/5), minimum contiguous run c_min of the higher groups,
- * split (0 classic, 1 split) and log2 of the tiles each CTA walks (0..4;
- * above 0 only for the 12/4 shape). Affects later simulate calls of ctx. */
+ * split (0 classic, 1 split) and log2 of the tiles each CTA walks (0..4).
+ * Affects later simulate calls of ctx. */
 int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2);
 

@@ -614,12 +614,30 @@ int paraqaoa_create(paraqaoa_ctx** out, int device, size_t hbm_budget) {
   }
   c->budget = hbm_budget;
   for (int n = 0; n <= PARAQAOA_MAX_QUBITS; ++n) {
-    // default: the smaller tile (more CTAs per SM) unless it needs more passes
-    // default: the 2^12 tile with 16 registers per thread (highest occupancy)
-    // unless the 2^13 tile needs fewer passes
-    c->c_min[n] = 3;
-    c->tile_kind[n] = (n >= kMaxTileBits && schedule_groups(n, kMinTileBits, 3, 0) > schedule_groups(n, kMaxTileBits, 3, 0))
-                          ? 2 : 1;
+    // Default schedules: the autotuner's choices on the p = 2 amplitude-layer
+    // sweep (parts of G(*, 0.3), weights 1..10): 2^12 x 32-register split
+    // schedules up to 18 qubits, 2^12 x 16 classic walking 8 tiles per CTA for
+    // 19-20, 2^13 x 32 classic walking 4 tiles for 21-24, and the split
+    // schedule walking 4 tiles from 25 qubits (three qubit groups). Parts of
+    // other graphs may prefer another; paraqaoa_autotune measures.
+    c->c_min[n] = 2;
+    if (n <= 18) {
+      c->tile_kind[n] = 0;
+      c->split[n] = 1;
+      c->tpc_log2[n] = 1;
+    } else if (n <= 20) {
+      c->tile_kind[n] = 1;
+      c->split[n] = 0;
+      c->tpc_log2[n] = 3;
+    } else if (n <= 24) {
+      c->tile_kind[n] = 2;
+      c->split[n] = 0;
+      c->tpc_log2[n] = 2;
+    } else {
+      c->tile_kind[n] = 0;
+      c->split[n] = 1;
+      c->tpc_log2[n] = 2;
+    }
   }
   *out = c;
   return PARAQAOA_OK;
@@ -1360,7 +1378,6 @@ int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t
   for (int kind = 0; kind < kTileKinds; ++kind)
     if (kTileShapes[kind].tb == tile_bits && kTileShapes[kind].r == reg_bits) {
       if (n < tile_bits || (split && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
-      if (tiles_per_cta_log2 > 0 && !layer_kind_multi_tile(kind)) return PARAQAOA_E_INVAL;
       c->tile_kind[n] = (int8_t)kind;
       c->c_min[n] = (int8_t)c_min;
       c->split[n] = (int8_t)split;
@@ -1406,7 +1423,7 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
           const std::pair<int, int> key(G * 1000 + kind * 10 + sp, sched.size() > 1 ? sched[1].c : 0);
           if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
           seen.push_back(key);
-          for (int tpc = 0; tpc <= (layer_kind_multi_tile(kind) ? kMaxTpcLog2 : 0) && tpc <= n - tb; ++tpc)
+          for (int tpc = 0; tpc <= kMaxTpcLog2 && tpc <= n - tb; ++tpc)
             cands.push_back({kind, cm, sp, tpc, 1e30f});
         }
     }

@@ -90,10 +90,6 @@ __global__ void __launch_bounds__(1 << (TB - R))
   }
 }
 
-// Shapes whose CTAs may walk 2^tpc_log2 tiles of one instance (sharing the
-// per-instance set-up loads).
-__host__ __device__ constexpr bool layer_multi_tile(int tb, int r) { return r == 4; }
-
 // Occupancy target of a tile shape: resident CTAs per SM. The 16-register
 // shape fits 64 registers per thread (four CTAs of 256 threads); the 2^12 x 32
 // shape is held to 96 registers for five CTAs of 128 threads (a few bytes of
@@ -165,9 +161,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   // below order every reuse of shared memory: warp 0 rewrites the tile
   // constants only after the first barrier of the next tile, which every
   // thread reaches after its last read of them.
-  // (Only the 16-register shape walks several tiles: the 32-register shapes
-  // keep one tile per CTA, where the loop's live set would spill.)
-  const uint32_t ntiles = layer_multi_tile(TB, R) ? (1u << pd.tpc_log2) : 1u;
+  const uint32_t ntiles = 1u << pd.tpc_log2;
   // this thread's <C> terms over the CTA's tiles, summed in FP32 in two
   // levels (2^R positive terms per tile, then at most 2^kMaxTpcLog2 tile
   // sums: relative error below 48 x 2^-24, about 3e-6), FP64 from the block
@@ -325,7 +319,6 @@ size_t layer_pass_smem(int kind, int tabcap) {
          PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 16 * sizeof(double);
 }
 
-bool layer_kind_multi_tile(int kind) { return layer_multi_tile(kTileShapes[kind].tb, kTileShapes[kind].r); }
 
 
 int64_t cut_consts_elems(int kind, int32_t nlist) {
@@ -377,7 +370,7 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles_log2 = n - TB;
-  const int tpc = layer_multi_tile(TB, R) ? pd.tpc_log2 : 0;
+  const int tpc = pd.tpc_log2;
   if (tpc < 0 || tpc > tiles_log2 || tpc > kMaxTpcLog2) return cudaErrorInvalidValue;
   const int64_t blocks = (int64_t)nlist << (tiles_log2 - tpc);
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;

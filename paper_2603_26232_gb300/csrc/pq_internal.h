@@ -19,8 +19,6 @@ struct TileShape {
 };
 constexpr int kTileKinds = 3;
 constexpr TileShape kTileShapes[kTileKinds] = {{12, 5}, {12, 4}, {13, 5}};
-constexpr int kMinTileBits = 12;
-constexpr int kMaxTileBits = 13;
 constexpr int kSmemMaxQubits = 14;  // states of <= 14 qubits stay on chip
 constexpr int kTinyMaxQubits = 9;   // n <= 9: one small CTA, plain loops
 constexpr int kMaxPlanes = 16;      // weight bit-planes (weights < 2^16)
@@ -83,7 +81,6 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
 int64_t cut_consts_elems(int kind, int32_t nlist);
-bool layer_kind_multi_tile(int kind);  // may the shape's CTAs walk several tiles
 // `list`: one instance per distinct part, in cc_slot order
 cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,

@@ -373,7 +373,8 @@ def test_autotune_choices_keep_parity(api, orc):
 
 
 @pytest.mark.parametrize("tb,rb,split,tpc", [(12, 5, 0, 0), (12, 4, 0, 0), (13, 5, 0, 0), (12, 5, 1, 0), (12, 4, 1, 0),
-                                             (13, 5, 1, 0), (12, 4, 0, 3), (12, 4, 1, 2)])
+                                             (13, 5, 1, 0), (12, 4, 0, 3), (12, 4, 1, 2), (12, 5, 0, 2),
+                                             (12, 5, 1, 3), (13, 5, 0, 1), (13, 5, 1, 2)])
 def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
     """Every tile shape in classic and split schedules, one or several tiles
     per CTA, on parts of 15..24 qubits (two and three qubit groups), depth 3,
@@ -406,11 +407,10 @@ def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
 
 def test_set_schedule_rejects_out_of_range(api):
     """Host-side validation of hand-set schedules: unknown shapes, runs,
-    tiles per CTA above 2^4 or on a single-tile shape, split schedules that
-    do not fit the part."""
+    tiles per CTA above 2^4, split schedules that do not fit the part."""
     capi, ctx = api
     for args in [(20, 12, 3, 2, 0, 0), (20, 12, 4, 9, 0, 0), (20, 12, 4, 2, 2, 0), (20, 12, 4, 2, 0, 5),
-                 (20, 12, 5, 2, 0, 1), (8, 12, 4, 2, 0, 0), (20, 14, 5, 2, 0, 0)]:
+                 (20, 13, 5, 2, 0, 5), (8, 12, 4, 2, 0, 0), (20, 14, 5, 2, 0, 0)]:
         with pytest.raises(capi.ParaQAOAError):
             capi.paraqaoa_set_schedule(ctx, *args)
     capi.paraqaoa_set_schedule(ctx, 20, 12, 4, 2, 0, 4)   # the largest walk is accepted
