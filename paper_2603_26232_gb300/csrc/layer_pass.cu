@@ -96,7 +96,10 @@ __global__ void __launch_bounds__(1 << (TB - R))
 // spills, measured 3% faster than four CTAs at 128 registers).
 __host__ __device__ constexpr int layer_min_blocks(int tb, int r) { return r == 4 ? 4 : (tb >= 13 ? 2 : 5); }
 
-template <int TB, int R, int NR, bool SPLIT>
+// CONTIG: the pass's tile is 2^TB contiguous amplitudes (the low qubit
+// group, c = s = TB), so every register slot's offset is a compile-time
+// constant and loads and stores take immediate offsets from one base.
+template <int TB, int R, int NR, bool SPLIT, bool CONTIG>
 __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
     k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
                  const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   uint32_t* pls = reinterpret_cast<uint32_t*>(tc + 1);  // the instance's bit-planes
   double* red = reinterpret_cast<double*>(pls + PARAQAOA_MAX_QUBITS * kMaxPlanes);
   const uint32_t tid = threadIdx.x;
-  const int c = pd.c, s = pd.s, g = TB - c;
+  const int c = CONTIG ? TB : pd.c, s = CONTIG ? TB : pd.s, g = TB - c;
   const uint32_t lowt = (uint32_t)(s - c);
   // this CTA's 2^tpc_log2 tiles, all of one instance, strided by the
   // instance's CTA count: CTAs that run side by side then cover consecutive
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   // [c, TB) move up by s - c (a monotone bit map, so it keeps popcounts).
   const uint32_t lowm = (1u << c) - 1u;
   const int sh = s - c;
-  auto zmap = [&](uint32_t li) -> uint32_t { return (li & lowm) | ((li & ~lowm) << sh); };
+  auto zmap = [&](uint32_t li) -> uint32_t { return CONTIG ? li : (li & lowm) | ((li & ~lowm) << sh); };
   // load/store layout O0: this thread's amplitude offsets are zmap(lt | register bits)
   const uint32_t lt = lir_o<TB, R, O0>(tid, 0);
   // Tiles of one CTA share the set-up above. Across iterations the barriers
@@ -360,13 +363,14 @@ cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev
   return cudaErrorInvalidValue;
 }
 
-template <int TB, int R, int NR, bool SPLIT>
+template <int TB, int R, int NR, bool SPLIT, bool CONTIG>
 static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const InstDev* inst,
                                   const int32_t* list, int32_t nlist, const SubDev* subs,
                                   const uint32_t* planes, const float2* tables, float2* states,
                                   double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
   const size_t smem = layer_pass_smem(kind, tabcap);
-  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, R, NR, SPLIT>,
+  if (CONTIG && (pd.c != TB || pd.s != TB)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, R, NR, SPLIT, CONTIG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int tiles_log2 = n - TB;
@@ -381,7 +385,7 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
     if (SPLIT || TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
     if (!SPLIT && j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
   }
-  k_layer_pass<TB, R, NR, SPLIT><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
+  k_layer_pass<TB, R, NR, SPLIT, CONTIG><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
       pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts, mm0, mm1, mm2);
   return cudaGetLastError();
 }
@@ -395,19 +399,26 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
   const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
   if (n < tb) return cudaErrorInvalidValue;
   const int nr = pass_rounds(tb, r, pd);
+  // split passes always cover the contiguous low group; classic passes over
+  // it mix all TB local bits in three rounds
+  const bool contig = pd.c == tb && pd.s == tb;
+  if (pd.split && !contig) return cudaErrorInvalidValue;
+#define PQ_ARGS kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st
 #define PQ_LAUNCH(TBV, RV) \
   do { \
     if (tb == TBV && r == RV) { \
-      if (pd.split) return launch_layer_t<TBV, RV, 2, true>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
-      if (nr == 1) return launch_layer_t<TBV, RV, 1, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
-      if (nr == 2) return launch_layer_t<TBV, RV, 2, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
-      return launch_layer_t<TBV, RV, 3, false>(kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st); \
+      if (pd.split) return launch_layer_t<TBV, RV, 2, true, true>(PQ_ARGS); \
+      if (contig && nr == 3) return launch_layer_t<TBV, RV, 3, false, true>(PQ_ARGS); \
+      if (nr == 1) return launch_layer_t<TBV, RV, 1, false, false>(PQ_ARGS); \
+      if (nr == 2) return launch_layer_t<TBV, RV, 2, false, false>(PQ_ARGS); \
+      return launch_layer_t<TBV, RV, 3, false, false>(PQ_ARGS); \
     } \
   } while (0)
   PQ_LAUNCH(12, 5);
   PQ_LAUNCH(12, 4);
   PQ_LAUNCH(13, 5);
 #undef PQ_LAUNCH
+#undef PQ_ARGS
   return cudaErrorInvalidValue;
 }
 
