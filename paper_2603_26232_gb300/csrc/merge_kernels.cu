@@ -158,10 +158,17 @@ __global__ void k_beam_score(MergeDev md, int32_t l, int32_t nb, const uint32_t*
 }
 
 // Bitonic sort of n (power of two) keys in shared memory, descending.
+// Thread t handles indices t, t + blockDim.x, ... (blockDim.x a multiple of
+// 32), so a compare-exchange at a stride below 32 pairs two indices of one
+// 32-element chunk, handled by lanes of one warp: a stage at such a stride
+// that follows another one needs only a warp barrier.
 __device__ void block_sort_desc(uint64_t* k, int n) {
+  int prev = n;  // stride of the previous stage (n: the fill before the sort)
   for (int size = 2; size <= n; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      __syncthreads();
+      if (stride < 32 && prev < 32) __syncwarp();
+      else __syncthreads();
+      prev = stride;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         int p = i ^ stride;
         if (p > i) {
