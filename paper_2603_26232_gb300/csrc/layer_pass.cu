@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   // constants only after the first barrier of the next tile, which every
   // thread reaches after its last read of them.
   const uint32_t ntiles = 1u << pd.tpc_log2;
+  const bool tile_barrier_covered =
+      !SPLIT && NR >= 2 && !warp_local_transpose<TB, R, O0, O1>() && (pd.layerA >= 0 || pd.layerB >= 0);
   // this thread's <C> terms over the CTA's tiles, summed in FP32 in two
   // levels (2^R positive terms per tile, then at most 2^kMaxTpcLog2 tile
   // sums: relative error below 48 x 2^-24, about 3e-6), FP64 from the block
@@ -196,7 +198,12 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
       a[k] = base[off];
     }
   }
-  __syncthreads();  // phase table, planes and Q_K visible
+  // Set-up visible (first tile); later, this barrier keeps warp 0 from
+  // rewriting the tile constants while others still read the previous
+  // tile's. A classic pass of two or more rounds that mixes crosses a CTA
+  // barrier (a transpose between warps) after those reads in every tile, so
+  // there it is needed for the first tile only.
+  if (tt == 0 || !tile_barrier_covered) __syncthreads();
   int A = 0, kap[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) kap[j] = 0;
