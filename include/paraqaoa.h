@@ -342,6 +342,28 @@ int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, i
 int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2);
 
+/* The layer-pass schedule of one n-qubit state at depth p for a tile shape
+ * (tile_bits/reg_bits one of 12/5, 12/4, 13/5), minimum contiguous run
+ * c_min of the higher groups and split flag, without a context or a GPU
+ * (Sec. 2.2: the p layers' mixers commute qubit by qubit, so a layer can be
+ * applied in qubit groups that fit a tile, and one pass ends layer l on a
+ * group, applies phase l + 1 and starts layer l + 1 on the same group).
+ * keep: the last pass stores the state; expect: the last pass reduces <C>.
+ * Writes up to max_passes records of PARAQAOA_PASS_FIELDS int32 each into
+ * out (caller-owned) and the pass count into *out_count; a record is
+ * {c, s, mix_lo, layerA, layerP, layerB, init, store, expect, last, split}:
+ * the tile holds qubits [0, c) and [s, s + tile_bits - c) as its local bits
+ * 0..tile_bits-1, the pass mixes local bits >= mix_lo (split passes: bits
+ * [0, 2 reg_bits)), finishes mixer layerA, applies phase layerP and starts
+ * mixer layerB (-1: none). Returns PARAQAOA_E_INVAL for an unknown shape, n
+ * below the tile or above PARAQAOA_MAX_QUBITS, p outside 1..PARAQAOA_MAX_P,
+ * or a split schedule that does not fit; *out_count holds the full count
+ * even when max_passes is smaller (then only max_passes records are
+ * written). */
+#define PARAQAOA_PASS_FIELDS 11
+int paraqaoa_schedule(int32_t n, int32_t p, int32_t tile_bits, int32_t reg_bits, int32_t c_min, int32_t split,
+                      int32_t keep, int32_t expect, int32_t max_passes, int32_t *out, int32_t *out_count);
+
 /* Per-kernel device time recorded with CUDA events on the context stream.
  * enable != 0 starts recording (and clears the counters). While it is on,
  * size classes run in order on the context stream and Adam steps are

@@ -62,6 +62,7 @@ _SIGS = {
     "paraqaoa_optimize": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                            ctypes.c_double, P, P, P], ctypes.c_int),
     "paraqaoa_autotune": ([P, P, ctypes.c_int32, P, P, P, P, P], ctypes.c_int),
+    "paraqaoa_schedule": ([ctypes.c_int32] * 9 + [P, P], ctypes.c_int),
     "paraqaoa_set_schedule": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                ctypes.c_int32], ctypes.c_int),
     "paraqaoa_profile_enable": ([P, ctypes.c_int32], ctypes.c_int),
@@ -398,6 +399,22 @@ def paraqaoa_simulate_tc(ctx, part, ids, p: int, gamma, beta, flags: int = SIM_E
         raise ValueError("gamma/beta must hold count x p angles")
     _check(load().paraqaoa_simulate_tc(ctx, part, _ptr(ids), ids.size, int(p), _ptr(g), _ptr(b), int(flags),
                                        int(precision), int(block_qubits)), "paraqaoa_simulate_tc")
+
+
+PASS_FIELDS = ("c", "s", "mix_lo", "layerA", "layerP", "layerB", "init", "store", "expect", "last", "split")
+
+
+def paraqaoa_schedule(n: int, p: int, tile_bits: int, reg_bits: int, c_min: int = 3, split: int = 0,
+                      keep: bool = False, expect: bool = True):
+    """The layer-pass schedule (no context, no GPU): a list of dicts with PASS_FIELDS."""
+    cnt = np.zeros(1, np.int32)
+    _check(load().paraqaoa_schedule(int(n), int(p), int(tile_bits), int(reg_bits), int(c_min), int(split),
+                                    int(bool(keep)), int(bool(expect)), 0, None, _ptr(cnt)), "paraqaoa_schedule")
+    out = np.zeros((max(int(cnt[0]), 1), len(PASS_FIELDS)), np.int32)
+    _check(load().paraqaoa_schedule(int(n), int(p), int(tile_bits), int(reg_bits), int(c_min), int(split),
+                                    int(bool(keep)), int(bool(expect)), int(cnt[0]), _ptr(out), _ptr(cnt)),
+           "paraqaoa_schedule")
+    return [dict(zip(PASS_FIELDS, (int(v) for v in row))) for row in out[:int(cnt[0])]]
 
 
 def paraqaoa_set_schedule(ctx, n: int, tile_bits: int, reg_bits: int, c_min: int = 3, split: int = 0,

@@ -1370,6 +1370,26 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   return PARAQAOA_OK;
 }
 
+int paraqaoa_schedule(int32_t n, int32_t p, int32_t tile_bits, int32_t reg_bits, int32_t c_min, int32_t split,
+                      int32_t keep, int32_t expect, int32_t max_passes, int32_t* out, int32_t* out_count) {
+  if (!out_count || max_passes < 0 || (max_passes > 0 && !out)) return PARAQAOA_E_INVAL;
+  if (n > PARAQAOA_MAX_QUBITS || p < 1 || p > PARAQAOA_MAX_P || c_min < 0 || c_min > 8 || (split != 0 && split != 1))
+    return PARAQAOA_E_INVAL;
+  int kind = -1;
+  for (int k = 0; k < kTileKinds; ++k)
+    if (kTileShapes[k].tb == tile_bits && kTileShapes[k].r == reg_bits) kind = k;
+  if (kind < 0 || n < tile_bits || (split && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
+  const auto sched = make_schedule(n, p, tile_bits, c_min, keep != 0, expect != 0, split ? reg_bits : 0);
+  *out_count = (int32_t)sched.size();
+  for (int32_t i = 0; i < (int32_t)sched.size() && i < max_passes; ++i) {
+    const PassDesc& d = sched[i];
+    const int32_t rec[PARAQAOA_PASS_FIELDS] = {d.c,    d.s,     d.mix_lo, d.layerA, d.layerP, d.layerB,
+                                               d.init, d.store, d.expect, d.last,   d.split};
+    std::memcpy(out + (int64_t)i * PARAQAOA_PASS_FIELDS, rec, sizeof(rec));
+  }
+  return PARAQAOA_OK;
+}
+
 int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2) {
   if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || (split != 0 && split != 1) ||

@@ -1,0 +1,101 @@
+"""The layer-pass schedule (paraqaoa_schedule, host code of the C ABI) checked
+on the CPU by replaying it symbolically: every pass's tile holds distinct
+qubits of the state, every layer's mixer covers each qubit exactly once, the
+phase of layer l comes after all of layer l-1's mixer and before any of
+layer l's, and the pass count is 1 + p (G - 1) for G qubit groups.
+
+The mixers of one layer act on different qubits and commute, so this order
+is the circuit U_M(b_{p-1}) U_C(g_{p-1}) ... U_M(b_0) U_C(g_0) |+> of Sec. 2.2."""
+import itertools
+
+import pytest
+
+from paper_2603_26232_gb300 import _capi as capi
+
+SHAPES = [(12, 5), (12, 4), (13, 5)]
+
+
+def _tile_qubits(pd, tb):
+    return [lb if lb < pd["c"] else pd["s"] + (lb - pd["c"]) for lb in range(tb)]
+
+
+def _mixed_qubits(pd, tb, r):
+    q = _tile_qubits(pd, tb)
+    if pd["split"]:
+        return set(q[: 2 * r])
+    return set(q[pd["mix_lo"]:])
+
+
+def _replay(n, p, tb, r, c_min, split, keep, expect):
+    passes = capi.paraqaoa_schedule(n, p, tb, r, c_min, split, keep, expect)
+    full = set(range(n))
+    mixed = [set() for _ in range(p)]
+    phased = [False] * p
+    groups = set()
+    initialised = False
+    for i, pd in enumerate(passes):
+        tq = _tile_qubits(pd, tb)
+        assert len(set(tq)) == tb and all(0 <= q < n for q in tq), (i, pd)
+        assert pd["init"] == (1 if i == 0 else 0)
+        assert pd["last"] == (1 if i == len(passes) - 1 else 0)
+        if pd["c"] < tb:  # a high group carries at least c_min contiguous low qubits
+            assert pd["c"] >= min(c_min, tb - 1) and not pd["split"]
+        assert pd["split"] == (1 if split and pd["c"] == tb else 0)
+        mq = _mixed_qubits(pd, tb, r)
+        assert mq
+        groups.add(frozenset(mq))
+        initialised = initialised or bool(pd["init"])
+        assert initialised
+        if pd["layerA"] >= 0:  # finish a mixer started by an earlier pass
+            la = pd["layerA"]
+            assert phased[la] and mixed[la] and not (mixed[la] & mq)
+            mixed[la] |= mq
+        if pd["layerP"] >= 0:
+            lp = pd["layerP"]
+            assert not phased[lp]
+            assert lp == 0 or mixed[lp - 1] == full, "phase before the previous mixer is complete"
+            assert all(phased[:lp])
+            phased[lp] = True
+        if pd["layerB"] >= 0:  # start a mixer on this pass's group, after its phase
+            lb = pd["layerB"]
+            assert phased[lb] and not mixed[lb]
+            assert pd["layerP"] == lb
+            mixed[lb] |= mq
+        if i < len(passes) - 1:
+            assert pd["store"] == 1 and pd["expect"] == 0
+        else:
+            assert pd["store"] == (1 if keep else 0) and pd["expect"] == (1 if expect else 0)
+    assert all(phased) and all(m == full for m in mixed)
+    # the groups partition the qubits
+    assert sum(len(g) for g in groups) == n and set().union(*groups) == full
+    assert len(passes) == 1 + p * (len(groups) - 1)
+    return passes, len(groups)
+
+
+@pytest.mark.parametrize("tb,r", SHAPES)
+@pytest.mark.parametrize("split", [0, 1])
+def test_schedules_replay_the_circuit(tb, r, split):
+    for n, p, c_min, keep, expect in itertools.product(range(15, 31), (1, 2, 3, 4), (2, 3, 4), (0, 1), (0, 1)):
+        if n < tb:
+            continue
+        _replay(n, p, tb, r, c_min, split, keep, expect)
+
+
+def test_pass_counts_of_the_measured_schedules():
+    # two groups at n = 20 (12 + 8 qubits): p = 2 takes three passes
+    passes, G = _replay(20, 2, 12, 4, 2, 0, 0, 1)
+    assert G == 2 and len(passes) == 3
+    assert [pd["c"] for pd in passes] == [12, 4, 12]
+    # n = 26, split 2^12 x 32: 10 low qubits + two groups of 8 -> five passes at p = 2
+    passes, G = _replay(26, 2, 12, 5, 2, 1, 0, 1)
+    assert G == 3 and len(passes) == 5
+    # n = 24 on the 2^13 tile: 13 + 11 qubits (2 contiguous carried), three passes
+    passes, G = _replay(24, 2, 13, 5, 2, 0, 0, 1)
+    assert G == 2 and passes[1]["c"] == 2
+
+
+def test_schedule_rejects_invalid_arguments():
+    for args in [(20, 2, 12, 3, 2, 0), (20, 2, 14, 5, 2, 0), (11, 1, 12, 4, 2, 0), (20, 0, 12, 4, 2, 0),
+                 (20, 17, 12, 4, 2, 0), (31, 1, 12, 4, 2, 0), (20, 1, 12, 4, 9, 0), (20, 1, 12, 4, 2, 2)]:
+        with pytest.raises(capi.ParaQAOAError):
+            capi.paraqaoa_schedule(*args)
