@@ -405,6 +405,31 @@ def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
         capi.paraqaoa_part_free(part)
 
 
+def test_default_schedules_match_oracle(api, orc):
+    """A fresh context's built-in schedules (no autotune, no set_schedule):
+    2^12 x 32-register split walking 2 tiles up to 18 qubits, 2^12 x 16
+    classic walking 8 for 19-20, 2^13 x 32 classic walking 4 for 21-24;
+    depth 2, states kept."""
+    capi, _ = api
+    ctx = capi.paraqaoa_create(0)
+    sizes = [15, 17, 19, 20, 21, 23, 24]
+    g = chain_graph(sizes, 0.3, 91, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), 2, 92)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+        ex = capi.paraqaoa_expect(ctx, len(ids))
+        for i, s in enumerate(subs):
+            ref = orc.simulate(s, gam[i], bet[i])
+            assert np.max(np.abs(capi.paraqaoa_state(ctx, i, s.n) - ref)) <= AMP_TOL, (s.n,)
+            assert abs(ex[i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL, (s.n,)
+    finally:
+        capi.paraqaoa_part_free(part)
+        capi.paraqaoa_destroy(ctx)
+
+
 def test_set_schedule_rejects_out_of_range(api):
     """Host-side validation of hand-set schedules: unknown shapes, runs,
     tiles per CTA above 2^4, split schedules that do not fit the part."""
@@ -420,7 +445,8 @@ def test_set_schedule_rejects_out_of_range(api):
 def test_large_parts_full_size(api, orc):
     """Parts of 25 and 26 qubits (the 16,000-vertex workload's sizes, 256 and
     512 MB complex64 states), p = 2, in the split schedule the autotuner picks
-    there (three qubit groups, five passes) and in a classic one: <C>, 4096
+    there and the context uses by default (three qubit groups, five passes, 4
+    tiles per CTA) and in a classic one: <C>, 4096
     sampled amplitudes plus the top-32 entries, and the top-32 lists."""
     capi, ctx = api
     sizes = [25, 26]
@@ -432,7 +458,7 @@ def test_large_parts_full_size(api, orc):
     oex = [orc.expect_state(s, r) for s, r in zip(subs, refs)]
     rng = np.random.default_rng(5)
     try:
-        for sched in [(12, 5, 2, 1), (13, 5, 2, 0)]:
+        for sched in [(12, 5, 2, 1, 2), (13, 5, 2, 0)]:   # the default from 25 qubits, and a classic one
             for n in sizes:
                 capi.paraqaoa_set_schedule(ctx, n, *sched)
             ids = np.arange(2, dtype=np.int32)
