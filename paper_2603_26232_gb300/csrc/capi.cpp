@@ -1,576 +1,8 @@
-// C ABI of the ParaQAOA hot path: context, partition, admission, pass
-// scheduling and the host side of every entry point in include/paraqaoa.h.
-// Every numerical step runs in the CUDA kernels of this directory; this file
-// validates arguments, lays out device memory and enqueues launches.
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <array>
-#include <atomic>
-#include <cmath>
-#include <cstring>
-#include <map>
-#include <new>
-#include <vector>
-
-#include "pq_internal.h"
-
-using namespace pq;
-
-namespace {
-
-std::atomic<uint64_t> g_part_serial{1};
-
-// Grow-only device buffer.
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap) return cudaSuccess;
-    if (p) cudaFree(p);  // synchronous: no queued kernel still uses it
-    p = nullptr;
-    cap = 0;
-    const size_t want = (bytes + 255) & ~size_t(255);
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e == cudaSuccess) cap = want;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-  template <class T>
-  T* as() const { return reinterpret_cast<T*>(p); }
-};
-
-int cuda_rc(cudaError_t e) {
-  if (e == cudaSuccess) return PARAQAOA_OK;
-  if (e == cudaErrorMemoryAllocation) return PARAQAOA_E_NOMEM;
-  return PARAQAOA_E_CUDA;
-}
-
-#define PQ_CUDA(call)                       \
-  do {                                      \
-    cudaError_t e_ = (call);                \
-    if (e_ != cudaSuccess) return cuda_rc(e_); \
-  } while (0)
-
-int bitlen(int64_t x) {
-  int b = 0;
-  while (x > 0) {
-    ++b;
-    x >>= 1;
-  }
-  return b;
-}
-
-struct ProfRec {
-  int cls;
-  cudaEvent_t a, b;
-};
-
-}  // namespace
-
-struct paraqaoa_part {
-  uint64_t serial;
-  int32_t nv = 0, M = 0;
-  std::vector<int32_t> first, size;
-  std::vector<int64_t> eoff;  // M+1 into eu/ev/ew
-  std::vector<int32_t> eu, ev, ew;
-  std::vector<int64_t> weight;
-  std::vector<int32_t> P;
-  std::vector<int32_t> plane_off;
-  std::vector<uint32_t> planes;
-};
-
-// A simulate plan: the instances of one batch and where their data lives.
-struct SimPlan {
-  int32_t count = 0, p = 0;
-  uint32_t flags = 0;
-  std::vector<InstDev> inst;
-  std::vector<int32_t> lists;                   // concatenated instance lists
-  std::pair<int32_t, int32_t> tiny{0, 0};       // offset, length into lists
-  std::map<int, std::pair<int32_t, int32_t>> smem, hbm;  // n -> (offset, length)
-  // n -> (offset, length) into lists: one instance per distinct part of the
-  // class (the instances of a part share their cut constants)
-  std::map<int, std::pair<int32_t, int32_t>> hbm_reps;
-  int64_t table_elems = 0, state_elems = 0, partial_elems = 0;
-  int32_t tabcap = 1;  // largest W + 1 of the batch (phase-table entries on chip)
-  bool valid = false;
-  // the layer passes' cut constants (functions of the parts and the pass
-  // layouts only) are on the device from an earlier run of this plan
-  bool cc_ready = false;
-};
-
-constexpr int kSideStreams = 4;
-
-struct paraqaoa_ctx {
-  int device = 0;
-  size_t budget = 0;
-  cudaStream_t own = nullptr, stream = nullptr;
-  // per qubit count n: tile bits of the layer passes and the fewest contiguous
-  // low qubits a high-group tile carries (heuristic, or measured by autotune)
-  int8_t tile_kind[PARAQAOA_MAX_QUBITS + 1] = {};  // index into kTileShapes
-  int8_t c_min[PARAQAOA_MAX_QUBITS + 1] = {};
-  // split schedule (the low group is 2R qubits, one transpose per pass) per n
-  int8_t split[PARAQAOA_MAX_QUBITS + 1] = {};
-  // tiles per CTA of the layer passes (log2) per n
-  int8_t tpc_log2[PARAQAOA_MAX_QUBITS + 1] = {};
-  int num_sms = 0;
-  // partition on the device
-  uint64_t part_serial = 0;
-  DevBuf d_subs, d_planes;
-  // simulate
-  SimPlan plan;
-  DevBuf d_inst, d_lists, d_gamma, d_beta, d_tables, d_states, d_partials, d_expect;
-  DevBuf d_consts;  // cut constants of the current plan's layer passes (the tensor-core variant: its lists)
-  // top-K
-  DevBuf d_chunk_off, d_topk_scratch, d_topk_z, d_topk_p;
-  // merge
-  DevBuf m_first, m_size, m_level, m_cand, m_intra, m_eoff, m_eu, m_ev, m_ew, m_key, m_path;
-  DevBuf m_sides[2], m_score[2], m_rank[2], m_r2s[2], m_keys, m_nb;
-  // angle loop
-  DevBuf o_vals, o_best, o_theta, o_m, o_v, o_w, o_g2, o_b2;
-  // tensor-core variant: device error flag of its bounded waits
-  DevBuf d_tc_err;
-  // Adam step counter on the device (read by the update kernel)
-  DevBuf o_step;
-  // side streams for concurrent size classes, with their fork / join events
-  cudaStream_t side[kSideStreams] = {};
-  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
-  // profiling
-  bool prof = false;
-  uint32_t prof_mask = ~0u;  // classes bracketed by events while profiling
-  std::vector<ProfRec> pending;
-  std::vector<cudaEvent_t> pool;
-  int64_t launches[PARAQAOA_KCLASS_COUNT] = {};
-  double ms[PARAQAOA_KCLASS_COUNT] = {}, bytes[PARAQAOA_KCLASS_COUNT] = {};
-};
-
-namespace {
-
-cudaEvent_t get_event(paraqaoa_ctx* c) {
-  if (!c->pool.empty()) {
-    cudaEvent_t e = c->pool.back();
-    c->pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-void prof_flush(paraqaoa_ctx* c);
-
-// Records kept unread before a flush; the event pool is filled to cover them
-// when profiling is switched on, so a profiled run neither synchronises nor
-// creates events in the middle of a call.
-constexpr size_t kProfPendingMax = 16384;
-
-struct ProfScope {
-  paraqaoa_ctx* c;
-  int cls;
-  double bytes;
-  int kernels;
-  cudaEvent_t a = nullptr;
-  ProfScope(paraqaoa_ctx* c_, int cls_, double bytes_, int kernels_ = 1)
-      : c(c_), cls(cls_), bytes(bytes_), kernels(kernels_) {
-    if (c->prof) {
-      c->launches[cls] += kernels;
-      c->bytes[cls] += bytes;
-      if ((c->prof_mask >> cls) & 1u) {
-        a = get_event(c);
-        cudaEventRecord(a, c->stream);
-      }
-    }
-  }
-  ~ProfScope() {
-    if (c->prof && a) {
-      cudaEvent_t b = get_event(c);
-      cudaEventRecord(b, c->stream);
-      c->pending.push_back({cls, a, b});
-      if (c->pending.size() >= kProfPendingMax) prof_flush(c);
-    }
-  }
-};
-
-void prof_flush(paraqaoa_ctx* c) {
-  if (c->pending.empty()) return;
-  cudaStreamSynchronize(c->stream);
-  for (auto& r : c->pending) {
-    float t = 0.f;
-    cudaEventElapsedTime(&t, r.a, r.b);
-    c->ms[r.cls] += t;
-    c->pool.push_back(r.a);
-    c->pool.push_back(r.b);
-  }
-  c->pending.clear();
-}
-
-int validate_csr(const paraqaoa_csr* g) {
-  if (!g || g->n < 1 || g->nnz < 0 || !g->row_ptr || (g->nnz > 0 && (!g->col || !g->w)))
-    return PARAQAOA_E_INVAL;
-  if (g->row_ptr[0] != 0 || g->row_ptr[g->n] != g->nnz) return PARAQAOA_E_INVAL;
-  int64_t up = 0, down = 0, wbal = 0;
-  for (int32_t u = 0; u < g->n; ++u) {
-    if (g->row_ptr[u + 1] < g->row_ptr[u]) return PARAQAOA_E_INVAL;
-    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
-      const int32_t v = g->col[k];
-      if (v < 0 || v >= g->n || v == u || g->w[k] <= 0) return PARAQAOA_E_INVAL;
-      if (u < v) {
-        ++up;
-        wbal += g->w[k];
-      } else {
-        ++down;
-        wbal -= g->w[k];
-      }
-    }
-  }
-  if (up != down || wbal != 0) return PARAQAOA_E_INVAL;  // not symmetric
-  return PARAQAOA_OK;
-}
-
-// Level (part index) at which each vertex is first assigned.
-std::vector<int32_t> levels_of(const paraqaoa_part* pt) {
-  std::vector<int32_t> lv(pt->nv, 0);
-  for (int32_t i = 0; i < pt->M; ++i)
-    for (int32_t v = (i == 0 ? 0 : 1); v < pt->size[i]; ++v) lv[pt->first[i] + v] = i;
-  return lv;
-}
-
-int upload_part(paraqaoa_ctx* c, const paraqaoa_part* pt, bool force) {
-  if (!force && c->part_serial == pt->serial) return PARAQAOA_OK;
-  std::vector<SubDev> subs(pt->M);
-  for (int32_t i = 0; i < pt->M; ++i) {
-    subs[i].n = pt->size[i];
-    subs[i].P = pt->P[i];
-    subs[i].W = (int32_t)std::min<int64_t>(pt->weight[i], 0x7fffffff);
-    subs[i].first = pt->first[i];
-    subs[i].plane_off = pt->plane_off[i];
-  }
-  PQ_CUDA(c->d_subs.ensure(sizeof(SubDev) * std::max<size_t>(subs.size(), 1)));
-  PQ_CUDA(c->d_planes.ensure(sizeof(uint32_t) * std::max<size_t>(pt->planes.size(), 1)));
-  PQ_CUDA(cudaMemcpyAsync(c->d_subs.p, subs.data(), sizeof(SubDev) * subs.size(),
-                          cudaMemcpyHostToDevice, c->stream));
-  if (!pt->planes.empty())
-    PQ_CUDA(cudaMemcpyAsync(c->d_planes.p, pt->planes.data(), sizeof(uint32_t) * pt->planes.size(),
-                            cudaMemcpyHostToDevice, c->stream));
-  PQ_CUDA(cudaStreamSynchronize(c->stream));  // host vectors are temporaries
-  c->part_serial = pt->serial;
-  return PARAQAOA_OK;
-}
-
-cudaError_t ensure_side_streams(paraqaoa_ctx* c) {
-  if (c->fork_ev) return cudaSuccess;
-  for (int k = 0; k < kSideStreams; ++k) {
-    cudaError_t e = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
-}
-
-// Build the plan of a batch (validation, admission, memory layout).
-int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
-               int32_t p, uint32_t flags) {
-  SimPlan& pl = c->plan;
-  pl = SimPlan();
-  if (count < 1 || p < 1 || p > PARAQAOA_MAX_P || !ids) return PARAQAOA_E_INVAL;
-  pl.count = count;
-  pl.p = p;
-  pl.flags = flags;
-  pl.inst.resize(count);
-  const bool keep = flags & PARAQAOA_SIM_KEEP_STATE;
-  std::vector<int32_t> tiny;
-  std::map<int, std::vector<int32_t>> smem, hbm;
-  for (int32_t i = 0; i < count; ++i) {
-    const int32_t s = ids[i];
-    if (s < 0 || s >= pt->M) return PARAQAOA_E_INVAL;
-    const int n = pt->size[s];
-    if (n > PARAQAOA_MAX_QUBITS) return PARAQAOA_E_TOO_MANY_QUBITS;
-    if (pt->weight[s] > PARAQAOA_MAX_SUBGRAPH_WEIGHT) return PARAQAOA_E_INVAL;
-    InstDev& I = pl.inst[i];
-    std::memset(&I, 0, sizeof(I));
-    I.sub = s;
-    I.n = n;
-    I.P = pt->P[s];
-    I.W = (int32_t)pt->weight[s];
-    I.table_off = pl.table_elems;
-    pl.tabcap = std::max(pl.tabcap, I.W + 1);
-    pl.table_elems += (int64_t)p * (I.W + 1);
-    I.state_off = -1;
-    I.part_off = -1;
-    const bool big = n > kSmemMaxQubits;
-    if (big || keep) {
-      I.state_off = pl.state_elems;
-      pl.state_elems += int64_t(1) << n;
-    }
-    if (big) {
-      I.part_off = pl.partial_elems;
-      pl.partial_elems += int64_t(1) << (n - kTileShapes[c->tile_kind[n]].tb);
-      hbm[n].push_back(i);
-    } else if (n >= 10) {
-      smem[n].push_back(i);
-    } else {
-      tiny.push_back(i);
-    }
-  }
-  pl.tabcap = (pl.tabcap + 15) & ~15;
-  auto add = [&](std::vector<int32_t>& v) {
-    std::pair<int32_t, int32_t> r((int32_t)pl.lists.size(), (int32_t)v.size());
-    pl.lists.insert(pl.lists.end(), v.begin(), v.end());
-    return r;
-  };
-  auto t = add(tiny);
-  pl.tiny = t;
-  for (auto& kv : smem) pl.smem[kv.first] = add(kv.second);
-  for (auto& kv : hbm) pl.hbm[kv.first] = add(kv.second);
-  for (auto& kv : hbm) {
-    std::map<int32_t, int32_t> slot;  // part -> slot, in order of first appearance
-    std::vector<int32_t> reps;
-    for (int32_t i : kv.second) {
-      auto it = slot.find(pl.inst[i].sub);
-      if (it == slot.end()) {
-        it = slot.emplace(pl.inst[i].sub, (int32_t)reps.size()).first;
-        reps.push_back(i);
-      }
-      pl.inst[i].cc_slot = it->second;
-    }
-    pl.hbm_reps[kv.first] = add(reps);
-  }
-  // admission: every byte this batch puts on the device
-  const double need = (double)pl.state_elems * 8 + (double)pl.table_elems * 8 +
-                      (double)pl.partial_elems * 8 + (double)count * (sizeof(InstDev) + 8 + 16 * p) +
-                      (double)pl.lists.size() * 4;
-  if (need > (double)c->budget) return PARAQAOA_E_ADMISSION;
-  PQ_CUDA(c->d_inst.ensure(sizeof(InstDev) * count));
-  PQ_CUDA(c->d_lists.ensure(sizeof(int32_t) * std::max<size_t>(pl.lists.size(), 1)));
-  PQ_CUDA(c->d_gamma.ensure(sizeof(double) * count * p));
-  PQ_CUDA(c->d_beta.ensure(sizeof(double) * count * p));
-  PQ_CUDA(c->d_tables.ensure(sizeof(float2) * std::max<int64_t>(pl.table_elems, 1)));
-  PQ_CUDA(c->d_states.ensure(sizeof(float2) * std::max<int64_t>(pl.state_elems, 1)));
-  PQ_CUDA(c->d_partials.ensure(sizeof(double) * std::max<int64_t>(pl.partial_elems, 1)));
-  PQ_CUDA(c->d_expect.ensure(sizeof(double) * count));
-  PQ_CUDA(cudaMemcpyAsync(c->d_inst.p, pl.inst.data(), sizeof(InstDev) * count,
-                          cudaMemcpyHostToDevice, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(c->d_lists.p, pl.lists.data(), sizeof(int32_t) * pl.lists.size(),
-                          cudaMemcpyHostToDevice, c->stream));
-  PQ_CUDA(cudaStreamSynchronize(c->stream));  // pl vectors may change before the copy ran
-  pl.valid = true;
-  return PARAQAOA_OK;
-}
-
-// Enqueue the whole simulation of the current plan; angles in c->d_gamma/d_beta.
-int plan_run(paraqaoa_ctx* c) {
-  SimPlan& pl = c->plan;
-  const int32_t p = pl.p;
-  const bool keep = pl.flags & PARAQAOA_SIM_KEEP_STATE;
-  const bool want = pl.flags & PARAQAOA_SIM_EXPECT;
-  InstDev* inst = c->d_inst.as<InstDev>();
-  const int32_t* lists = c->d_lists.as<int32_t>();
-  const SubDev* subs = c->d_subs.as<SubDev>();
-  const uint32_t* planes = c->d_planes.as<uint32_t>();
-  float2* tables = c->d_tables.as<float2>();
-  float2* states = c->d_states.as<float2>();
-  double* partials = c->d_partials.as<double>();
-  double* expect = c->d_expect.as<double>();
-  {
-    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-    PQ_CUDA(launch_prep_layers(inst, pl.count, p, c->d_gamma.as<double>(), c->d_beta.as<double>(),
-                               tables, inst, c->stream));
-  }
-  // Size classes are independent (disjoint instances, states, partials and
-  // cut-constant regions): without per-kernel profiling they run on side
-  // streams forked from and joined back to the context stream, so that small
-  // classes fill the GPU next to large ones. Stream capture follows the fork.
-  const int ncls = (pl.tiny.second > 0 ? 1 : 0) + (int)pl.smem.size() + (int)pl.hbm.size();
-  const bool fork = !c->prof && ncls > 1;
-  int used = 0;
-  if (fork) {
-    PQ_CUDA(ensure_side_streams(c));
-    PQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
-    for (int k = 0; k < kSideStreams; ++k) PQ_CUDA(cudaStreamWaitEvent(c->side[k], c->fork_ev, 0));
-  }
-  auto cls_stream = [&]() -> cudaStream_t {
-    if (!fork) return c->stream;
-    const int k = used++ % kSideStreams;
-    return c->side[k];
-  };
-  // Cut constants: one array per size class and distinct cut layout of its
-  // schedule (a layout is fixed by the pass's qubit group and round count),
-  // computed by the first run of the plan and reused by the later ones (Adam
-  // steps, replayed graphs, the autotuner's timed runs).
-  struct ClassSched {
-    int kind, tb;
-    std::vector<PassDesc> sched;
-    std::vector<int> set;  // per pass: index of its cut layout (-1: no cut)
-    int nsets = 0;
-    int64_t off = 0, elems = 0;
-  };
-  std::map<int, ClassSched> cs;
-  int64_t cc_total = 0;
-  for (auto& kv : pl.hbm) {
-    const int n = kv.first;
-    ClassSched& q = cs[n];
-    q.kind = c->tile_kind[n];
-    q.tb = kTileShapes[q.kind].tb;
-    q.sched = make_schedule(n, p, q.tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[q.kind].r : 0);
-    std::vector<std::array<int, 4>> keys;
-    for (const PassDesc& pd : q.sched) {
-      int k = -1;
-      if (pd.layerP >= 0 || pd.expect) {
-        const std::array<int, 4> key{pd.c, pd.s, pd.split, pd.mix_lo};
-        k = (int)(std::find(keys.begin(), keys.end(), key) - keys.begin());
-        if (k == (int)keys.size()) keys.push_back(key);
-      }
-      q.set.push_back(k);
-    }
-    q.nsets = (int)keys.size();
-    q.elems = cut_consts_elems(q.kind, pl.hbm_reps[n].second);
-    q.off = cc_total;
-    cc_total += q.nsets * q.elems;
-  }
-  if (!pl.cc_ready) PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * std::max<int64_t>(cc_total, 1)));
-  if (pl.tiny.second > 0) {
-    cudaStream_t st = cls_stream();
-    ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, 0);
-    PQ_CUDA(launch_tiny_sim(inst, lists + pl.tiny.first, pl.tiny.second, p, subs, planes, tables,
-                            states, expect, keep, want, pl.tabcap, st));
-  }
-  for (auto& kv : pl.smem) {
-    cudaStream_t st = cls_stream();
-    ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, keep ? (double)kv.second.second * 8.0 * (1 << kv.first) : 0.0);
-    PQ_CUDA(launch_smem_sim(kv.first, inst, lists + kv.second.first, kv.second.second, p, subs,
-                            planes, tables, states, expect, keep, want, pl.tabcap, st));
-  }
-  for (auto& kv : pl.hbm) {
-    cudaStream_t st = cls_stream();
-    const int n = kv.first;
-    const ClassSched& q = cs[n];
-    const int kind = q.kind, tb = q.tb;
-    const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
-    const auto reps = pl.hbm_reps[n];
-    std::vector<char> done(q.nsets, pl.cc_ready ? 1 : 0);
-    for (size_t ip = 0; ip < q.sched.size(); ++ip) {
-      PassDesc pd = q.sched[ip];
-      pd.tpc_log2 = std::min<int>(c->tpc_log2[n], n - tb);
-      const int k = q.set[ip];
-      int32_t* consts = c->d_consts.as<int32_t>() + q.off + (int64_t)std::max(k, 0) * q.elems;
-      if (k >= 0 && !done[k]) {
-        ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-        PQ_CUDA(launch_cut_consts(kind, n, pd, inst, lists + reps.first, reps.second, subs, planes, consts, st));
-        done[k] = 1;
-      }
-      const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
-      ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
-      PQ_CUDA(launch_layer_pass(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs,
-                                planes, tables, states, partials, pl.tabcap, consts, st));
-    }
-    if (want) {
-      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-      PQ_CUDA(launch_expect_reduce(inst, lists + kv.second.first, kv.second.second,
-                                   1 << (n - tb), partials, expect, st));
-    }
-  }
-  if (fork)
-    for (int k = 0; k < kSideStreams; ++k) {
-      PQ_CUDA(cudaEventRecord(c->join_ev[k], c->side[k]));
-      PQ_CUDA(cudaStreamWaitEvent(c->stream, c->join_ev[k], 0));
-    }
-  pl.cc_ready = true;
-  return PARAQAOA_OK;
-}
-
-}  // namespace
-
-namespace pq {
-
-cudaStream_t ctx_stream(paraqaoa_ctx* c) { return c->stream; }
-int ctx_device(paraqaoa_ctx* c) { return c->device; }
-int ctx_part_device(paraqaoa_ctx* c, const paraqaoa_part* pt, const SubDev** subs, const uint32_t** planes) {
-  int rc = upload_part(c, pt, false);
-  if (rc) return rc;
-  *subs = c->d_subs.as<SubDev>();
-  *planes = c->d_planes.as<uint32_t>();
-  return PARAQAOA_OK;
-}
-
-// p layers over G qubit groups: group 0 = qubits [0, tb) (a tile is 2^tb
-// consecutive amplitudes), groups 1.. split qubits [tb, n) evenly, each tile
-// carrying the lowest tb - g qubits (>= c_min) so that HBM accesses stay in
-// runs of 2^(tb-g) amplitudes. Layer l visits the groups in increasing order
-// for even l and decreasing for odd l, so the last group of layer l is the
-// first of layer l+1 and one pass can finish layer l, apply the phase of
-// l+1 and start its mixer: 1 + p (G - 1) passes in all.
-// Split schedules (split_r = R > 0) give group 0 only the 2R lowest qubits,
-// which a pass mixes in two register rounds with a single transpose; the
-// tile still loads 2^tb contiguous amplitudes, and qubits [2R, n) form the
-// higher groups.
-int schedule_groups(int n, int tb, int c_min, int split_r) {
-  const int gmax = tb - std::max(0, std::min(c_min, tb - 1));
-  const int low = split_r > 0 ? 2 * split_r : tb;
-  return 1 + (n - low + gmax - 1) / gmax;
-}
-
-std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect, int split_r) {
-  const int TB = tb;
-  struct Grp {
-    int c, s, mix_lo, split;
-  };
-  std::vector<Grp> grp;
-  const int low = split_r > 0 ? 2 * split_r : TB;
-  grp.push_back({TB, TB, 0, split_r > 0 ? 1 : 0});
-  const int rest = n - low;
-  const int H = schedule_groups(n, tb, c_min, split_r) - 1;
-  int s = low;
-  for (int h = 0; h < H; ++h) {
-    const int g = rest / H + (h < rest % H ? 1 : 0);
-    grp.push_back({TB - g, s, TB - g, 0});
-    s += g;
-  }
-  const int G = (int)grp.size();
-  auto mk = [&](int gi) {
-    PassDesc d;
-    std::memset(&d, 0, sizeof(d));
-    d.c = grp[gi].c;
-    d.s = grp[gi].s;
-    d.mix_lo = grp[gi].mix_lo;
-    d.split = grp[gi].split;
-    d.layerA = d.layerP = d.layerB = -1;
-    return d;
-  };
-  std::vector<PassDesc> out;
-  PassDesc first = mk(0);
-  first.init = 1;
-  first.layerP = 0;
-  first.layerB = 0;
-  first.store = 1;
-  out.push_back(first);
-  for (int l = 0; l < p; ++l) {
-    std::vector<int> ord(G);
-    for (int i = 0; i < G; ++i) ord[i] = (l % 2 == 0) ? i : G - 1 - i;
-    for (int idx = 1; idx < G; ++idx) {
-      PassDesc d = mk(ord[idx]);
-      d.layerA = l;
-      if (idx < G - 1) {
-        d.store = 1;
-      } else if (l < p - 1) {
-        d.layerP = l + 1;
-        d.layerB = l + 1;
-        d.store = 1;
-      } else {
-        d.store = keep ? 1 : 0;
-        d.expect = expect ? 1 : 0;
-        d.last = 1;
-      }
-      out.push_back(d);
-    }
-  }
-  return out;
-}
-
-}  // namespace pq
+// C ABI of the ParaQAOA hot path (include/paraqaoa.h): context, partition,
+// cut table, batch simulation and its results, schedules and the profiler.
+// Every numerical step runs in the CUDA kernels of this directory; these
+// functions validate arguments, lay out device memory and enqueue launches.
+#include "host_ctx.h"
 
 extern "C" {
 
@@ -908,465 +340,6 @@ int paraqaoa_state(paraqaoa_ctx* c, int32_t i, float* out_host) {
   PQ_CUDA(cudaMemcpyAsync(out_host, c->d_states.as<float2>() + I.state_off, sizeof(float2) << I.n,
                           cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
-  return PARAQAOA_OK;
-}
-
-int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* pt,
-                   const uint32_t* cand, int32_t K, int32_t L, int64_t beam, uint8_t* out_side,
-                   int64_t* out_cut) {
-  if (!c || !pt || !cand || !out_side || !out_cut || K < 1 || K > PARAQAOA_MAX_TOPK || beam < 0)
-    return PARAQAOA_E_INVAL;
-  int rc = validate_csr(g);
-  if (rc) return rc;
-  if (g->n != pt->nv) return PARAQAOA_E_INVAL;
-  const int32_t M = pt->M, nv = pt->nv;
-  for (int32_t i = 0; i < M; ++i) {
-    if (pt->size[i] > 32) return PARAQAOA_E_TOO_MANY_QUBITS;
-    const uint32_t mask = pt->size[i] >= 32 ? 0xffffffffu : ((1u << pt->size[i]) - 1u);
-    for (int32_t j = 0; j < K; ++j)
-      if (cand[(int64_t)i * K + j] & ~mask) return PARAQAOA_E_INVAL;
-  }
-  int64_t total_w = 0;
-  for (int64_t k = 0; k < g->nnz; ++k) total_w += g->w[k];
-  total_w /= 2;
-  PQ_CUDA(cudaSetDevice(c->device));
-  rc = upload_part(c, pt, false);
-  if (rc) return rc;
-  // inter-partition edges bucketed by the level of their larger end
-  std::vector<int32_t> lv = levels_of(pt);
-  std::vector<int64_t> cnt(M + 1, 0);
-  for (int32_t u = 0; u < nv; ++u)
-    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
-      const int32_t v = g->col[k];
-      if (u < v && u < pt->first[lv[v]]) cnt[lv[v] + 1]++;
-    }
-  for (int32_t i = 0; i < M; ++i) cnt[i + 1] += cnt[i];
-  std::vector<int32_t> eu(cnt[M]), ev(cnt[M]), ew(cnt[M]);
-  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
-  for (int32_t u = 0; u < nv; ++u)
-    for (int64_t k = g->row_ptr[u]; k < g->row_ptr[u + 1]; ++k) {
-      const int32_t v = g->col[k];
-      if (u < v && u < pt->first[lv[v]]) {
-        const int64_t at = fill[lv[v]]++;
-        eu[at] = u;
-        ev[at] = v - pt->first[lv[v]];
-        ew[at] = g->w[k];
-      }
-    }
-  const int64_t E = std::max<int64_t>(cnt[M], 1);
-  PQ_CUDA(c->m_first.ensure(4 * M));
-  PQ_CUDA(c->m_size.ensure(4 * M));
-  PQ_CUDA(c->m_level.ensure(4 * (size_t)nv));
-  PQ_CUDA(c->m_cand.ensure(4 * (size_t)M * K));
-  PQ_CUDA(c->m_intra.ensure(8 * (size_t)M * K));
-  PQ_CUDA(c->m_eoff.ensure(8 * (size_t)(M + 1)));
-  PQ_CUDA(c->m_eu.ensure(4 * E));
-  PQ_CUDA(c->m_ev.ensure(4 * E));
-  PQ_CUDA(c->m_ew.ensure(4 * E));
-  auto up = [&](DevBuf& b, const void* h, size_t n) {
-    return n ? cudaMemcpyAsync(b.p, h, n, cudaMemcpyHostToDevice, c->stream) : cudaSuccess;
-  };
-  PQ_CUDA(up(c->m_first, pt->first.data(), 4 * M));
-  PQ_CUDA(up(c->m_size, pt->size.data(), 4 * M));
-  PQ_CUDA(up(c->m_level, lv.data(), 4 * (size_t)nv));
-  PQ_CUDA(up(c->m_cand, cand, 4 * (size_t)M * K));
-  PQ_CUDA(up(c->m_eoff, cnt.data(), 8 * (size_t)(M + 1)));
-  PQ_CUDA(up(c->m_eu, eu.data(), 4 * cnt[M]));
-  PQ_CUDA(up(c->m_ev, ev.data(), 4 * cnt[M]));
-  PQ_CUDA(up(c->m_ew, ew.data(), 4 * cnt[M]));
-  MergeDev md;
-  md.M = M;
-  md.K = K;
-  md.nv = nv;
-  md.words = (nv + 31) / 32;
-  md.first = c->m_first.as<int32_t>();
-  md.size = c->m_size.as<int32_t>();
-  md.level_of = c->m_level.as<int32_t>();
-  md.cand = c->m_cand.as<uint32_t>();
-  md.intra = c->m_intra.as<int64_t>();
-  md.eoff = c->m_eoff.as<int64_t>();
-  md.eu = c->m_eu.as<int32_t>();
-  md.ev = c->m_ev.as<int32_t>();
-  md.ew = c->m_ew.as<int32_t>();
-  std::vector<uint32_t> packed(md.words, 0u);
-  {
-    ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
-    PQ_CUDA(launch_cand_intra(c->d_subs.as<SubDev>(), c->d_planes.as<uint32_t>(), md.cand, M, K,
-                              c->m_intra.as<int64_t>(), c->stream));
-  }
-  if (beam == 0) {
-    // exhaustive level-aware DFS (Alg. 2)
-    const double space = std::pow((double)K, (double)M);
-    if (space > 1099511627776.0 || M > kMaxExhaustiveLevels) return PARAQAOA_E_SEARCH_TOO_LARGE;
-    if (total_w >= (int64_t(1) << 31)) return PARAQAOA_E_INVAL;
-    if (L < 1) L = 1;
-    if (L > M) L = M;
-    int64_t nprefix = 1;
-    for (int32_t i = 0; i < L; ++i) nprefix *= K;
-    while (nprefix > (int64_t(1) << 30) && L > 1) {
-      --L;
-      nprefix /= K;
-    }
-    PQ_CUDA(c->m_key.ensure(8));
-    PQ_CUDA(c->m_path.ensure(4 * (size_t)M));
-    PQ_CUDA(cudaMemsetAsync(c->m_key.p, 0, 8, c->stream));
-    unsigned long long key = 0;
-    std::vector<int32_t> path(M);
-    {
-      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
-      PQ_CUDA(launch_merge_dfs(md, L, nprefix, c->m_key.as<unsigned long long>(), c->stream));
-    }
-    PQ_CUDA(cudaMemcpyAsync(&key, c->m_key.p, 8, cudaMemcpyDeviceToHost, c->stream));
-    PQ_CUDA(cudaStreamSynchronize(c->stream));
-    const int64_t winner = (int64_t)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
-    {
-      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0);
-      PQ_CUDA(launch_merge_dfs_path(md, L, nprefix, winner, c->m_path.as<int32_t>(), c->stream));
-    }
-    PQ_CUDA(cudaMemcpyAsync(path.data(), c->m_path.p, 4 * (size_t)M, cudaMemcpyDeviceToHost, c->stream));
-    PQ_CUDA(cudaStreamSynchronize(c->stream));
-    // assignment of the winning path (orientation as in the kernels)
-    std::vector<uint8_t> side(nv, 0);
-    for (int32_t l = 0; l < M; ++l) {
-      const int32_t f = pt->first[l], sz = pt->size[l];
-      uint32_t b = cand[(int64_t)l * K + path[l]];
-      if (l > 0 && (int)(b & 1u) != side[f]) b = ~b & (sz >= 32 ? 0xffffffffu : ((1u << sz) - 1u));
-      for (int32_t v = 0; v < sz; ++v) side[f + v] = (uint8_t)((b >> v) & 1u);
-    }
-    const uint8_t flip = side[0];
-    for (int32_t v = 0; v < nv; ++v) out_side[v] = side[v] ^ flip;
-    *out_cut = (int64_t)(key >> 32);
-    return PARAQAOA_OK;
-  }
-  // beam reading
-  if ((int64_t)beam * K > kBeamSortCap) return PARAQAOA_E_INVAL;
-  if (total_w >= (int64_t(1) << 38)) return PARAQAOA_E_INVAL;
-  const int32_t B = (int32_t)beam;
-  for (int q = 0; q < 2; ++q) {
-    PQ_CUDA(c->m_sides[q].ensure(4 * (size_t)B * md.words));
-    PQ_CUDA(c->m_score[q].ensure(8 * (size_t)B));
-    PQ_CUDA(c->m_rank[q].ensure(4 * (size_t)B));
-    PQ_CUDA(c->m_r2s[q].ensure(4 * (size_t)B));
-  }
-  PQ_CUDA(c->m_keys.ensure(8 * (size_t)B * K));
-  PQ_CUDA(c->m_nb.ensure(4));
-  PQ_CUDA(cudaMemsetAsync(c->m_sides[0].p, 0, 4 * (size_t)md.words, c->stream));
-  PQ_CUDA(cudaMemsetAsync(c->m_score[0].p, 0, 8, c->stream));
-  PQ_CUDA(cudaMemsetAsync(c->m_rank[0].p, 0, 4, c->stream));
-  PQ_CUDA(cudaMemsetAsync(c->m_r2s[0].p, 0, 4, c->stream));
-  int32_t nb = 1;
-  int cur = 0;
-  for (int32_t l = 0; l < M; ++l) {
-    const int nx = cur ^ 1;
-    {
-      ProfScope ps(c, PARAQAOA_KCLASS_MERGE, 0, 2);
-      PQ_CUDA(launch_beam_level(md, l, nb, B, c->m_keys.as<uint64_t>(), c->m_sides[cur].as<uint32_t>(),
-                                c->m_score[cur].as<int64_t>(), c->m_rank[cur].as<int32_t>(),
-                                c->m_r2s[cur].as<int32_t>(), c->m_sides[nx].as<uint32_t>(),
-                                c->m_score[nx].as<int64_t>(), c->m_rank[nx].as<int32_t>(),
-                                c->m_r2s[nx].as<int32_t>(), c->m_nb.as<int32_t>(), c->stream));
-    }
-    nb = (int32_t)std::min<int64_t>((int64_t)nb * K, B);
-    cur = nx;
-  }
-  int64_t best = 0;
-  PQ_CUDA(cudaMemcpyAsync(packed.data(), c->m_sides[cur].p, 4 * (size_t)md.words, cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(&best, c->m_score[cur].p, 8, cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaStreamSynchronize(c->stream));
-  const uint8_t flip = (uint8_t)(packed[0] & 1u);
-  for (int32_t v = 0; v < nv; ++v) out_side[v] = (uint8_t)(((packed[v >> 5] >> (v & 31)) & 1u) ^ flip);
-  *out_cut = best;
-  return PARAQAOA_OK;
-}
-
-int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids,
-                         int32_t count, int32_t points, double* out_gamma, double* out_beta,
-                         double* out_best, double* out_values) {
-  if (!c || !pt || !ids || count < 1 || points < 1 || points > 1024 || !out_gamma || !out_beta || !out_best)
-    return PARAQAOA_E_INVAL;
-  PQ_CUDA(cudaSetDevice(c->device));
-  int rc = upload_part(c, pt, false);
-  if (rc) return rc;
-  const int32_t G = points * points;
-  const int64_t total = (int64_t)count * G;
-  if (total > 0x7fffffff) return PARAQAOA_E_INVAL;
-  std::vector<int32_t> inst_ids(total);
-  std::vector<double> gam(total), bet(total);
-  const double pi = 3.14159265358979323846;
-  for (int32_t s = 0; s < count; ++s)
-    for (int32_t k = 0; k < G; ++k) {
-      inst_ids[(int64_t)s * G + k] = ids[s];
-      gam[(int64_t)s * G + k] = pi * (double)(k / points) / (double)points;
-      bet[(int64_t)s * G + k] = 0.5 * pi * (double)(k % points) / (double)points;
-    }
-  PQ_CUDA(c->o_vals.ensure(sizeof(double) * total));
-  PQ_CUDA(c->o_best.ensure(sizeof(double) * 3 * count));
-  // chunk subgraphs so that each batch passes admission
-  int32_t s0 = 0;
-  while (s0 < count) {
-    int32_t ns = count - s0;
-    for (;;) {
-      rc = plan_build(c, pt, inst_ids.data() + (int64_t)s0 * G, ns * G, 1, PARAQAOA_SIM_EXPECT);
-      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
-      ns = (ns + 1) / 2;
-    }
-    if (rc) return rc;
-    PQ_CUDA(cudaMemcpyAsync(c->d_gamma.p, gam.data() + (int64_t)s0 * G, sizeof(double) * ns * G, cudaMemcpyHostToDevice, c->stream));
-    PQ_CUDA(cudaMemcpyAsync(c->d_beta.p, bet.data() + (int64_t)s0 * G, sizeof(double) * ns * G, cudaMemcpyHostToDevice, c->stream));
-    rc = plan_run(c);
-    if (rc) return rc;
-    PQ_CUDA(cudaMemcpyAsync(c->o_vals.as<double>() + (int64_t)s0 * G, c->d_expect.p, sizeof(double) * ns * G,
-                            cudaMemcpyDeviceToDevice, c->stream));
-    PQ_CUDA(cudaStreamSynchronize(c->stream));  // host angle arrays are reused by the next chunk
-    s0 += ns;
-  }
-  double* ob = c->o_best.as<double>();
-  {
-    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-    PQ_CUDA(launch_grid_argmax(c->o_vals.as<double>(), count, points, ob, ob + count, ob + 2 * count, c->stream));
-  }
-  PQ_CUDA(cudaMemcpyAsync(out_gamma, ob, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(out_beta, ob + count, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(out_best, ob + 2 * count, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
-  if (out_values)
-    PQ_CUDA(cudaMemcpyAsync(out_values, c->o_vals.p, sizeof(double) * total, cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaStreamSynchronize(c->stream));
-  c->plan.valid = false;
-  return PARAQAOA_OK;
-}
-
-int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
-                      int32_t p, int32_t steps, double lr, double h, double* gamma_io,
-                      double* beta_io, double* out_value) {
-  if (!c || !pt || !ids || count < 1 || p < 1 || p > PARAQAOA_MAX_P || steps < 0 || !(h > 0) ||
-      !gamma_io || !beta_io || !out_value)
-    return PARAQAOA_E_INVAL;
-  PQ_CUDA(cudaSetDevice(c->device));
-  int rc = upload_part(c, pt, false);
-  if (rc) return rc;
-  const int32_t D = 2 * p, E = 4 * p;
-  std::vector<double> theta((size_t)count * D), wsum(count);
-  for (int32_t s = 0; s < count; ++s) {
-    if (ids[s] < 0 || ids[s] >= pt->M) return PARAQAOA_E_INVAL;
-    for (int32_t l = 0; l < p; ++l) {
-      theta[(size_t)s * D + l] = gamma_io[(size_t)s * p + l];
-      theta[(size_t)s * D + p + l] = beta_io[(size_t)s * p + l];
-    }
-    wsum[s] = (double)std::max<int64_t>(pt->weight[ids[s]], 1);
-  }
-  PQ_CUDA(c->o_theta.ensure(sizeof(double) * count * D));
-  PQ_CUDA(c->o_m.ensure(sizeof(double) * count * D));
-  PQ_CUDA(c->o_v.ensure(sizeof(double) * count * D));
-  PQ_CUDA(c->o_w.ensure(sizeof(double) * count));
-  PQ_CUDA(c->o_step.ensure(sizeof(int32_t)));
-  PQ_CUDA(cudaMemcpyAsync(c->o_theta.p, theta.data(), sizeof(double) * count * D, cudaMemcpyHostToDevice, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(c->o_w.p, wsum.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
-  PQ_CUDA(cudaMemsetAsync(c->o_m.p, 0, sizeof(double) * count * D, c->stream));
-  PQ_CUDA(cudaMemsetAsync(c->o_v.p, 0, sizeof(double) * count * D, c->stream));
-  // Subgraphs are independent: chunk them so that each batch of 4p shifted
-  // evaluations per subgraph passes admission (halving until it does).
-  std::vector<int32_t> ev_ids((size_t)count * E);
-  for (int32_t s = 0; s < count; ++s)
-    for (int32_t e = 0; e < E; ++e) ev_ids[(size_t)s * E + e] = ids[s];
-  int32_t s0 = 0;
-  while (steps > 0 && s0 < count) {
-    int32_t ns = count - s0;
-    for (;;) {
-      rc = plan_build(c, pt, ev_ids.data() + (size_t)s0 * E, ns * E, p, PARAQAOA_SIM_EXPECT);
-      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
-      ns = (ns + 1) / 2;
-    }
-    if (rc) return rc;
-    double* th = c->o_theta.as<double>() + (size_t)s0 * D;
-    double* mm = c->o_m.as<double>() + (size_t)s0 * D;
-    double* vv = c->o_v.as<double>() + (size_t)s0 * D;
-    const double* ww = c->o_w.as<double>() + s0;
-    int32_t* step = c->o_step.as<int32_t>();
-    PQ_CUDA(cudaMemsetAsync(step, 0, sizeof(int32_t), c->stream));
-    // one Adam step: shifted angles (and the step counter), the batch, the update
-    auto one_step = [&]() -> int {
-      {
-        ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-        PQ_CUDA(launch_adam_shifts(th, ns, p, h, c->d_gamma.as<double>(), c->d_beta.as<double>(), step, c->stream));
-      }
-      int r = plan_run(c);
-      if (r) return r;
-      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-      PQ_CUDA(launch_adam_update(c->d_expect.as<double>(), ww, ns, p, h, lr, step, th, mm, vv, c->stream));
-      return PARAQAOA_OK;
-    };
-    if ((rc = one_step())) return rc;  // the first step also sizes every buffer
-    if (steps > 1 && !c->prof) {
-      // the remaining steps replay one captured step as a CUDA graph (the
-      // launches depend only on device data: angles, counter, moments)
-      cudaGraph_t graph = nullptr;
-      cudaGraphExec_t exec = nullptr;
-      PQ_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-      rc = one_step();
-      cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
-      if (rc) {
-        if (graph) cudaGraphDestroy(graph);
-        return rc;
-      }
-      PQ_CUDA(ce);
-      ce = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      PQ_CUDA(ce);
-      for (int32_t t = 2; t <= steps && ce == cudaSuccess; ++t) ce = cudaGraphLaunch(exec, c->stream);
-      cudaGraphExecDestroy(exec);
-      PQ_CUDA(ce);
-    } else {
-      for (int32_t t = 2; t <= steps; ++t)
-        if ((rc = one_step())) return rc;
-    }
-    s0 += ns;
-  }
-  // final <C> at the optimised angles, chunked the same way
-  PQ_CUDA(c->o_vals.ensure(sizeof(double) * count));
-  s0 = 0;
-  while (s0 < count) {
-    int32_t ns = count - s0;
-    for (;;) {
-      rc = plan_build(c, pt, ids + s0, ns, p, PARAQAOA_SIM_EXPECT);
-      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
-      ns = (ns + 1) / 2;
-    }
-    if (rc) return rc;
-    {
-      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-      PQ_CUDA(launch_theta_split(c->o_theta.as<double>() + (size_t)s0 * D, ns, p, c->d_gamma.as<double>(),
-                                 c->d_beta.as<double>(), c->stream));
-    }
-    rc = plan_run(c);
-    if (rc) return rc;
-    PQ_CUDA(cudaMemcpyAsync(gamma_io + (size_t)s0 * p, c->d_gamma.p, sizeof(double) * ns * p, cudaMemcpyDeviceToHost,
-                            c->stream));
-    PQ_CUDA(cudaMemcpyAsync(beta_io + (size_t)s0 * p, c->d_beta.p, sizeof(double) * ns * p, cudaMemcpyDeviceToHost,
-                            c->stream));
-    PQ_CUDA(cudaMemcpyAsync(out_value + s0, c->d_expect.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->stream));
-    PQ_CUDA(cudaStreamSynchronize(c->stream));
-    s0 += ns;
-  }
-  return PARAQAOA_OK;
-}
-
-int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t p,
-                         const double* gamma, const double* beta, uint32_t flags, int32_t precision,
-                         int32_t block_qubits) {
-  if (!c || !pt || !ids || !gamma || !beta || count < 1 || p < 1 || p > PARAQAOA_MAX_P) return PARAQAOA_E_INVAL;
-  if ((precision != PARAQAOA_TC_BF16 && precision != PARAQAOA_TC_FP16) || block_qubits < 5 || block_qubits > 7)
-    return PARAQAOA_E_INVAL;
-  for (int32_t i = 0; i < count; ++i) {
-    if (ids[i] < 0 || ids[i] >= pt->M) return PARAQAOA_E_INVAL;
-    if (pt->size[ids[i]] < 12) return PARAQAOA_E_INVAL;
-  }
-  PQ_CUDA(cudaSetDevice(c->device));
-  int rc = upload_part(c, pt, false);
-  if (rc) return rc;
-  const uint32_t fl = (flags & (PARAQAOA_SIM_EXPECT | PARAQAOA_SIM_KEEP_STATE)) | PARAQAOA_SIM_KEEP_STATE;
-  rc = plan_build(c, pt, ids, count, p, fl);
-  if (rc) return rc;
-  SimPlan& pl = c->plan;
-  pl.flags = flags | PARAQAOA_SIM_EXPECT;  // <C> is always reduced; states kept only on request
-  // instances grouped by qubit count; cut tables (uint16, 2^n each) per instance
-  std::map<int, std::vector<int32_t>> by_n;
-  for (int32_t i = 0; i < count; ++i) by_n[pl.inst[i].n].push_back(i);
-  std::vector<int32_t> lists;
-  std::vector<std::pair<int, std::pair<int32_t, int32_t>>> groups;
-  // each size group gets its own cut-table and partial-sum region, so that
-  // the groups can run concurrently on side streams
-  int64_t cut_elems = 0, part_elems = 0;
-  std::vector<int64_t> cut_off, part_off;
-  for (auto& kv : by_n) {
-    groups.push_back({kv.first, {(int32_t)lists.size(), (int32_t)kv.second.size()}});
-    lists.insert(lists.end(), kv.second.begin(), kv.second.end());
-    cut_off.push_back(cut_elems);
-    part_off.push_back(part_elems);
-    cut_elems += (int64_t)kv.second.size() << kv.first;
-    part_elems += (int64_t)kv.second.size() * tc_finish_blocks(kv.first);
-  }
-  const double extra = (double)cut_elems * 2 + (double)part_elems * 8;
-  const double need = (double)pl.state_elems * 8 + (double)pl.table_elems * 8 + extra;
-  if (need > (double)c->budget) return PARAQAOA_E_ADMISSION;
-  PQ_CUDA(c->d_consts.ensure(std::max<size_t>(sizeof(int32_t) * lists.size(), 4)));
-  PQ_CUDA(c->d_topk_scratch.ensure((size_t)cut_elems * 2 + 256));
-  PQ_CUDA(c->d_partials.ensure(sizeof(double) * std::max<int64_t>(part_elems, 1)));
-  PQ_CUDA(c->d_tc_err.ensure(sizeof(int)));
-  int32_t* dl = c->d_consts.as<int32_t>();
-  uint16_t* cuts = reinterpret_cast<uint16_t*>(c->d_topk_scratch.p);
-  int* err = c->d_tc_err.as<int>();
-  PQ_CUDA(cudaMemcpyAsync(dl, lists.data(), sizeof(int32_t) * lists.size(), cudaMemcpyHostToDevice, c->stream));
-  PQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c->stream));
-  PQ_CUDA(cudaMemcpyAsync(c->d_gamma.p, gamma, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
-  PQ_CUDA(cudaMemcpyAsync(c->d_beta.p, beta, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
-  InstDev* inst = c->d_inst.as<InstDev>();
-  {
-    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-    PQ_CUDA(launch_prep_layers(inst, count, p, c->d_gamma.as<double>(), c->d_beta.as<double>(),
-                               c->d_tables.as<float2>(), inst, c->stream));
-  }
-  const bool fp16 = precision == PARAQAOA_TC_FP16;
-  float2* states = c->d_states.as<float2>();
-  // size groups on side streams (as in plan_run) unless per-kernel profiling is on
-  const bool fork = !c->prof && groups.size() > 1;
-  if (fork) {
-    PQ_CUDA(ensure_side_streams(c));
-    PQ_CUDA(cudaEventRecord(c->fork_ev, c->stream));
-    for (int k = 0; k < kSideStreams; ++k) PQ_CUDA(cudaStreamWaitEvent(c->side[k], c->fork_ev, 0));
-  }
-  for (size_t gi = 0; gi < groups.size(); ++gi) {
-    const auto& gr = groups[gi];
-    cudaStream_t st = fork ? c->side[gi % kSideStreams] : c->stream;
-    const int n = gr.first;
-    const int32_t off = gr.second.first, cnt = gr.second.second;
-    const int64_t stride = int64_t(1) << n;
-    uint16_t* gcuts = cuts + cut_off[gi];
-    double* gparts = c->d_partials.as<double>() + part_off[gi];
-    for (int32_t j = 0; j < cnt; ++j) {
-      ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)stride * 2);
-      PQ_CUDA(launch_cut_table(c->d_subs.as<SubDev>() + pl.inst[lists[off + j]].sub, n, c->d_planes.as<uint32_t>(),
-                               gcuts + (int64_t)j * stride, st));
-    }
-    // ceil(n / block_qubits) blocks of as even sizes as possible; fewer blocks
-    // (sizes up to 7) when that would leave blocks under 5 qubits. Every block
-    // has 5..7 qubits and at most n - 6, so that a tile holds 64 groups.
-    int nb = (n + block_qubits - 1) / block_qubits;
-    if (n / nb < 5) nb = n / 5;
-    std::vector<int> bs(nb, n / nb);
-    for (int b = 0; b < n % nb; ++b) ++bs[b];
-    for (int b : bs)
-      if (b < 5 || b > n - 6) return PARAQAOA_E_INVAL;
-    const float scale = fp16 ? std::ldexp(1.f, (n + 1) / 2) : 1.f;
-    for (int l = 0; l < p; ++l) {
-      {
-        ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)cnt * stride * (l == 0 ? 10.0 : 18.0));
-        PQ_CUDA(launch_tc_phase(inst, dl + off, cnt, n, l, l == 0, c->d_tables.as<float2>(), gcuts, stride, states,
-                                st));
-      }
-      int q0 = 0;
-      for (int b : bs) {
-        ProfScope ps(c, PARAQAOA_KCLASS_TC_MIXER, (double)cnt * stride * 16.0);
-        PQ_CUDA(launch_mixer_tc(b, fp16, inst, dl + off, cnt, n, q0, l, states, scale, err, c->num_sms, st));
-        q0 += b;
-      }
-    }
-    ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)cnt * stride * (flags & PARAQAOA_SIM_KEEP_STATE ? 18.0 : 10.0));
-    PQ_CUDA(launch_tc_finish(inst, dl + off, cnt, n, gcuts, stride, states, gparts,
-                             (flags & PARAQAOA_SIM_KEEP_STATE) ? 1 : 0, c->d_expect.as<double>(), st));
-  }
-  if (fork)
-    for (int k = 0; k < kSideStreams; ++k) {
-      PQ_CUDA(cudaEventRecord(c->join_ev[k], c->side[k]));
-      PQ_CUDA(cudaStreamWaitEvent(c->stream, c->join_ev[k], 0));
-    }
-  int herr = 0;
-  PQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  PQ_CUDA(cudaStreamSynchronize(c->stream));
-  if (herr) {
-    pl.valid = false;
-    return PARAQAOA_E_TIMEOUT;
-  }
-  if (!(flags & PARAQAOA_SIM_KEEP_STATE)) pl.flags &= ~PARAQAOA_SIM_KEEP_STATE;
   return PARAQAOA_OK;
 }
 
