@@ -4,6 +4,9 @@
 // functions validate arguments, lay out device memory and enqueue launches.
 #include "host_ctx.h"
 
+using namespace pq;
+using namespace pqh;
+
 extern "C" {
 
 const char* paraqaoa_strerror(int code) {

@@ -2,6 +2,9 @@
 // (Alg. 2, Sec. 3.4): exhaustive level-aware search or the beam reading.
 #include "host_ctx.h"
 
+using namespace pq;
+using namespace pqh;
+
 extern "C" {
 
 int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* pt,

@@ -2,6 +2,9 @@
 // central differences, batched over parts and replayed as a CUDA graph.
 #include "host_ctx.h"
 
+using namespace pq;
+using namespace pqh;
+
 extern "C" {
 
 int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids,

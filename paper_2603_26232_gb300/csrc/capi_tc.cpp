@@ -1,6 +1,9 @@
 // C ABI: the split-precision tensor-core mixer variant (paraqaoa_simulate_tc).
 #include "host_ctx.h"
 
+using namespace pq;
+using namespace pqh;
+
 extern "C" {
 
 int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t p,

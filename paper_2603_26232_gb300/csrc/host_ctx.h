@@ -72,21 +72,7 @@ struct ProfRec {
 };
 }  // namespace pqh
 
-using namespace pq;
-using namespace pqh;
-
-struct paraqaoa_part {
-  uint64_t serial;
-  int32_t nv = 0, M = 0;
-  std::vector<int32_t> first, size;
-  std::vector<int64_t> eoff;  // M+1 into eu/ev/ew
-  std::vector<int32_t> eu, ev, ew;
-  std::vector<int64_t> weight;
-  std::vector<int32_t> P;
-  std::vector<int32_t> plane_off;
-  std::vector<uint32_t> planes;
-};
-
+namespace pqh {
 // A simulate plan: the instances of one batch and where their data lives.
 struct SimPlan {
   int32_t count = 0, p = 0;
@@ -107,6 +93,21 @@ struct SimPlan {
 };
 
 constexpr int kSideStreams = 4;
+}  // namespace pqh
+
+struct paraqaoa_part {
+  uint64_t serial;
+  int32_t nv = 0, M = 0;
+  std::vector<int32_t> first, size;
+  std::vector<int64_t> eoff;  // M+1 into eu/ev/ew
+  std::vector<int32_t> eu, ev, ew;
+  std::vector<int64_t> weight;
+  std::vector<int32_t> P;
+  std::vector<int32_t> plane_off;
+  std::vector<uint32_t> planes;
+};
+
+
 
 struct paraqaoa_ctx {
   int device = 0;
@@ -123,29 +124,29 @@ struct paraqaoa_ctx {
   int num_sms = 0;
   // partition on the device
   uint64_t part_serial = 0;
-  DevBuf d_subs, d_planes;
+  pqh::DevBuf d_subs, d_planes;
   // simulate
-  SimPlan plan;
-  DevBuf d_inst, d_lists, d_gamma, d_beta, d_tables, d_states, d_partials, d_expect;
-  DevBuf d_consts;  // cut constants of the current plan's layer passes (the tensor-core variant: its lists)
+  pqh::SimPlan plan;
+  pqh::DevBuf d_inst, d_lists, d_gamma, d_beta, d_tables, d_states, d_partials, d_expect;
+  pqh::DevBuf d_consts;  // cut constants of the current plan's layer passes (the tensor-core variant: its lists)
   // top-K
-  DevBuf d_chunk_off, d_topk_scratch, d_topk_z, d_topk_p;
+  pqh::DevBuf d_chunk_off, d_topk_scratch, d_topk_z, d_topk_p;
   // merge
-  DevBuf m_first, m_size, m_level, m_cand, m_intra, m_eoff, m_eu, m_ev, m_ew, m_key, m_path;
-  DevBuf m_sides[2], m_score[2], m_rank[2], m_r2s[2], m_keys, m_nb;
+  pqh::DevBuf m_first, m_size, m_level, m_cand, m_intra, m_eoff, m_eu, m_ev, m_ew, m_key, m_path;
+  pqh::DevBuf m_sides[2], m_score[2], m_rank[2], m_r2s[2], m_keys, m_nb;
   // angle loop
-  DevBuf o_vals, o_best, o_theta, o_m, o_v, o_w, o_g2, o_b2;
+  pqh::DevBuf o_vals, o_best, o_theta, o_m, o_v, o_w, o_g2, o_b2;
   // tensor-core variant: device error flag of its bounded waits
-  DevBuf d_tc_err;
+  pqh::DevBuf d_tc_err;
   // Adam step counter on the device (read by the update kernel)
-  DevBuf o_step;
+  pqh::DevBuf o_step;
   // side streams for concurrent size classes, with their fork / join events
-  cudaStream_t side[kSideStreams] = {};
-  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
+  cudaStream_t side[pqh::kSideStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[pqh::kSideStreams] = {};
   // profiling
   bool prof = false;
   uint32_t prof_mask = ~0u;  // classes bracketed by events while profiling
-  std::vector<ProfRec> pending;
+  std::vector<pqh::ProfRec> pending;
   std::vector<cudaEvent_t> pool;
   int64_t launches[PARAQAOA_KCLASS_COUNT] = {};
   double ms[PARAQAOA_KCLASS_COUNT] = {}, bytes[PARAQAOA_KCLASS_COUNT] = {};

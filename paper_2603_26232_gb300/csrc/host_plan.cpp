@@ -5,6 +5,9 @@
 // bookkeeping, and the pass schedule of a state (make_schedule).
 #include "host_ctx.h"
 
+using namespace pq;
+using namespace pqh;
+
 namespace pqh {
 
 std::atomic<uint64_t> g_part_serial{1};
