@@ -172,8 +172,22 @@ def cpu_baseline(seconds: float = 15.0):
         done += chunk
     dt = time.perf_counter() - t0
     amps = done * (1 << 20) * 2
-    return {"value": amps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{done} oracle <C> evaluations of 20-qubit parts at p=2 (complex128), {dt:.1f} s"}
+    rate = amps / dt
+    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} oracle <C> evaluations of 20-qubit parts at p=2 (complex128), {dt:.1f} s",
+            # one graph's solve (its amplitude-layers) at the sampled rate
+            "projected_time_to_cut_s": amp_layers_per_graph() / rate}
+
+
+def cpu_baseline_one_core(seconds: float = 6.0):
+    """The same oracle sample on one host core: a child process (exec, not a
+    fork of this one) with OpenMP limited to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(seconds)],
+                       env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": (r.stderr or r.stdout).strip().splitlines()[-1:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args, rank, world):
@@ -568,7 +582,12 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex learned-form time-to-cut")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the context's default tile choice (fixed launch sequence for ncu)")
+    ap.add_argument("--oracle-sample", type=float, default=0.0,
+                    help="print one oracle CPU-baseline sample of about this many seconds and exit")
     args = ap.parse_args()
+    if args.oracle_sample > 0:
+        print(json.dumps(cpu_baseline(args.oracle_sample)), flush=True)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -600,6 +619,7 @@ def main():
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()  # before the first GPU call of the timed work
+        cb["one_core"] = cpu_baseline_one_core()
     stream = torch.cuda.Stream()
     solver = pkg.Solver(device=local)
     capi.paraqaoa_set_stream(solver.ctx, stream.cuda_stream)
