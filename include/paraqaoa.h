@@ -177,6 +177,40 @@ int paraqaoa_optimize(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_
                       int32_t count, int32_t p, int32_t steps, double lr, double h,
                       double *gamma_io, double *beta_io, double *out_value);
 
+/* The plain angle search with its grid size, learning rate and difference
+ * step as arguments: the p = 1 grid of points x points
+ * (paraqaoa_grid_search), `steps` Adam steps of learning
+ * rate lr and central-difference step h (paraqaoa_optimize), then for
+ * d = 2..p INTERP (Zhou et al., PRX 10, 021067, 2020) from depth d-1 and
+ * `steps` Adam steps at depth d; angles folded as in paraqaoa_solve_plain
+ * (which is this call with points 16, lr 0.02, h 1e-3). Sec. 2.2 leaves the
+ * optimiser open; the INTERP start and the folding change no <C>.
+ * gamma_out / beta_out: count x p (host), value_out (optional): <C> there.
+ * steps = 0: grid only at p = 1, INTERP and evaluation above. */
+int paraqaoa_angle_search(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count,
+                          int32_t p, int32_t points, int32_t steps, double lr, double h, double *gamma_out,
+                          double *beta_out, double *value_out);
+
+/* Final simulation and top-K of a solve (Sec. 3.3.2): simulate the parts in
+ * ids at the given angles (count x p each, host) with their states kept, in
+ * chunks that pass the context's admission (halving until a chunk fits), and
+ * rank each state's bitstrings as paraqaoa_topk does (flags CANONICAL or
+ * RAW). out_z / out_p: count x K (host); out_expect (optional): count <C>.
+ * Synchronises. */
+int paraqaoa_final_topk(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids, int32_t count,
+                        int32_t p, const double *gamma, const double *beta, int32_t K, uint32_t flags,
+                        double *out_expect, uint32_t *out_z, float *out_p);
+
+/* Limit, in nanoseconds, of the context's bounded device-side waits (the
+ * split-precision mixer waits for its tensor-core products on an mbarrier,
+ * timed by the GPU's global nanosecond timer). A wait that runs longer gives
+ * up: the kernel sets an error flag, gives the products already issued up to
+ * one more second to finish, frees its tensor memory and returns, and the
+ * call returns PARAQAOA_E_TIMEOUT with the context still usable. Default
+ * 200 ms; 0 makes every such wait give up before its first poll (the error
+ * path without a fault); at most 10 s. No counterpart in the paper. */
+int paraqaoa_set_wait_limit(paraqaoa_ctx *ctx, int64_t ns);
+
 /* Top-K of one state without any device allocation (the paper has no
  * counterpart; this is a deployment variant of paraqaoa_topk).
  * For callers that must not let a library allocate device memory: a host

@@ -444,13 +444,20 @@ int or_merge_beam(int32_t nv, const int64_t *row_ptr, const int32_t *col, const 
   int64_t cap = beam * K;
   path_t *cur = (path_t *)calloc((size_t)cap, sizeof(path_t));
   path_t *ext = (path_t *)calloc((size_t)cap, sizeof(path_t));
-  if (!cur || !ext) return OR_ENOMEM;
+  int rc = OR_OK;
+  if (!cur || !ext) {
+    rc = OR_ENOMEM;
+    goto done;
+  }
   for (int64_t i = 0; i < cap; i++) {
     cur[i].tuple = (int32_t *)malloc(sizeof(int32_t) * M);
     cur[i].side = (uint8_t *)calloc((size_t)nv, 1);
     ext[i].tuple = (int32_t *)malloc(sizeof(int32_t) * M);
     ext[i].side = (uint8_t *)calloc((size_t)nv, 1);
-    if (!cur[i].tuple || !cur[i].side || !ext[i].tuple || !ext[i].side) return OR_ENOMEM;
+    if (!cur[i].tuple || !cur[i].side || !ext[i].tuple || !ext[i].side) {
+      rc = OR_ENOMEM;
+      goto done;
+    }
   }
   int64_t ncur = 1; /* the empty path */
   cur[0].score = 0;
@@ -490,13 +497,18 @@ int or_merge_beam(int32_t nv, const int64_t *row_ptr, const int32_t *col, const 
     for (int32_t v = 0; v < nv; v++) out_side[v] ^= 1u;
   }
   *out_cut = cur[0].score;
+done: /* calloc zeroed the path records, so unallocated members are NULL */
   for (int64_t i = 0; i < cap; i++) {
-    free(cur[i].tuple);
-    free(cur[i].side);
-    free(ext[i].tuple);
-    free(ext[i].side);
+    if (cur) {
+      free(cur[i].tuple);
+      free(cur[i].side);
+    }
+    if (ext) {
+      free(ext[i].tuple);
+      free(ext[i].side);
+    }
   }
   free(cur);
   free(ext);
-  return OR_OK;
+  return rc;
 }

@@ -51,18 +51,6 @@ class SolveResult:
     times: dict = field(default_factory=dict)
 
 
-def interp(gamma: np.ndarray, beta: np.ndarray):
-    """INTERP (Zhou et al., PRX 10, 021067, 2020): depth-p angles -> p+1."""
-    p = gamma.shape[-1]
-
-    def one(x):
-        x0 = np.concatenate([np.zeros(x.shape[:-1] + (1,)), x, np.zeros(x.shape[:-1] + (1,))], axis=-1)
-        i = np.arange(1, p + 2)
-        return ((i - 1) / p) * x0[..., i - 1] + ((p - i + 1) / p) * x0[..., i]
-
-    return one(gamma), one(beta)
-
-
 class Solver:
     """One CUDA context and the full ParaQAOA pipeline on it:
     partition -> angle search -> final simulation -> top-K -> merge."""
@@ -81,38 +69,13 @@ class Solver:
         except Exception:
             pass
 
-    def final_topk(self, part, ids, p, gam, bet, K):
-        """Final simulation (states kept) and top-K per part, in chunks that
-        pass the context's device-memory admission."""
-        n = len(ids)
-        ex = np.zeros(n)
-        cand = np.zeros((n, K), np.uint32)
-        cand_p = np.zeros((n, K), np.float32)
-        s0, ns = 0, n
-        while s0 < n:
-            ns = min(ns, n - s0)
-            try:
-                _capi.paraqaoa_simulate_batch(self.ctx, part, ids[s0:s0 + ns], p, gam[s0:s0 + ns],
-                                              bet[s0:s0 + ns], _capi.SIM_EXPECT | _capi.SIM_KEEP_STATE)
-            except ParaQAOAError as e:
-                if e.code != _capi.E_ADMISSION or ns == 1:
-                    raise
-                ns = (ns + 1) // 2
-                continue
-            ex[s0:s0 + ns] = _capi.paraqaoa_expect(self.ctx, ns)
-            z, pr = _capi.paraqaoa_topk(self.ctx, ns, K)
-            cand[s0:s0 + ns] = z.reshape(ns, K)
-            cand_p[s0:s0 + ns] = pr.reshape(ns, K)
-            s0 += ns
-        return ex, cand, cand_p
-
-    def solve(self, g, cfg: SolveConfig, sync_times: bool = False) -> SolveResult:
+    def solve(self, g, cfg: SolveConfig) -> SolveResult:
         G = Graph.of(g)
         t = {}
         t0 = time.perf_counter()
         part = _capi.paraqaoa_partition(G, cfg.M, cfg.mode, cfg.sizes)
         try:
-            first, size, _, _ = _capi.paraqaoa_part_info(part)
+            _, size, _, _ = _capi.paraqaoa_part_info(part)
             ids = np.arange(len(size), dtype=np.int32)
             _capi.paraqaoa_part_upload(self.ctx, part)
             t["partition"] = time.perf_counter() - t0
@@ -121,18 +84,10 @@ class Solver:
                 gam, bet, val, fallback = _capi.paraqaoa_solve_learned(self.ctx, part, ids, cfg.mlp, cfg.p,
                                                                        cfg.fallback_steps, cfg.judge_tol)
             else:
-                gam, bet, best, _ = _capi.paraqaoa_grid_search(self.ctx, part, ids, cfg.grid_points)
-                gam, bet = gam[:, None], bet[:, None]
-                val = best
-                if cfg.adam_steps > 0:
-                    gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, 1, gam, bet, cfg.adam_steps,
-                                                            cfg.lr, cfg.h)
-                for depth in range(2, cfg.p + 1):
-                    gam, bet = interp(gam, bet)
-                    gam, bet, val = _capi.paraqaoa_optimize(self.ctx, part, ids, depth, gam, bet,
+                gam, bet, val = _capi.paraqaoa_angle_search(self.ctx, part, ids, cfg.p, cfg.grid_points,
                                                             cfg.adam_steps, cfg.lr, cfg.h)
             t["angles"] = time.perf_counter() - t0 - t["partition"]
-            ex, cand, cand_p = self.final_topk(part, ids, cfg.p, gam, bet, cfg.K)
+            ex, cand, cand_p = _capi.paraqaoa_final_topk(self.ctx, part, ids, cfg.p, gam, bet, cfg.K)
             t["final"] = time.perf_counter() - t0 - t["partition"] - t["angles"]
             side, cut = _capi.paraqaoa_merge(self.ctx, G, part, cand, cfg.K, cfg.L, cfg.beam)
             t["merge"] = time.perf_counter() - t0 - t["partition"] - t["angles"] - t["final"]

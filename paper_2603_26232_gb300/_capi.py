@@ -74,6 +74,11 @@ _SIGS = {
     "paraqaoa_simulate_tc": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_uint32, ctypes.c_int32,
                               ctypes.c_int32], ctypes.c_int),
     "paraqaoa_solve_plain": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "paraqaoa_angle_search": ([P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_double, ctypes.c_double, P, P, P], ctypes.c_int),
+    "paraqaoa_final_topk": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_uint32,
+                             P, P, P], ctypes.c_int),
+    "paraqaoa_set_wait_limit": ([P, ctypes.c_int64], ctypes.c_int),
     "paraqaoa_mlp_param_count": ([ctypes.c_int32], ctypes.c_int64),
     "paraqaoa_mlp_create": ([P, ctypes.c_int32, P, ctypes.POINTER(P)], ctypes.c_int),
     "paraqaoa_mlp_free": ([P], None),
@@ -318,6 +323,36 @@ def paraqaoa_solve_plain(ctx, part, ids, p: int, steps: int = 32):
     _check(load().paraqaoa_solve_plain(ctx, part, _ptr(ids), ids.size, p, steps, _ptr(g), _ptr(b), _ptr(v)),
            "paraqaoa_solve_plain")
     return g, b, v
+
+
+def paraqaoa_angle_search(ctx, part, ids, p: int, points: int = 16, steps: int = 32, lr: float = 0.02,
+                          h: float = 1e-3):
+    ids = _arr(ids, np.int32)
+    g = np.zeros((ids.size, p))
+    b = np.zeros((ids.size, p))
+    v = np.zeros(ids.size)
+    _check(load().paraqaoa_angle_search(ctx, part, _ptr(ids), ids.size, int(p), int(points), int(steps), float(lr),
+                                        float(h), _ptr(g), _ptr(b), _ptr(v)), "paraqaoa_angle_search")
+    return g, b, v
+
+
+def paraqaoa_final_topk(ctx, part, ids, p: int, gamma, beta, K: int, flags: int = TOPK_CANONICAL):
+    """Returns (<C>, z, probabilities) of the final states, z / P of shape count x K."""
+    ids = _arr(ids, np.int32)
+    g = _arr(gamma, np.float64)
+    b = _arr(beta, np.float64)
+    if g.size != ids.size * p or b.size != ids.size * p:
+        raise ValueError("gamma/beta must hold count x p angles")
+    ex = np.zeros(ids.size)
+    z = np.zeros((ids.size, K), np.uint32)
+    pr = np.zeros((ids.size, K), np.float32)
+    _check(load().paraqaoa_final_topk(ctx, part, _ptr(ids), ids.size, int(p), _ptr(g), _ptr(b), int(K), int(flags),
+                                      _ptr(ex), _ptr(z), _ptr(pr)), "paraqaoa_final_topk")
+    return ex, z, pr
+
+
+def paraqaoa_set_wait_limit(ctx, ns: int):
+    _check(load().paraqaoa_set_wait_limit(ctx, int(ns)), "paraqaoa_set_wait_limit")
 
 
 def paraqaoa_mlp_param_count(p: int) -> int:

@@ -92,7 +92,6 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
     for (int b = 0; b < n % nb; ++b) ++bs[b];
     for (int b : bs)
       if (b < 5 || b > n - 6) return PARAQAOA_E_INVAL;
-    const float scale = fp16 ? std::ldexp(1.f, (n + 1) / 2) : 1.f;
     for (int l = 0; l < p; ++l) {
       {
         ProfScope ps(c, PARAQAOA_KCLASS_OTHER, (double)cnt * stride * (l == 0 ? 10.0 : 18.0));
@@ -102,7 +101,7 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
       int q0 = 0;
       for (int b : bs) {
         ProfScope ps(c, PARAQAOA_KCLASS_TC_MIXER, (double)cnt * stride * 16.0);
-        PQ_CUDA(launch_mixer_tc(b, fp16, inst, dl + off, cnt, n, q0, l, states, scale, err, c->num_sms, st));
+        PQ_CUDA(launch_mixer_tc(b, fp16, inst, dl + off, cnt, n, q0, l, states, c->wait_ns, err, c->num_sms, st));
         q0 += b;
       }
     }
@@ -123,6 +122,12 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
     return PARAQAOA_E_TIMEOUT;
   }
   if (!(flags & PARAQAOA_SIM_KEEP_STATE)) pl.flags &= ~PARAQAOA_SIM_KEEP_STATE;
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_set_wait_limit(paraqaoa_ctx* c, int64_t ns) {
+  if (!c || ns < 0 || ns > 10000000000ll) return PARAQAOA_E_INVAL;
+  c->wait_ns = (uint64_t)ns;
   return PARAQAOA_OK;
 }
 

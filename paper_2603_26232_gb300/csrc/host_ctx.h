@@ -136,8 +136,10 @@ struct paraqaoa_ctx {
   pqh::DevBuf m_sides[2], m_score[2], m_rank[2], m_r2s[2], m_keys, m_nb;
   // angle loop
   pqh::DevBuf o_vals, o_best, o_theta, o_m, o_v, o_w, o_g2, o_b2;
-  // tensor-core variant: device error flag of its bounded waits
+  // tensor-core variant: device error flag of its bounded waits, and their
+  // limit in nanoseconds (paraqaoa_set_wait_limit)
   pqh::DevBuf d_tc_err;
+  uint64_t wait_ns = 200000000ull;
   // Adam step counter on the device (read by the update kernel)
   pqh::DevBuf o_step;
   // side streams for concurrent size classes, with their fork / join events

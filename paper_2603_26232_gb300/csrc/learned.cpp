@@ -377,11 +377,18 @@ int paraqaoa_mlp_predict(paraqaoa_mlp* q, const float* X, int32_t rows, double* 
 
 int paraqaoa_solve_plain(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int32_t* ids, int32_t count, int32_t p,
                          int32_t steps, double* gamma_out, double* beta_out, double* value_out) {
-  if (!ctx || !part || !ids || count < 1 || p < 1 || p > PARAQAOA_MAX_P || steps < 0 || !gamma_out || !beta_out)
+  return paraqaoa_angle_search(ctx, part, ids, count, p, 16, steps, 0.02, 1e-3, gamma_out, beta_out, value_out);
+}
+
+int paraqaoa_angle_search(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int32_t* ids, int32_t count, int32_t p,
+                          int32_t points, int32_t steps, double lr, double h, double* gamma_out, double* beta_out,
+                          double* value_out) {
+  if (!ctx || !part || !ids || count < 1 || p < 1 || p > PARAQAOA_MAX_P || steps < 0 || !gamma_out || !beta_out ||
+      points < 1 || points > 1024 || !(h > 0.0) || !(lr > 0.0))
     return PARAQAOA_E_INVAL;
   std::vector<double> g(count), b(count), best(count), val(count);
-  LQ_RC(paraqaoa_grid_search(ctx, part, ids, count, 16, g.data(), b.data(), best.data(), nullptr));
-  if (steps > 0) LQ_RC(paraqaoa_optimize(ctx, part, ids, count, 1, steps, 0.02, 1e-3, g.data(), b.data(), val.data()));
+  LQ_RC(paraqaoa_grid_search(ctx, part, ids, count, points, g.data(), b.data(), best.data(), nullptr));
+  if (steps > 0) LQ_RC(paraqaoa_optimize(ctx, part, ids, count, 1, steps, lr, h, g.data(), b.data(), val.data()));
   else val = best;
   std::vector<double> x, y;
   for (int d = 2; d <= p; ++d) {
@@ -395,7 +402,7 @@ int paraqaoa_solve_plain(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int
     g.swap(g2);
     b.swap(b2);
     if (steps > 0) {
-      LQ_RC(paraqaoa_optimize(ctx, part, ids, count, d, steps, 0.02, 1e-3, g.data(), b.data(), val.data()));
+      LQ_RC(paraqaoa_optimize(ctx, part, ids, count, d, steps, lr, h, g.data(), b.data(), val.data()));
     } else {
       LQ_RC(expect_chunked(ctx, part, ids, count, d, g.data(), b.data(), val.data()));
     }
@@ -404,6 +411,30 @@ int paraqaoa_solve_plain(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int
   std::copy(g.begin(), g.end(), gamma_out);
   std::copy(b.begin(), b.end(), beta_out);
   if (value_out) std::copy(val.begin(), val.end(), value_out);
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_final_topk(paraqaoa_ctx* ctx, const paraqaoa_part* part, const int32_t* ids, int32_t count, int32_t p,
+                        const double* gamma, const double* beta, int32_t K, uint32_t flags, double* out_expect,
+                        uint32_t* out_z, float* out_p) {
+  if (!ctx || !part || !ids || count < 1 || p < 1 || p > PARAQAOA_MAX_P || !gamma || !beta || K < 1 ||
+      K > PARAQAOA_MAX_TOPK || !out_z || !out_p)
+    return PARAQAOA_E_INVAL;
+  int32_t s0 = 0;
+  while (s0 < count) {
+    int32_t ns = count - s0;
+    int rc;
+    for (;;) {  // halve the chunk until its states pass the context's admission
+      rc = paraqaoa_simulate_batch(ctx, part, ids + s0, ns, p, gamma + (size_t)s0 * p, beta + (size_t)s0 * p,
+                                   PARAQAOA_SIM_EXPECT | PARAQAOA_SIM_KEEP_STATE);
+      if (rc != PARAQAOA_E_ADMISSION || ns == 1) break;
+      ns = (ns + 1) / 2;
+    }
+    LQ_RC(rc);
+    if (out_expect) LQ_RC(paraqaoa_expect(ctx, ns, out_expect + s0));
+    LQ_RC(paraqaoa_topk(ctx, ns, K, out_z + (size_t)s0 * K, out_p + (size_t)s0 * K, flags));
+    s0 += ns;
+  }
   return PARAQAOA_OK;
 }
 

@@ -155,7 +155,7 @@ cudaError_t launch_adam_raw(float* w, const float* g, float* m, float* v, int64_
 
 // Split-precision tensor-core mixer variant (tc_mixer.cu).
 cudaError_t launch_mixer_tc(int kb, bool fp16, const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n,
-                            int32_t q0, int32_t layer, float2* states, float scale, int* err, int num_sms,
+                            int32_t q0, int32_t layer, float2* states, uint64_t wait_ns, int* err, int num_sms,
                             cudaStream_t st);
 cudaError_t launch_tc_phase(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n, int32_t layer,
                             int32_t init, const float2* tables, const uint16_t* cuts, int64_t cut_stride,

@@ -14,7 +14,14 @@
 // A_hi M_hi^T + A_hi M_lo^T + A_lo M_hi^T accumulated in FP32 in tensor memory
 // (the lo x lo term is below the split's own rounding). FP16 parts carry 11
 // significant bits each but have a narrow exponent range, so A is scaled by a
-// power of two (exact) before splitting and D scaled back.
+// power of two (exact) before splitting and D scaled back. The gauge
+// butterflies are unnormalised: each mixed qubit multiplies the state's norm
+// by sqrt(1 + mu^2) (the layer scalar is folded into the next phase), so
+// after the q0 qubits below the block the norm, and with it every amplitude,
+// is at most (1 + mu^2)^(q0/2). The block's scale 2^(ceil(n/2) - e) with
+// e = ceil((q0/2) log2(1 + mu^2)) keeps every scaled amplitude below
+// 2^ceil(n/2) <= 2^15 (FP16 overflows at 65504) while a spread-out state's
+// amplitudes, 2^(-n/2) of the norm, land near 1.
 //
 // One CTA of 256 threads owns a tile of 64 amplitude groups x 2^k amplitudes
 // (128 rows: real parts, then imaginary parts). Per tile: coalesced FP32
@@ -90,7 +97,34 @@ __device__ __forceinline__ uint32_t canon_off(uint32_t row, uint32_t k) {
 
 constexpr int kRows = 128;      // MMA M: 64 amplitude groups x (re, im)
 constexpr int kGroups = 64;
-constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier wait
+// Bounded waits are measured on the global nanosecond timer. After a wait
+// gave up, the products still in flight get kDrainNs more before the TMEM
+// columns are freed.
+constexpr uint64_t kDrainNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait until the mbarrier completes phase `phase`, for at most limit_ns
+// (checked before each poll, so a limit of 0 gives up at once). True when the
+// phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase, uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (global_ns() - t0 >= limit_ns) return false;
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+}
 
 }  // namespace
 
@@ -103,13 +137,15 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
 // Apply the mixer block [q0, q0 + KB) of layer `layer` to every instance in
 // list (all with n qubits), in place on the interleaved complex64 states.
 // Grid: nlist x ctas_per_inst CTAs; CTA (i, j) walks tiles j, j + ctas, ...
-// of instance i. err (device int) is set to 1 if an mbarrier wait gave up.
+// of instance i. err (device int) is set to 1 if an mbarrier wait gave up
+// (after wait_ns nanoseconds); the CTA then stops, lets the products in
+// flight finish (bounded by kDrainNs), frees its TMEM columns and returns.
 constexpr int kThreads = 256;  // 8 warps: TMEM lane quarter w % 4, column half w / 4
 
 template <int KB, bool FP16>
 __global__ void __launch_bounds__(kThreads, KB < 7 ? 2 : 1)
     k_mixer_tc(const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list, int32_t n, int32_t q0,
-               int32_t layer, int32_t ctas_per_inst, float2* __restrict__ states, float scale,
+               int32_t layer, int32_t ctas_per_inst, float2* __restrict__ states, uint64_t wait_ns,
                int* __restrict__ err) {
   constexpr int K = 1 << KB;       // MMA N and K extent
   constexpr int A_BYTES = kRows * K * 2;
@@ -158,6 +194,12 @@ __global__ void __launch_bounds__(kThreads, KB < 7 ? 2 : 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // FP16 parts: the block's power-of-two scale (see the header comment)
+  float scale = 1.f;
+  if (FP16) {
+    const int e = (int)ceilf(0.5f * (float)q0 * log2f(fmaf(mu, mu, 1.f)));
+    scale = ldexpf(1.f, (n + 1) / 2 - e);
+  }
   const float inv = 1.f / scale;
   uint32_t phase = 0;
   bool ok = true;
@@ -224,16 +266,7 @@ __global__ void __launch_bounds__(kThreads, KB < 7 ? 2 : 1)
     }
     // ---- wait for the products (bounded)
     {
-      uint32_t done = 0, spins = 0;
-      while (!done) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(mbar)), "r"(phase)
-            : "memory");
-        if (!done && ++spins > kSpinLimit) break;
-      }
+      const bool done = mbar_wait_bounded(smem_u32(mbar), phase, wait_ns);
       // every thread takes the same decision (the loads below are warp-collective)
       ok = !__syncthreads_or(!done);
       if (!ok && tid == 0) atomicExch(err, 1);
@@ -279,16 +312,7 @@ __global__ void __launch_bounds__(kThreads, KB < 7 ? 2 : 1)
           make_float2(stage[u * K + (c ^ (u & 31))], stage[(u + kGroups) * K + (c ^ ((u + kGroups) & 31))]);
     __syncthreads();  // staging (aliasing A) is free for the next tile's split
   }
-  if (!ok) {  // give the products in flight another bounded wait before the columns are freed
-    uint32_t done = 0, spins = 0;
-    while (!done && ++spins < kSpinLimit)
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(smem_u32(mbar)), "r"(phase)
-          : "memory");
-  }
+  if (!ok) mbar_wait_bounded(smem_u32(mbar), phase, kDrainNs);  // the products in flight, before the columns are freed
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -300,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, KB < 7 ? 2 : 1)
 
 template <int KB, bool FP16>
 static cudaError_t launch_tc_t(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n, int32_t q0,
-                               int32_t layer, float2* states, float scale, int* err, int num_sms, cudaStream_t st) {
+                               int32_t layer, float2* states, uint64_t wait_ns, int* err, int num_sms, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(KB);
   static_assert((size_t)2 * kRows * (1 << KB) * 2 == (size_t)kRows * (1 << KB) * 4, "staging fills the A buffers");
   cudaError_t e = cudaFuncSetAttribute(k_mixer_tc<KB, FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -309,19 +333,19 @@ static cudaError_t launch_tc_t(const InstDev* inst, const int32_t* list, int32_t
   const int per = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, ((int64_t)num_sms * 2 + nlist - 1) / nlist));
   const int64_t blocks = (int64_t)nlist * per;
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-  k_mixer_tc<KB, FP16><<<(unsigned)blocks, kThreads, smem, st>>>(inst, list, n, q0, layer, per, states, scale, err);
+  k_mixer_tc<KB, FP16><<<(unsigned)blocks, kThreads, smem, st>>>(inst, list, n, q0, layer, per, states, wait_ns, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mixer_tc(int kb, bool fp16, const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n,
-                            int32_t q0, int32_t layer, float2* states, float scale, int* err, int num_sms,
+                            int32_t q0, int32_t layer, float2* states, uint64_t wait_ns, int* err, int num_sms,
                             cudaStream_t st) {
   if (nlist <= 0) return cudaSuccess;
   if (n < kb + 6 || q0 < 0 || q0 + kb > n) return cudaErrorInvalidValue;
 #define PQ_TC(KBV)                                                                                            \
   if (kb == KBV)                                                                                              \
-    return fp16 ? launch_tc_t<KBV, true>(inst, list, nlist, n, q0, layer, states, scale, err, num_sms, st)    \
-                : launch_tc_t<KBV, false>(inst, list, nlist, n, q0, layer, states, scale, err, num_sms, st);
+    return fp16 ? launch_tc_t<KBV, true>(inst, list, nlist, n, q0, layer, states, wait_ns, err, num_sms, st)    \
+                : launch_tc_t<KBV, false>(inst, list, nlist, n, q0, layer, states, wait_ns, err, num_sms, st);
   PQ_TC(5)
   PQ_TC(6)
   PQ_TC(7)

@@ -211,8 +211,20 @@ def test_learned_angles_gain_over_plain_and_constant(api, orc):
     plain_evals = 256 + steps * 4 * p + 1
     learned_evals = 2 + fb.mean() * plain_evals
     assert plain_evals / learned_evals >= 10
-    # the judge: a prediction is kept exactly when the oracle's <C> there is at
-    # least the oracle's <C> at the reference angles (up to the 1e-5 W tolerance)
+    _check_judge(orc, Gte, sizes_te, ite, (g0, b0), (rg, rb), (gq, bq, fb), (gt, bt, fbt), 1e-3)
+
+
+def _check_judge(orc, Gte, sizes_te, ite, pred, ref, at0, at_tol, tol):
+    """The judge's verdicts against the oracle: with tol = 0 a prediction is
+    kept exactly when the oracle's <C> there is at least the oracle's <C> at
+    the reference angles (up to the 1e-5 W tolerance), else the part falls
+    back; with tol > 0 the reference angles are taken where the prediction
+    loses by less than tol W."""
+    g0, b0 = pred
+    rg, rb = ref
+    gq, bq, fb = at0
+    gt, bt, fbt = at_tol
+    nte = len(ite)
     subs = orc.subgraphs(Gte, len(sizes_te), 2, sizes_te)
     batch = orc.Batch(subs)
     W = np.array([max(s.total_weight, 1) for s in subs], float)
@@ -223,10 +235,47 @@ def test_learned_angles_gain_over_plain_and_constant(api, orc):
     assert set(np.unique(fb)) <= {0, 1}  # tol = 0: no reference verdicts
     kept = fb == 0
     np.testing.assert_allclose(gq[kept], g0[kept]), np.testing.assert_allclose(bq[kept], b0[kept])
-    # tol = 1e-3: reference angles where the prediction loses by less than 1e-3 W
-    thr = o_ref - 1e-3 * W
+    thr = o_ref - tol * W
     decided = decided & (np.abs(o_pred - thr) > 1e-5 * W)
     want = np.where(o_pred >= o_ref, 0, np.where(o_pred >= thr, 2, 1))
     assert np.array_equal(fbt[decided], want[decided])
     ref_taken = fbt == 2
     assert np.allclose(gt[ref_taken], rg) and np.allclose(bt[ref_taken], rb)
+    return o_pred, o_ref
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_learned_judge_weighted(api, orc, p):
+    """Weighted random subgraphs (weights 1..10, n 8..14, edge probability
+    0.05..0.5): a depth-p network trained on plain-form labels; the judge's
+    verdicts at tol = 0 and tol = 1e-2 against the oracle's <C>, every kept
+    or fallen-back part's <C> against the oracle at its final angles, and
+    every kept prediction at least the reference's <C>."""
+    capi, ctx = api
+    ntr, nte, epochs, steps = 1024, 128, 60, 32
+    _, _, ptr, itr = _workload(capi, ntr, 3 + p, 10)
+    Gte, sizes_te, pte, ite = _workload(capi, nte, 200000 + p, 10)
+    net = None
+    try:
+        gl, bl, _ = capi.paraqaoa_solve_plain(ctx, ptr, itr, p, steps)
+        Xtr = capi.paraqaoa_features(ctx, ptr, itr)
+        Xte = capi.paraqaoa_features(ctx, pte, ite)
+        T = np.concatenate([gl, bl], axis=1).astype(np.float32)
+        net = capi.paraqaoa_mlp_create(ctx, p, synth.mlp_init(p, p))
+        capi.paraqaoa_mlp_train(net, Xtr, T, epochs, 128, 1e-3, synth.epoch_orders(ntr, epochs, p))
+        g0, b0 = capi.paraqaoa_mlp_predict(net, p, Xte)
+        rg, rb = capi.paraqaoa_mlp_reference(net, p)
+        gq, bq, vq, fb = capi.paraqaoa_solve_learned(ctx, pte, ite, net, p, steps, 0.0)
+        gt, bt, vt, fbt = capi.paraqaoa_solve_learned(ctx, pte, ite, net, p, steps, 1e-2)
+    finally:
+        if net is not None:
+            capi.paraqaoa_mlp_free(net)
+        capi.paraqaoa_part_free(ptr)
+        capi.paraqaoa_part_free(pte)
+    o_pred, o_ref = _check_judge(orc, Gte, sizes_te, ite, (g0, b0), (rg, rb), (gq, bq, fb), (gt, bt, fbt), 1e-2)
+    subs = orc.subgraphs(Gte, len(sizes_te), 2, sizes_te)
+    W = np.array([max(s.total_weight, 1) for s in subs], float)
+    o_final = orc.expect_batch(orc.Batch(subs), ite, gq, bq)
+    assert np.all(np.abs(vq - o_final) <= 1e-5 * W)
+    kept = fb == 0
+    assert np.all(vq[kept] >= o_ref[kept] - 1e-5 * W[kept])

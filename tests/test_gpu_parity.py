@@ -4,6 +4,9 @@ Tolerances (stated for the floating-point results): amplitude max error
 <= 1e-5 and |<C>_gpu - <C>_oracle| / W <= 1e-5. Integer results (cut tables,
 partitions, merged cuts) must match exactly.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -205,6 +208,51 @@ def test_merge_beam_parity(api, orc, beam):
         ref_side, ref_cut = orc.merge_beam(g, first, size, cand, K, beam)
         side, cut = capi.paraqaoa_merge(ctx, G, part, cand, K, 1, beam)
         assert cut == ref_cut and np.array_equal(side, ref_side)
+        assert orc.cutval(g, side) == cut
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def test_merge_beam_hand_worked_ties(api):
+    """The hand-worked beam case of the oracle pins (ties planted at levels
+    0 and 2, a complemented candidate at level 1): B = 1 and B = 2 give the
+    assignments worked out by hand, B = 4 the exhaustive optimum."""
+    capi, ctx = api
+    h = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "beam_hand_case.json")))
+    g = synth.from_edges(h["num_vertices"], h["edges"], h["weights"])
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, h["M"])
+    try:
+        cand = np.array(h["candidates"], np.uint32)
+        for B, (bits, cut_want) in list(h["want"].items()) + [("4", (None, h["exhaustive_cut"]))]:
+            side, cut = capi.paraqaoa_merge(ctx, G, part, cand, h["K"], 1, int(B))
+            assert cut == cut_want, B
+            if bits is not None:
+                assert "".join(str(int(b)) for b in side) == bits, B
+        side_x, cut_x = capi.paraqaoa_merge(ctx, G, part, cand, h["K"], 1, 0)
+        assert cut_x == h["exhaustive_cut"] and np.array_equal(side_x, side)
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def test_merge_beam_16k_vertex_scale(api, orc):
+    """The merge of the 16,000-vertex workload: G(16000, 0.01), unit weights,
+    640 parts of 25-26 vertices, K = 32 seeded candidates per part, beam 64
+    (500-word side bitsets, 640 levels): cut and assignment bit-exact
+    against the oracle's beam merge."""
+    capi, ctx = api
+    g = synth.erdos_renyi(16000, 0.01, 0, wmax=1)
+    G = capi.Graph.of(g)
+    M, K, B = 640, 32, 64
+    part = capi.paraqaoa_partition(G, M)
+    try:
+        first, size, _, _ = capi.paraqaoa_part_info(part)
+        assert set(size.tolist()) == {25, 26}
+        rng = np.random.default_rng(16000)
+        cand = np.array([rng.integers(0, 1 << int(s), K) for s in size], dtype=np.uint32)
+        side, cut = capi.paraqaoa_merge(ctx, G, part, cand, K, 1, B)
+        oside, ocut = orc.merge_beam(g, first, size, cand, K, B)
+        assert cut == ocut and np.array_equal(side, oside)
         assert orc.cutval(g, side) == cut
     finally:
         capi.paraqaoa_part_free(part)

@@ -307,6 +307,48 @@ def test_merge_exhaustive_equals_brute_force(orc, seed):
         assert cb <= best and cb == orc.cutval(g, sb)
 
 
+# A hand-worked beam case (the beam reading of Sec. 3.4 for K^M beyond reach:
+# keep the best B partial paths per level by the cut of the edges with both
+# ends assigned, ties to the lexicographically smaller candidate tuple). Path
+# 0-1 | 2-3 | 4-5 (unit weights) plus a weight-5 edge (1, 3) between levels 0
+# and 1; parts {0,1,2}, {2,3,4}, {4,5,6}; K = 2 candidates per part with ties
+# planted at levels 0 and 2, worked out by hand:
+#   level 0: cand 0 = 0b010 (v1 in S), cand 1 = 0b001 (v0 in S): both cut
+#            (0, 1), partial score 1 each -> a tie.
+#   level 1: cand 0 = 0b111 has v2 = 1 against side[2] = 0, so it is taken
+#            complemented (0b000); cand 1 = 0b010 (v3 in S).
+#            (0,0): 1 + 0 + 5 (edge (1,3), v1 = 1, v3 = 0) = 6
+#            (0,1): 1 + 1 (edge (2,3)) + 0 = 2
+#            (1,0): 1 + 0 + 0 = 1;  (1,1): 1 + 1 + 5 = 7
+#   level 2: cand 0 = 0b010 (v5 in S), cand 1 = 0b110 (v5, v6 in S): both cut
+#            only (4, 5) -> +1 each, another tie (v6 has no edges).
+# B = 1 keeps (0) at level 0 (the tie goes to the smaller tuple), then (0,0)
+# with 6, then (0,0,0) with 7: side 0100010, cut 7. Picking the larger tuple
+# on the level-0 tie would reach (1,1) and cut 8 instead; on the level-2 tie
+# it would put v6 in S.
+# B = 2 keeps both level-0 paths, then (1,1) = 7 and (0,0) = 6, then
+# (1,1,0) = (1,1,1) = 8 > 7: (1,1,0), side 1001010, normalised so that
+# vertex 0 is on side 0: 0110101, cut 8.
+# (The case is stored in tests/golden/beam_hand_case.json for the GPU test.)
+BEAM_HAND = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "beam_hand_case.json")))
+
+
+def test_merge_beam_hand_worked_ties(orc):
+    h = BEAM_HAND
+    assert h["candidates"] == [[0b010, 0b001], [0b111, 0b010], [0b010, 0b110]]
+    g = synth.from_edges(h["num_vertices"], h["edges"], h["weights"])
+    first, size = orc.partition(h["num_vertices"], h["M"])
+    assert list(first) == [0, 2, 4] and list(size) == [3, 3, 3]
+    cand = np.array(h["candidates"], np.uint32)
+    for B, (bits, cut_want) in h["want"].items():
+        side, cut = orc.merge_beam(g, first, size, cand, h["K"], int(B))
+        assert "".join(str(int(b)) for b in side) == bits and cut == cut_want, B
+    # B >= K^(M-1) = 4 is the exhaustive merge: the best leaf, cut 8
+    side4, cut4 = orc.merge_beam(g, first, size, cand, h["K"], 4)
+    sidex, cutx, _ = orc.merge_exhaustive(g, first, size, cand, h["K"], 1)
+    assert cut4 == cutx == h["exhaustive_cut"] and np.array_equal(side4, sidex)
+
+
 def test_merge_space_counts(orc):
     ex = GOLD["merge_space"]
     # 2K^L workers in the paper = K^L starting paths times the two orientations

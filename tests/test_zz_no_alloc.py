@@ -70,3 +70,40 @@ def test_noalloc_rejects_inputs_beyond_its_scratch():
         with pytest.raises(capi.ParaQAOAError) as e:
             capi.paraqaoa_topk_noalloc(dummy.data_ptr(), n, 4, out_z.data_ptr(), out_p.data_ptr(), flags, None)
         assert e.value.code == capi.E_SCRATCH_LIMIT
+
+
+def test_noalloc_topk_at_the_scratch_limit():
+    """n = 25 ranked raw is exactly 2^25 entries: every chunk of the fixed
+    scratch array is used. Two calls in a row must both equal the
+    context-owned paraqaoa_topk of the same 256 MB state."""
+    import torch
+
+    import paper_2603_26232_gb300 as pkg
+    pkg.build()
+    from paper_2603_26232_gb300 import _capi as capi
+
+    ctx = capi.paraqaoa_create(0)
+    try:
+        n, K = 25, 32
+        g = synth.erdos_renyi(n, 0.3, 25, wmax=10)
+        part = capi.paraqaoa_partition(capi.Graph.of(g), 1)
+        try:
+            ids = np.zeros(1, np.int32)
+            gam, bet = synth.random_angles(1, 2, 25)
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_KEEP_STATE)
+            z_ref, p_ref = capi.paraqaoa_topk(ctx, 1, K, capi.TOPK_RAW)
+            d_state = torch.from_numpy(capi.paraqaoa_state(ctx, 0, n).view(np.float32)).cuda()
+            stream = torch.cuda.current_stream()
+            for _ in range(2):
+                d_z = torch.full((K,), -1, dtype=torch.int32, device="cuda")
+                d_p = torch.full((K,), -1.0, dtype=torch.float32, device="cuda")
+                capi.paraqaoa_topk_noalloc(d_state.data_ptr(), n, K, d_z.data_ptr(), d_p.data_ptr(),
+                                           capi.TOPK_RAW, stream.cuda_stream)
+                stream.synchronize()
+                assert np.array_equal(d_z.cpu().numpy().view(np.uint32), z_ref[0])
+                assert np.max(np.abs(d_p.cpu().numpy() - p_ref[0])) <= 1e-5 * float(p_ref[0].max())
+            del d_state
+        finally:
+            capi.paraqaoa_part_free(part)
+    finally:
+        capi.paraqaoa_destroy(ctx)
