@@ -10,8 +10,12 @@ every amplitude-layer the step simulates (2^n * p per evaluated instance).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank solves its own copy of the workload (graph seeds
-offset by rank): weak scaling, no data-path collective.
+Under torchrun (N > 1) the same workload is sharded across the ranks by
+default: each graph's parts are assigned to ranks by longest processing time
+first, each rank solves its parts on its GPU, the M x K candidate arrays are
+summed onto rank 0 (the one exchange) and rank 0 merges (strong scaling).
+--replicas instead gives every rank its own copy of the workload (graph
+seeds offset by rank; weak scaling, no data-path collective).
 """
 from __future__ import annotations
 
@@ -52,11 +56,14 @@ def max_over_ranks(values, dist, device):
 
 def job_value(units_per_rank_step: float, steps: int, world: int, ms: float) -> float:
     """Whole-job throughput under weak scaling: the units every rank processed
-    over the slowest rank's time."""
+    over the slowest rank's time (under strong scaling pass world = 1 and the
+    whole job's units per step)."""
     return units_per_rank_step * steps * world / (ms / 1e3)
 
 
 def workload(rank: int):
+    """The paper-scale graphs; rank r's own copy has seed r (replica mode),
+    the sharded job uses rank 0's."""
     return [synth.erdos_renyi(NV, pe, seed=rank, wmax=WMAX) for pe in DENSITIES]
 
 
@@ -582,6 +589,9 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex learned-form time-to-cut")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the context's default tile choice (fixed launch sequence for ncu)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: every rank solves its own copy of the workload (weak scaling) instead of "
+                         "one workload sharded across the ranks")
     ap.add_argument("--oracle-sample", type=float, default=0.0,
                     help="print one oracle CPU-baseline sample of about this many seconds and exit")
     args = ap.parse_args()
@@ -623,7 +633,8 @@ def main():
     stream = torch.cuda.Stream()
     solver = pkg.Solver(device=local)
     capi.paraqaoa_set_stream(solver.ctx, stream.cuda_stream)
-    graphs = workload(rank)
+    sharded = world > 1 and not args.replicas
+    graphs = workload(0 if sharded else rank)
     Gs = [capi.Graph.of(g) for g in graphs]
     cfg = pkg.SolveConfig(M=M, K=K, p=P_FINAL, grid_points=GRID, adam_steps=STEPS_ADAM, beam=BEAM)
     # tile size per qubit count, measured once on this GPU (outside the timed region)
@@ -640,11 +651,18 @@ def main():
             sched.append(capi.paraqaoa_autotune(solver.ctx, part, P_FINAL)[20])
             capi.paraqaoa_part_free(part)
 
+    if sharded:
+        from paper_2603_26232_gb300 import sharded as shard
+        part_solver, merger = shard.cuda_part_solver(solver.ctx, cfg), shard.cuda_merger(solver.ctx, cfg)
+
     def step():
         out = []
         for G, sc in zip(Gs, sched):
             capi.paraqaoa_set_schedule(solver.ctx, 20, *sc)
-            out.append(solver.solve(G, cfg))
+            if sharded:
+                out.append(shard.solve_sharded(dist, G, cfg, part_solver, merger, device="cuda"))
+            else:
+                out.append(solver.solve(G, cfg))
         return out
 
     for _ in range(max(3, args.warmup)):
@@ -652,12 +670,10 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # the headline: the product mode (size classes on side streams, Adam
+    # steps replayed from a CUDA graph, no event brackets), device time
+    # between two events on the context's stream
     clocks = Clocks(local)
-    capi.paraqaoa_profile_enable(solver.ctx, True)
-    # only the layer passes are bracketed by events (the roofline's kernel);
-    # the other classes are counted, not timed, so that the timed region
-    # carries few extra event records
-    capi.paraqaoa_profile_classes(solver.ctx, 1 << capi.KCLASS_LAYER_PASS)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
@@ -668,6 +684,18 @@ def main():
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
+    # the roofline's kernel in a separate pass of the same steps: every
+    # layer-pass launch bracketed by CUDA events on its stream (profiling
+    # runs the size classes in order and the Adam steps launch by launch);
+    # the other kernel classes are counted, not timed
+    prof_steps = max(1, min(args.steps, 5))
+    capi.paraqaoa_profile_enable(solver.ctx, True)
+    capi.paraqaoa_profile_classes(solver.ctx, 1 << capi.KCLASS_LAYER_PASS)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(prof_steps):
+            step()
+    torch.cuda.synchronize()
     prof = {k: capi.paraqaoa_profile_read(solver.ctx, k) for k in range(6)}
     capi.paraqaoa_profile_enable(solver.ctx, False)
     capi.paraqaoa_profile_classes(solver.ctx, 0xFFFFFFFF)
@@ -687,21 +715,27 @@ def main():
     if rank == 0 and not args.no_large:
         large = large_learned(capi, pkg)
     amps_step = amp_layers_per_graph() * len(graphs)
-    value = job_value(amps_step, args.steps, world, ms)
-    e2e_value = job_value(amps_step, args.steps, world, e2e_s * 1e3)
+    copies = 1 if sharded else world  # sharded: one workload in all; replicas: one per rank
+    value = job_value(amps_step, args.steps, copies, ms)
+    e2e_value = job_value(amps_step, args.steps, copies, e2e_s * 1e3)
     launches, lp_ms, lp_bytes = prof[capi.KCLASS_LAYER_PASS]
     peak, peak_kind = read_peaks()
     achieved = (lp_bytes / (lp_ms / 1e3)) / 1e9 if lp_ms > 0 else 0.0
     traffic = traffic_for(LAYER_PASS_SOURCES, lp_bytes / max(launches, 1))
-    total_launches = sum(v[0] for v in prof.values())
+    # the kernels of a step are the same in both modes (graph replay repeats
+    # the captured step's launches): launches per profiled step x timed steps
+    total_launches = sum(v[0] for v in prof.values()) * args.steps // prof_steps
     h2d = sum(int(G.row_ptr.nbytes + G.col.nbytes + G.w.nbytes) for G in Gs)
     d2h = len(Gs) * (M * K * 8 + NV + M * 8 * 3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 state, f64 <C>",
-            "data": "synthetic (seeded Erdos-Renyi graphs)", "config": config_dict(),
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "c64/f32 state, f64 <C>",
+            "data": "synthetic (seeded Erdos-Renyi graphs)",
+            "config": dict(config_dict(), parallelism=(f"parts sharded over {world} ranks (LPT), candidates "
+                                                       "reduced to rank 0, merge on rank 0") if sharded else
+                           (f"{world} replicas" if world > 1 else "1 GPU")),
             "time_to_cut_s": (ms / 1e3) / args.steps / len(graphs),
             "cuts": [int(r.cut) for r in res],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -710,7 +744,8 @@ def main():
                          "launches": launches, "avg_launch_ms": lp_ms / max(launches, 1),
                          "algorithmic_bytes_per_launch": lp_bytes / max(launches, 1),
                          "peak_source": f"{peak_kind} hbm_gbs"},
-            "layer_pass_share": lp_ms / ms if ms else None,
+            "layer_pass_share": (lp_ms / prof_steps) / (ms / args.steps) if ms else None,
+            "roofline_pass": {"steps": prof_steps, "mode": "profiled (layer passes bracketed by CUDA events)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(total_launches),
             "clocks": clk,

@@ -105,6 +105,18 @@ void paraqaoa_part_free(paraqaoa_part *part);
 int paraqaoa_part_info(const paraqaoa_part *part, int32_t *M, int32_t *first, int32_t *size,
                        int64_t *edges, int64_t *weight);
 
+/* Sec. 3.3.1 (the solver pool balances subgraphs across GPUs by size): an
+ * assignment of the partition's parts to `world` ranks by longest processing
+ * time first. Part i costs 2^n_i * p * evals[i] (evals NULL: 1 each); parts
+ * are taken by cost descending, ties by index, and each goes to the rank
+ * with the least load so far, ties to the lowest rank, so every rank computes
+ * the same plan. Graham's bound holds: the largest load is at most
+ * (4/3 - 1/(3 world)) of the best possible. out_rank (M entries) receives
+ * each part's rank, out_load (optional, world entries) each rank's load.
+ * Host-only. */
+int paraqaoa_shard_plan(const paraqaoa_part *part, int32_t world, int32_t p, const double *evals,
+                        int32_t *out_rank, double *out_load);
+
 /* Local edge list (u < v, sorted) of part `id`; arrays sized by part_info. */
 int paraqaoa_part_edges(const paraqaoa_part *part, int32_t id, int32_t *u, int32_t *v, int32_t *w);
 

@@ -51,6 +51,7 @@ _SIGS = {
     "paraqaoa_part_free": ([P], None),
     "paraqaoa_part_info": ([P, P, P, P, P, P], ctypes.c_int),
     "paraqaoa_part_edges": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "paraqaoa_shard_plan": ([P, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
     "paraqaoa_part_upload": ([P, P, ctypes.c_int32], ctypes.c_int),
     "paraqaoa_cut_table": ([P, P, ctypes.c_int32, P], ctypes.c_int),
     "paraqaoa_simulate_batch": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_uint32], ctypes.c_int),
@@ -194,6 +195,19 @@ def paraqaoa_part_edges(part, pid: int, count: int):
     w = np.zeros(count, np.int32)
     _check(load().paraqaoa_part_edges(part, int(pid), _ptr(u), _ptr(v), _ptr(w)), "paraqaoa_part_edges")
     return u, v, w
+
+
+def paraqaoa_shard_plan(part, world: int, p: int, evals=None):
+    """Rank of each part (longest processing time first) and each rank's load."""
+    M = int(paraqaoa_part_info(part)[0].size)
+    ev = None if evals is None else _arr(evals, np.float64)
+    if ev is not None and ev.size != M:
+        raise ValueError("evals must hold one entry per part")
+    rank = np.zeros(M, np.int32)
+    loads = np.zeros(int(world), np.float64)
+    _check(load().paraqaoa_shard_plan(part, int(world), int(p), _ptr(ev), _ptr(rank), _ptr(loads)),
+           "paraqaoa_shard_plan")
+    return rank, loads
 
 
 def paraqaoa_part_upload(ctx, part, force: bool = False):

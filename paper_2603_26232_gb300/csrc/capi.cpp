@@ -242,6 +242,33 @@ int paraqaoa_part_info(const paraqaoa_part* pt, int32_t* M, int32_t* first, int3
   return PARAQAOA_OK;
 }
 
+int paraqaoa_shard_plan(const paraqaoa_part* pt, int32_t world, int32_t p, const double* evals, int32_t* out_rank,
+                        double* out_load) {
+  if (!pt || world < 1 || p < 1 || !out_rank) return PARAQAOA_E_INVAL;
+  const int32_t M = pt->M;
+  std::vector<double> cost(M);
+  for (int32_t i = 0; i < M; ++i) {
+    const double e = evals ? evals[i] : 1.0;
+    if (!(e >= 0.0)) return PARAQAOA_E_INVAL;
+    cost[i] = std::ldexp(1.0, pt->size[i]) * (double)p * e;
+  }
+  // longest processing time first: parts by cost descending (ties by index),
+  // each to the rank with the least load so far (ties to the lowest rank)
+  std::vector<int32_t> order(M);
+  for (int32_t i = 0; i < M; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  std::vector<double> load(world, 0.0);
+  for (int32_t i : order) {
+    int32_t r = 0;
+    for (int32_t k = 1; k < world; ++k)
+      if (load[k] < load[r]) r = k;
+    out_rank[i] = r;
+    load[r] += cost[i];
+  }
+  if (out_load) std::copy(load.begin(), load.end(), out_load);
+  return PARAQAOA_OK;
+}
+
 int paraqaoa_part_edges(const paraqaoa_part* pt, int32_t id, int32_t* u, int32_t* v, int32_t* w) {
   if (!pt || id < 0 || id >= pt->M) return PARAQAOA_E_INVAL;
   for (int64_t e = pt->eoff[id], k = 0; e < pt->eoff[id + 1]; ++e, ++k) {
