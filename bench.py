@@ -221,8 +221,9 @@ def run_reference(args, rank, world):
 
 
 def run_layer_case(args):
-    """168 instances (21 parts x 8 angle sets) of 20 qubits at p = 2, <C> only:
-    one Adam-step batch of the workload; prints per-launch layer-pass timing."""
+    """168 instances (21 parts x 8 angle sets) of 20 qubits at p = --layer-p
+    (default 2: one Adam-step batch of the workload), <C> only; prints the
+    layer passes' timing."""
     import torch
     import paper_2603_26232_gb300 as pkg
     from paper_2603_26232_gb300 import _capi as capi
@@ -233,7 +234,8 @@ def run_layer_case(args):
     G = capi.Graph.of(g)
     part = capi.paraqaoa_partition(G, M)
     ids = np.repeat(np.arange(M, dtype=np.int32), 8)
-    gam, bet = synth.random_angles(len(ids), 2, 3)
+    P = args.layer_p
+    gam, bet = synth.random_angles(len(ids), P, 3)
     capi.paraqaoa_part_upload(ctx, part)
     if args.sched:
         sc = tuple(int(x) for x in args.sched.split(","))
@@ -241,15 +243,15 @@ def run_layer_case(args):
         capi.paraqaoa_set_schedule(ctx, 20, *sc)
         tuned = {20: sc}
     else:
-        tuned = {20: (None,) * 5} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, 2)
+        tuned = {20: (None,) * 5} if args.no_autotune else capi.paraqaoa_autotune(ctx, part, P)
     for it in range(args.iters):
         if it == args.iters - 1:
             capi.paraqaoa_profile_enable(ctx, True)
-        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, P, gam, bet, capi.SIM_EXPECT)
         capi.paraqaoa_expect(ctx, len(ids))
     n_l, ms, by = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
     peak, kind = read_peaks()
-    print(json.dumps({"case": "layer_pass", "instances": int(len(ids)), "qubits": 20, "p": 2,
+    print(json.dumps({"case": "layer_pass", "instances": int(len(ids)), "qubits": 20, "p": P,
                       "tile_bits": tuned[20][0], "reg_bits": tuned[20][1], "min_run_qubits": tuned[20][2],
                       "split": tuned[20][3], "tiles_per_cta_log2": tuned[20][4],
                       "launches": n_l, "ms": ms, "algorithmic_bytes": by,
@@ -310,17 +312,13 @@ def large_learned(capi, pkg):
             "plain_form": "measured by bench.py --case large"}
 
 
-def run_batching_case(args):
+def batching_measure(capi, ctx, reps: int = 5):
     """Batching configuration: G(2000, 0.05), unit weights, uneven parts of
     12..24 vertices (about 120), p = 3, random angles, <C> of every part in one
-    simulate call; amplitude-layers/s with the size classes on side streams
-    (profiling off) and in order (profiling on, per-class device times)."""
+    simulate call, schedules autotuned; amplitude-layers/s over the wall time
+    of simulate + expect, with the size classes on side streams (profiling
+    off) and in order (profiling on), and the 16 B roofline fraction."""
     import torch
-    import paper_2603_26232_gb300 as pkg
-    from paper_2603_26232_gb300 import _capi as capi
-
-    pkg.build()
-    ctx = capi.paraqaoa_create(0)
     g = synth.erdos_renyi(2000, 0.05, 0, wmax=1)
     sizes = synth.uneven_sizes(2000, 12, 24, 1)
     part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
@@ -328,7 +326,8 @@ def run_batching_case(args):
     gam, bet = synth.random_angles(len(sizes), 3, 3)
     capi.paraqaoa_autotune(ctx, part, 3)
     amp_layers = float(np.sum(np.left_shift(1, sizes.astype(np.int64)))) * 3
-    out = {"case": "batching", "workload": "G(2000,0.05) unit weights, seed 0; uneven parts of 12..24 vertices; p=3",
+    peak, _ = read_peaks()
+    out = {"workload": "G(2000,0.05) unit weights, seed 0; uneven parts of 12..24 vertices; p=3",
            "parts": int(len(sizes)), "amplitude_layers": amp_layers}
     for name, prof in (("side_streams", False), ("serial", True)):
         capi.paraqaoa_profile_enable(ctx, prof)
@@ -336,15 +335,25 @@ def run_batching_case(args):
         capi.paraqaoa_expect(ctx, len(ids))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        reps = 5
         for _ in range(reps):
             capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
             ex = capi.paraqaoa_expect(ctx, len(ids))
         dt = (time.perf_counter() - t0) / reps
-        out[name] = {"s_per_batch": dt, "amp_layers_per_s": amp_layers / dt}
+        rate = amp_layers / dt
+        out[name] = {"s_per_batch": dt, "amp_layers_per_s": rate, "frac_16B_roofline": rate * 16 / (peak * 1e9)}
     capi.paraqaoa_profile_enable(ctx, False)
     out["mean_expect"] = float(np.mean(ex))
     capi.paraqaoa_part_free(part)
+    return out
+
+
+def run_batching_case(args):
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    ctx = capi.paraqaoa_create(0)
+    out = dict(case="batching", **batching_measure(capi, ctx))
     capi.paraqaoa_destroy(ctx)
     print(json.dumps(out), flush=True)
 
@@ -406,19 +415,75 @@ def run_tc_case(args):
     print(json.dumps(out), flush=True)
 
 
-def run_sweep_case(args):
-    """Amplitude-layer sweep over qubit counts: for n = 14..26, a batch of
-    parts of n vertices (G(*, 0.3) chain, weights 1..10) with sum 2^n >= 2^28
-    amplitudes, p = 2, <C> only, schedule chosen by the autotuner; reports
-    amplitude-layers/s and the layer passes' achieved bandwidth against the
-    measured HBM peak (n <= 14 stays on chip and has no HBM roofline)."""
+def sweep_point(capi, ctx, n: int, reps: int = 3):
+    """One point of the amplitude-layer sweep: a batch of parts of n vertices
+    (G(*, 0.3) chain below 24 qubits, 0.2 from 24, weights 1..10) with
+    sum 2^n >= 2^28 amplitudes, p = 2, <C> only, schedule chosen by the
+    autotuner; amplitude-layers/s over the summed device time of every kernel,
+    its fraction of the 16 B roofline, and the layer passes' own bandwidth
+    against the measured HBM peak (n <= 14 stays on chip: no HBM roofline)."""
     import torch
+    peak, _ = read_peaks()
+    count = max(1, (1 << 28) >> n)
+    sizes = [n] * min(count, 64)
+    nv = int(sum(sizes) - (len(sizes) - 1))
+    g = synth.erdos_renyi(nv, 0.3 if n < 24 else 0.2, 7, wmax=10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    ids = np.resize(np.arange(len(sizes), dtype=np.int32), count)
+    gam, bet = synth.random_angles(count, 2, 11)
+    tuned = capi.paraqaoa_autotune(ctx, part, 2).get(n) if n >= 15 else None
+    capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)  # warm-up
+    capi.paraqaoa_expect(ctx, count)
+    capi.paraqaoa_profile_enable(ctx, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+        capi.paraqaoa_expect(ctx, count)
+    dt = time.perf_counter() - t0
+    lp = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
+    sm = capi.paraqaoa_profile_read(ctx, capi.KCLASS_SMEM_SIM)
+    dev_ms = sum(capi.paraqaoa_profile_read(ctx, k)[1] for k in range(6))
+    capi.paraqaoa_profile_enable(ctx, False)
+    amp_layers = reps * count * (1 << n) * 2
+    rate = amp_layers / (dev_ms / 1e3)
+    line = {"qubits": n, "instances": count, "p": 2, "amp_layers_per_s": rate,
+            "wall_amp_layers_per_s": amp_layers / dt, "roofline_frac_16B": rate * 16 / (peak * 1e9),
+            "schedule": tuned}
+    if lp[0]:
+        gbs = lp[2] / (lp[1] / 1e3) / 1e9
+        line.update({"layer_passes": int(lp[0] // reps), "layer_pass_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                     "hbm_bytes_per_amp_layer": lp[2] / amp_layers})
+    else:
+        line.update({"on_chip_ms": sm[1] / reps})
+    capi.paraqaoa_part_free(part)
+    return line
+
+
+def run_sweep_case(args):
     import paper_2603_26232_gb300 as pkg
     from paper_2603_26232_gb300 import _capi as capi
 
     pkg.build()
     ctx = capi.paraqaoa_create(0)
-    peak, kind = read_peaks()
+    for n in range(args.sweep_lo, args.sweep_hi + 1):
+        print(json.dumps(dict(case="sweep", **sweep_point(capi, ctx, n))), flush=True)
+    capi.paraqaoa_destroy(ctx)
+
+
+def run_shapes_case(args):
+    """Every distinct layer-pass schedule (tile shape, contiguous run, classic
+    or split, tiles per CTA) at n = sweep-lo..sweep-hi, on the sweep's batch
+    (sum 2^n >= 2^28, p = 2, <C> only): the layer passes' summed event time
+    per batch, their fraction of the 16 B roofline and their streamed bytes'
+    fraction of the measured copy bandwidth; the 12 fastest per n."""
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    peak, _ = read_peaks()
+    ctx = capi.paraqaoa_create(0)
+    shapes = [(12, 5), (12, 4), (13, 5), (13, 4), (14, 4)]
     for n in range(args.sweep_lo, args.sweep_hi + 1):
         count = max(1, (1 << 28) >> n)
         sizes = [n] * min(count, 64)
@@ -427,35 +492,210 @@ def run_sweep_case(args):
         part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
         ids = np.resize(np.arange(len(sizes), dtype=np.int32), count)
         gam, bet = synth.random_angles(count, 2, 11)
-        tuned = capi.paraqaoa_autotune(ctx, part, 2).get(n) if n >= 15 else None
-        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)  # warm-up
-        capi.paraqaoa_expect(ctx, count)
-        capi.paraqaoa_profile_enable(ctx, True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        reps = 3
-        for _ in range(reps):
-            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
-            capi.paraqaoa_expect(ctx, count)
-        dt = time.perf_counter() - t0
-        lp = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
-        sm = capi.paraqaoa_profile_read(ctx, capi.KCLASS_SMEM_SIM)
-        dev_ms = sum(capi.paraqaoa_profile_read(ctx, k)[1] for k in range(6))
-        capi.paraqaoa_profile_enable(ctx, False)
-        amp_layers = reps * count * (1 << n) * 2
-        rate = amp_layers / (dev_ms / 1e3)
-        line = {"case": "sweep", "qubits": n, "instances": count, "p": 2,
-                "amp_layers_per_s": rate, "wall_amp_layers_per_s": amp_layers / dt,
-                "roofline_frac_16B": rate * 16 / (peak * 1e9), "schedule": tuned}
-        if lp[0]:
-            gbs = lp[2] / (lp[1] / 1e3) / 1e9
-            line.update({"layer_passes": int(lp[0] // reps), "layer_pass_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                         "hbm_bytes_per_amp_layer": lp[2] / amp_layers})
-        else:
-            line.update({"on_chip_ms": sm[1] / reps})
-        print(json.dumps(line), flush=True)
+        rows, seen = [], set()
+        for tb, r in shapes:
+            for sp in (0, 1):
+                for cm in (2, 3, 4):
+                    for tpc in range(4):
+                        try:
+                            capi.paraqaoa_set_schedule(ctx, n, tb, r, cm, sp, tpc)
+                        except capi.ParaQAOAError:
+                            continue
+                        sched = capi.paraqaoa_schedule(n, 2, tb, r, cm, sp)
+                        key = (tb, r, sp, tuple((d["c"], d["s"]) for d in sched), tpc)
+                        if key in seen:
+                            continue
+                        seen.add(key)
+                        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+                        capi.paraqaoa_expect(ctx, count)
+                        capi.paraqaoa_profile_enable(ctx, True)
+                        capi.paraqaoa_profile_classes(ctx, 1 << capi.KCLASS_LAYER_PASS)
+                        for _ in range(3):
+                            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT)
+                            capi.paraqaoa_expect(ctx, count)
+                        lp = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
+                        capi.paraqaoa_profile_enable(ctx, False)
+                        capi.paraqaoa_profile_classes(ctx, 0xFFFFFFFF)
+                        ms = lp[1] / 3
+                        frac16 = count * (1 << n) * 2 * 16 / (ms / 1e3) / (peak * 1e9)
+                        rows.append({"tile_bits": tb, "reg_bits": r, "split": sp, "c_min": cm, "tiles_per_cta_log2": tpc,
+                                     "passes": len(sched), "ms": ms, "frac_16B": frac16,
+                                     "pass_frac_of_copy": lp[2] / (lp[1] / 1e3) / 1e9 / peak})
+        rows.sort(key=lambda x: x["ms"])
+        print(json.dumps({"case": "shapes", "qubits": n, "instances": count, "p": 2, "fastest": rows[:12]}), flush=True)
         capi.paraqaoa_part_free(part)
     capi.paraqaoa_destroy(ctx)
+
+
+def onchip_measure(capi, ctx, peaks):
+    """Roofline of the on-chip kernel (states of 10..14 qubits held in
+    registers and shared memory for all p layers): its flops and shared-memory
+    bytes over its event time against the probed FP32 and shared-memory peaks.
+    Per amplitude-layer it does n butterflies (one FFMA2, 4 flops, each) and a
+    phase multiply (6 flops), and moves 16 B through shared memory per
+    transpose: 2 transposes per layer (one at n = 10); <C> adds 3 flops per
+    amplitude. Workloads: the 12..14-vertex parts of the batching
+    configuration (G(2000, 0.05), p = 3) as they come, and 256 angle sets of
+    each (the shape of a grid-search batch)."""
+    fp32, smem = peaks
+    g = synth.erdos_renyi(2000, 0.05, 0, wmax=1)
+    sizes = synth.uneven_sizes(2000, 12, 24, 1)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    small = np.flatnonzero((sizes >= 12) & (sizes <= 14)).astype(np.int32)
+    out = {"fp32_peak_tflops": fp32, "smem_peak_tbs": smem, "parts": int(len(small))}
+    for name, reps_ids in (("c3_parts", small), ("x256_angle_sets", np.repeat(small, 256))):
+        ids = reps_ids.astype(np.int32)
+        gam, bet = synth.random_angles(len(ids), 3, 5)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+        capi.paraqaoa_expect(ctx, len(ids))
+        capi.paraqaoa_profile_enable(ctx, True)
+        reps = 5
+        for _ in range(reps):
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+            capi.paraqaoa_expect(ctx, len(ids))
+        n_l, ms, _ = capi.paraqaoa_profile_read(ctx, capi.KCLASS_SMEM_SIM)
+        capi.paraqaoa_profile_enable(ctx, False)
+        n = sizes[ids].astype(np.int64)
+        amps = float(np.sum(np.left_shift(1, n)))
+        flops = reps * float(np.sum(np.left_shift(1, n) * (3 * (4 * n + 6) + 3)))
+        sbytes = reps * float(np.sum(np.left_shift(1, n) * 3 * np.where(n > 10, 32, 16)))
+        sec = ms / 1e3
+        out[name] = {"instances": int(len(ids)), "launches": int(n_l), "ms_per_batch": ms / reps,
+                     "amp_layers_per_s": reps * amps * 3 / sec,
+                     "tflops": flops / sec / 1e12, "frac_fp32": flops / sec / 1e12 / fp32,
+                     "smem_tbs": sbytes / sec / 1e12, "frac_smem": sbytes / sec / 1e12 / smem}
+    capi.paraqaoa_part_free(part)
+    return out
+
+
+def run_onchip_case(args):
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    peaks = capi.paraqaoa_probe_peaks(0)
+    ctx = capi.paraqaoa_create(0)
+    out = dict(case="onchip", **onchip_measure(capi, ctx, peaks))
+    capi.paraqaoa_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
+def run_merge_levels_case(args):
+    """Level-aware merge at the paper's scale (Sec. 3.4.2; Sec. 4.2 runs 600
+    vertices with K = 2 and L = 1..3): G(600, P), unit weights, seed 0, for
+    P in 0.1 / 0.3 / 0.5 / 0.8, 24 parts of 25-26 vertices, the top-2 of each
+    part from the p = 1 grid, and the exhaustive merge over all 2^24 paths
+    with the GPU walk filled (at least 2^17 starting paths) for L = 1, 2, 3.
+    The paper's worker scaling (K^L walkers, one GPU thread each, fill off) is
+    timed on the first 12 parts of the P = 0.1 graph (4096 paths)."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    solver = pkg.Solver()
+    ctx = solver.ctx
+    out = {"case": "merge_levels", "graphs": []}
+
+    def timed_merge(G, part, cand, K, L, reps=3):
+        capi.paraqaoa_merge(ctx, G, part, cand, K, L, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            side, cut = capi.paraqaoa_merge(ctx, G, part, cand, K, L, 0)
+        return (time.perf_counter() - t0) / reps, int(cut), capi.paraqaoa_set_merge_fill(ctx, -1)
+
+    for pe in (0.1, 0.3, 0.5, 0.8):
+        g = synth.erdos_renyi(600, pe, 0, wmax=1)
+        G = capi.Graph.of(g)
+        M = 24
+        part = capi.paraqaoa_partition(G, M)
+        ids = np.arange(M, dtype=np.int32)
+        gam, bet, _ = capi.paraqaoa_angle_search(ctx, part, ids, 1, 16, 0)
+        _, cand, _ = capi.paraqaoa_final_topk(ctx, part, ids, 1, gam, bet, 2)
+        row = {"graph": f"G(600,{pe})", "edges": g.num_edges, "parts": M, "K": 2, "paths": 2 ** M, "levels": []}
+        for L in (1, 2, 3):
+            dt, cut, used = timed_merge(G, part, cand, 2, L)
+            row["levels"].append({"L": L, "starting_level_used": used, "s": dt, "cut": cut})
+        out["graphs"].append(row)
+        print(json.dumps(row), flush=True)
+        if pe == 0.1:
+            nv12 = 12 * 25 + 1
+            g12 = synth.erdos_renyi(nv12, pe, 0, wmax=1)
+            G12 = capi.Graph.of(g12)
+            p12 = capi.paraqaoa_partition(G12, 12)
+            ids12 = np.arange(12, dtype=np.int32)
+            g1, b1, _ = capi.paraqaoa_angle_search(ctx, p12, ids12, 1, 16, 0)
+            _, c12, _ = capi.paraqaoa_final_topk(ctx, p12, ids12, 1, g1, b1, 2)
+            scal = []
+            for fill in (0, 1):
+                capi.paraqaoa_set_merge_fill(ctx, fill)
+                for L in (1, 2, 3):
+                    dt, cut, used = timed_merge(G12, p12, c12, 2, L)
+                    scal.append({"fill": fill, "L": L, "gpu_walkers": 2 ** used, "s": dt, "cut": cut})
+            capi.paraqaoa_set_merge_fill(ctx, 1)
+            out["worker_scaling"] = {"graph": f"G({nv12},{pe})", "parts": 12, "K": 2, "paths": 4096, "runs": scal}
+            print(json.dumps(out["worker_scaling"]), flush=True)
+            capi.paraqaoa_part_free(p12)
+        capi.paraqaoa_part_free(part)
+    solver.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_ksweep_case(args):
+    """Top-K sweep (Sec. 4.2: cut and time against K) and the Performance
+    Efficiency Index (Sec. 3.5: PEI = AR x EF x 100, EF = 1 / (1 + exp(alpha
+    (T_ALG - T_Base))), alpha = 0.001 per second).
+    (a) G(200, P), unit weights, seed 0, P in 0.1 / 0.3 / 0.5 / 0.8: 8 parts
+    of 25-26 vertices, p = 1 grid, top-K, exhaustive merge, K = 1, 2, 4, 8;
+    solve time and cut per K; AR against the best cut of the sweep (the
+    paper's GW reference is out of scope), T_Base = the K = 1 solve.
+    (b) G(n, P) for n = 20, 22, 24, 26 (the paper's small-scale sizes): two
+    parts, K = 1, 4, 16; AR against the exact maximum cut, the largest entry
+    of the whole graph's cut table (computed on the GPU, one part of n
+    vertices)."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    solver = pkg.Solver()
+    out = {"case": "ksweep", "alpha_per_s": 1e-3, "sweep_200": [], "small_exact": []}
+    for pe in (0.1, 0.3, 0.5, 0.8):
+        g = synth.erdos_renyi(200, pe, 0, wmax=1)
+        rows = []
+        for K in (1, 2, 4, 8):
+            cfg = pkg.SolveConfig(M=8, K=K, p=1, grid_points=16)
+            solver.solve(g, cfg)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = solver.solve(g, cfg)
+            torch.cuda.synchronize()
+            rows.append({"K": K, "s": time.perf_counter() - t0, "cut": int(r.cut)})
+        best = max(x["cut"] for x in rows)
+        for x in rows:
+            x["ar_vs_best_of_sweep"] = x["cut"] / best
+            x["ef"], x["pei"] = capi.paraqaoa_pei(x["ar_vs_best_of_sweep"], x["s"], rows[0]["s"], 1e-3)
+        out["sweep_200"].append({"graph": f"G(200,{pe})", "edges": g.num_edges, "rows": rows})
+        print(json.dumps(out["sweep_200"][-1]), flush=True)
+    for n in (20, 22, 24, 26):
+        for pe in (0.1, 0.3, 0.5, 0.8):
+            g = synth.erdos_renyi(n, pe, 0, wmax=1)
+            whole = capi.paraqaoa_partition(capi.Graph.of(g), 1)
+            opt = int(capi.paraqaoa_cut_table(solver.ctx, whole, 0, n).max())
+            capi.paraqaoa_part_free(whole)
+            row = {"graph": f"G({n},{pe})", "opt": opt, "rows": []}
+            for K in (1, 4, 16):
+                t0 = time.perf_counter()
+                r = solver.solve(g, pkg.SolveConfig(M=2, K=K, p=1, grid_points=16))
+                dt = time.perf_counter() - t0
+                ar = r.cut / opt if opt else 1.0
+                ef, pei = capi.paraqaoa_pei(ar, dt, dt, 1e-3)
+                row["rows"].append({"K": K, "s": dt, "cut": int(r.cut), "ar": ar, "pei_at_parity": pei})
+            out["small_exact"].append(row)
+            print(json.dumps(row), flush=True)
+    solver.close()
+    print(json.dumps(out), flush=True)
 
 
 def run_learned_case(args):
@@ -580,13 +820,18 @@ def main():
     ap.add_argument("--sweep-lo", type=int, default=14)
     ap.add_argument("--sweep-hi", type=int, default=26)
     ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large", "learned", "sweep",
-                                                        "batching", "tc"],
+                                                        "batching", "tc", "shapes", "onchip", "merge_levels",
+                                                        "ksweep"],
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--layer-p", type=int, default=2, help="layer_pass case: QAOA depth of the batch (1: the "
+                                                             "grid batches' two half passes, 2: the Adam batches)")
     ap.add_argument("--sched", default="", help="fixed schedule of the 20-qubit parts instead of the autotuner: "
                                                 "tile_bits,reg_bits,c_min,split[,tiles_per_cta_log2]")
     ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex learned-form time-to-cut")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batching configuration and the n = 22 / 26 sweep points of the default line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the context's default tile choice (fixed launch sequence for ncu)")
     ap.add_argument("--replicas", action="store_true",
@@ -615,6 +860,14 @@ def main():
         return run_batching_case(args)
     if args.case == "tc":
         return run_tc_case(args)
+    if args.case == "shapes":
+        return run_shapes_case(args)
+    if args.case == "onchip":
+        return run_onchip_case(args)
+    if args.case == "merge_levels":
+        return run_merge_levels_case(args)
+    if args.case == "ksweep":
+        return run_ksweep_case(args)
 
     import torch
     import paper_2603_26232_gb300 as pkg
@@ -711,7 +964,17 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     ms, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
-    large = None
+    large = batching = sweep = None
+    if rank == 0 and not args.no_extras:
+        # the batching configuration and two points of the amplitude-layer
+        # sweep, on a context of their own (their autotuning leaves the
+        # solver's schedules alone)
+        xctx = capi.paraqaoa_create(local)
+        try:
+            batching = batching_measure(capi, xctx)
+            sweep = [sweep_point(capi, xctx, n) for n in (22, 26)]
+        finally:
+            capi.paraqaoa_destroy(xctx)
     if rank == 0 and not args.no_large:
         large = large_learned(capi, pkg)
     amps_step = amp_layers_per_graph() * len(graphs)
@@ -754,6 +1017,8 @@ def main():
                                    for pe, sc in zip(DENSITIES, sched)],
             "cpu_baseline": cb,
             "time_to_cut_16k": large,
+            "batching": batching,
+            "sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     solver.close()

@@ -117,6 +117,14 @@ int paraqaoa_part_info(const paraqaoa_part *part, int32_t *M, int32_t *first, in
 int paraqaoa_shard_plan(const paraqaoa_part *part, int32_t world, int32_t p, const double *evals,
                         int32_t *out_rank, double *out_load);
 
+/* Sec. 3.5, Performance Efficiency Index: EF = 1 / (1 + exp(alpha (t_alg -
+ * t_base))) (the efficiency factor; 0.5 at t_alg = t_base, towards 1 when
+ * the evaluated run is much faster than the baseline) and PEI = AR x EF x
+ * 100 with AR = CutVal_ALG / CutVal_OPT. Times in the unit alpha is given
+ * per (the paper takes alpha = 0.001); ar, times and alpha must be >= 0.
+ * ef_out / pei_out optional. Host-only. */
+int paraqaoa_pei(double ar, double t_alg, double t_base, double alpha, double *ef_out, double *pei_out);
+
 /* Local edge list (u < v, sorted) of part `id`; arrays sized by part_info. */
 int paraqaoa_part_edges(const paraqaoa_part *part, int32_t id, int32_t *u, int32_t *v, int32_t *w);
 
@@ -171,6 +179,17 @@ int paraqaoa_state(paraqaoa_ctx *ctx, int32_t i, float *out_host);
 int paraqaoa_merge(paraqaoa_ctx *ctx, const paraqaoa_csr *g, const paraqaoa_part *part,
                    const uint32_t *cand, int32_t K, int32_t L, int64_t beam, uint8_t *out_side,
                    int64_t *out_cut);
+
+/* Exhaustive merge parallelism. Sec. 3.4.2 walks K^L starting paths in
+ * parallel processes (2K^L workers with both orientations); the answer, the
+ * first best leaf in lexicographic order, does not depend on L. With fill on
+ * (the default) paraqaoa_merge starts its GPU walk at the first level L' >= L
+ * with K^L' >= 2^17 starting paths (at most M levels and 2^30 paths), so
+ * that every SM has work; off, it walks exactly K^L paths, one GPU thread
+ * each, as the paper's L prescribes (for comparing against its worker
+ * counts). enable < 0 leaves the setting; levels_used (optional) receives the
+ * starting level the last exhaustive merge of ctx used. */
+int paraqaoa_set_merge_fill(paraqaoa_ctx *ctx, int32_t enable, int32_t *levels_used);
 
 /* p = 1 grid search (angle loop, first stage): gamma_a = pi a / points,
  * beta_b = (pi/2) b / points for a, b in [0, points); every part in ids is
@@ -380,6 +399,24 @@ int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, i
                       int32_t *out_reg_bits, int32_t *out_c_min, int32_t *out_split,
                       int32_t *out_tiles_per_cta_log2);
 
+/* Persistent layer passes (on/off; off by default). On: every pass of every
+ * size class of n >= 15 qubits that shares a tile shape runs in ONE launch
+ * of a persistent kernel (grid: the resident CTAs of the shape on every SM)
+ * over a work queue of (pass, instance, tile group) items, ordered pass by
+ * pass across the size classes; a CTA takes the next item from a global
+ * counter and waits for its instance's previous pass to finish (every item
+ * waits only for items taken before it, so the queue always progresses).
+ * Each wait is bounded (paraqaoa_set_wait_limit); one that gives up lets its
+ * item run on, and the call that returns the results (paraqaoa_expect,
+ * paraqaoa_topk, paraqaoa_grid_search, paraqaoa_optimize) returns
+ * PARAQAOA_E_TIMEOUT. The phase tables and cut constants are built by
+ * separate launches before it, <C> is reduced by one launch per size class
+ * after it, and the on-chip classes (n <= 14) run beside it; Adam steps
+ * replay all of it from one CUDA graph. Results equal the per-pass
+ * launches' bit for bit. No counterpart in the paper, which runs one solver
+ * per subgraph (Sec. 3.3). */
+int paraqaoa_set_persistent(paraqaoa_ctx *ctx, int32_t enable);
+
 /* Set the layer-pass schedule of n-qubit parts by hand (the choice the
  * autotuner makes): tile bits and register bits per thread (one of the
  * shapes 12/5, 12/4, 13/5), minimum contiguous run c_min of the higher groups,
@@ -409,6 +446,15 @@ int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32
 #define PARAQAOA_PASS_FIELDS 11
 int paraqaoa_schedule(int32_t n, int32_t p, int32_t tile_bits, int32_t reg_bits, int32_t c_min, int32_t split,
                       int32_t keep, int32_t expect, int32_t max_passes, int32_t *out, int32_t *out_count);
+
+/* Measured throughput of device `device` for the roofline of the on-chip
+ * simulation (states of <= 14 qubits, which stay in registers and shared
+ * memory between layers): packed FP32 FMA (FFMA2; two FMAs, four flops,
+ * per instruction) in TFLOP/s, and shared-memory store + load bandwidth in
+ * TB/s, each the best of three timed launches of a probe kernel that keeps
+ * every SM busy. Allocates and frees its own small buffers; synchronises.
+ * No counterpart in the paper. */
+int paraqaoa_probe_peaks(int device, double *fp32_tflops, double *smem_tbs);
 
 /* Per-kernel device time recorded with CUDA events on the context stream.
  * enable != 0 starts recording (and clears the counters). While it is on,

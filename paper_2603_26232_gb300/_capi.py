@@ -80,6 +80,10 @@ _SIGS = {
     "paraqaoa_final_topk": ([P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_uint32,
                              P, P, P], ctypes.c_int),
     "paraqaoa_set_wait_limit": ([P, ctypes.c_int64], ctypes.c_int),
+    "paraqaoa_set_persistent": ([P, ctypes.c_int32], ctypes.c_int),
+    "paraqaoa_probe_peaks": ([ctypes.c_int, P, P], ctypes.c_int),
+    "paraqaoa_set_merge_fill": ([P, ctypes.c_int32, P], ctypes.c_int),
+    "paraqaoa_pei": ([ctypes.c_double] * 4 + [P, P], ctypes.c_int),
     "paraqaoa_mlp_param_count": ([ctypes.c_int32], ctypes.c_int64),
     "paraqaoa_mlp_create": ([P, ctypes.c_int32, P, ctypes.POINTER(P)], ctypes.c_int),
     "paraqaoa_mlp_free": ([P], None),
@@ -363,6 +367,35 @@ def paraqaoa_final_topk(ctx, part, ids, p: int, gamma, beta, K: int, flags: int 
     _check(load().paraqaoa_final_topk(ctx, part, _ptr(ids), ids.size, int(p), _ptr(g), _ptr(b), int(K), int(flags),
                                       _ptr(ex), _ptr(z), _ptr(pr)), "paraqaoa_final_topk")
     return ex, z, pr
+
+
+def paraqaoa_set_persistent(ctx, enable: bool = True):
+    _check(load().paraqaoa_set_persistent(ctx, 1 if enable else 0), "paraqaoa_set_persistent")
+
+
+def paraqaoa_pei(ar: float, t_alg: float, t_base: float, alpha: float = 1e-3):
+    """(EF, PEI) of a run (Sec. 3.5)."""
+    ef = ctypes.c_double(0.0)
+    pei = ctypes.c_double(0.0)
+    _check(load().paraqaoa_pei(float(ar), float(t_alg), float(t_base), float(alpha), ctypes.byref(ef),
+                               ctypes.byref(pei)), "paraqaoa_pei")
+    return ef.value, pei.value
+
+
+def paraqaoa_set_merge_fill(ctx, enable: int = -1) -> int:
+    """Set the exhaustive merge's fill mode (1 on, 0 off, -1 keep); returns the
+    starting level the context's last exhaustive merge used."""
+    lv = ctypes.c_int32(0)
+    _check(load().paraqaoa_set_merge_fill(ctx, int(enable), ctypes.byref(lv)), "paraqaoa_set_merge_fill")
+    return int(lv.value)
+
+
+def paraqaoa_probe_peaks(device: int = 0):
+    """(FP32 TFLOP/s, shared-memory TB/s) measured on the device."""
+    f = ctypes.c_double(0.0)
+    m = ctypes.c_double(0.0)
+    _check(load().paraqaoa_probe_peaks(int(device), ctypes.byref(f), ctypes.byref(m)), "paraqaoa_probe_peaks")
+    return f.value, m.value
 
 
 def paraqaoa_set_wait_limit(ctx, ns: int):

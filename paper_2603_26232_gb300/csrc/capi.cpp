@@ -242,6 +242,14 @@ int paraqaoa_part_info(const paraqaoa_part* pt, int32_t* M, int32_t* first, int3
   return PARAQAOA_OK;
 }
 
+int paraqaoa_pei(double ar, double t_alg, double t_base, double alpha, double* ef_out, double* pei_out) {
+  if (!(alpha >= 0.0) || !(t_alg >= 0.0) || !(t_base >= 0.0) || !(ar >= 0.0)) return PARAQAOA_E_INVAL;
+  const double ef = 1.0 / (1.0 + std::exp(alpha * (t_alg - t_base)));
+  if (ef_out) *ef_out = ef;
+  if (pei_out) *pei_out = ar * ef * 100.0;
+  return PARAQAOA_OK;
+}
+
 int paraqaoa_shard_plan(const paraqaoa_part* pt, int32_t world, int32_t p, const double* evals, int32_t* out_rank,
                         double* out_load) {
   if (!pt || world < 1 || p < 1 || !out_rank) return PARAQAOA_E_INVAL;
@@ -314,6 +322,7 @@ int paraqaoa_simulate_batch(paraqaoa_ctx* c, const paraqaoa_part* pt, const int3
   if (rc) return rc;
   rc = plan_build(c, pt, ids, count, p, flags);
   if (rc) return rc;
+  if (c->persistent && (rc = persist_clear(c))) return rc;
   PQ_CUDA(cudaMemcpyAsync(c->d_gamma.p, gamma, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
   PQ_CUDA(cudaMemcpyAsync(c->d_beta.p, beta, sizeof(double) * count * p, cudaMemcpyHostToDevice, c->stream));
   return plan_run(c);
@@ -326,7 +335,7 @@ int paraqaoa_expect(paraqaoa_ctx* c, int32_t count, double* out_host) {
   PQ_CUDA(cudaSetDevice(c->device));
   PQ_CUDA(cudaMemcpyAsync(out_host, c->d_expect.p, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
-  return PARAQAOA_OK;
+  return c->plan.persist_used ? persist_status(c) : PARAQAOA_OK;
 }
 
 int paraqaoa_topk(paraqaoa_ctx* c, int32_t count, int32_t K, uint32_t* out_z, float* out_p,
@@ -335,6 +344,10 @@ int paraqaoa_topk(paraqaoa_ctx* c, int32_t count, int32_t K, uint32_t* out_z, fl
   if (!c->plan.valid || c->plan.count != count || !(c->plan.flags & PARAQAOA_SIM_KEEP_STATE))
     return PARAQAOA_E_NO_RESULT;
   PQ_CUDA(cudaSetDevice(c->device));
+  if (c->plan.persist_used) {
+    const int prc = persist_status(c);
+    if (prc) return prc;
+  }
   const int raw = (flags & PARAQAOA_TOPK_RAW) ? 1 : 0;
   std::vector<int64_t> off(count + 1, 0);
   for (int32_t i = 0; i < count; ++i) {
@@ -393,6 +406,13 @@ int paraqaoa_schedule(int32_t n, int32_t p, int32_t tile_bits, int32_t reg_bits,
   return PARAQAOA_OK;
 }
 
+int paraqaoa_set_persistent(paraqaoa_ctx* c, int32_t enable) {
+  if (!c) return PARAQAOA_E_INVAL;
+  c->persistent = enable != 0;
+  c->plan.valid = false;
+  return PARAQAOA_OK;
+}
+
 int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2) {
   if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || (split != 0 && split != 1) ||
@@ -401,6 +421,9 @@ int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t
   for (int kind = 0; kind < kTileKinds; ++kind)
     if (kTileShapes[kind].tb == tile_bits && kTileShapes[kind].r == reg_bits) {
       if (n < tile_bits || (split && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
+      // four-round shapes mix high groups in at most three rounds, which
+      // needs at least two contiguous qubits carried
+      if (tile_bits > 3 * reg_bits && c_min < 2) return PARAQAOA_E_INVAL;
       c->tile_kind[n] = (int8_t)kind;
       c->c_min[n] = (int8_t)c_min;
       c->split[n] = (int8_t)split;

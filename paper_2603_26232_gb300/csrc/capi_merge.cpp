@@ -99,10 +99,20 @@ int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* 
     if (L > M) L = M;
     int64_t nprefix = 1;
     for (int32_t i = 0; i < L; ++i) nprefix *= K;
+    // The first best leaf in lexicographic order wins whatever the starting
+    // level, so the walk may start deeper than L to give every SM work: at
+    // least kMergeFillThreads starting paths when the tree has that many
+    // (unless the context keeps exactly K^L, the paper's worker count).
+    if (c->merge_fill)
+      while (L < M && nprefix < kMergeFillThreads && nprefix * K <= (int64_t(1) << 30)) {
+        ++L;
+        nprefix *= K;
+      }
     while (nprefix > (int64_t(1) << 30) && L > 1) {
       --L;
       nprefix /= K;
     }
+    c->merge_levels_used = L;
     PQ_CUDA(c->m_key.ensure(8));
     PQ_CUDA(c->m_path.ensure(4 * (size_t)M));
     PQ_CUDA(cudaMemsetAsync(c->m_key.p, 0, 8, c->stream));
@@ -172,6 +182,13 @@ int paraqaoa_merge(paraqaoa_ctx* c, const paraqaoa_csr* g, const paraqaoa_part* 
   const uint8_t flip = (uint8_t)(packed[0] & 1u);
   for (int32_t v = 0; v < nv; ++v) out_side[v] = (uint8_t)(((packed[v >> 5] >> (v & 31)) & 1u) ^ flip);
   *out_cut = best;
+  return PARAQAOA_OK;
+}
+
+int paraqaoa_set_merge_fill(paraqaoa_ctx* c, int32_t enable, int32_t* levels_used) {
+  if (!c) return PARAQAOA_E_INVAL;
+  if (enable >= 0) c->merge_fill = enable != 0;
+  if (levels_used) *levels_used = c->merge_levels_used;
   return PARAQAOA_OK;
 }
 

@@ -15,6 +15,7 @@ int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   PQ_CUDA(cudaSetDevice(c->device));
   int rc = upload_part(c, pt, false);
   if (rc) return rc;
+  if (c->persistent && (rc = persist_clear(c))) return rc;
   const int32_t G = points * points;
   const int64_t total = (int64_t)count * G;
   if (total > 0x7fffffff) return PARAQAOA_E_INVAL;
@@ -60,7 +61,7 @@ int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
     PQ_CUDA(cudaMemcpyAsync(out_values, c->o_vals.p, sizeof(double) * total, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
   c->plan.valid = false;
-  return PARAQAOA_OK;
+  return c->persistent ? persist_status(c) : PARAQAOA_OK;
 }
 
 int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
@@ -72,6 +73,7 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
   PQ_CUDA(cudaSetDevice(c->device));
   int rc = upload_part(c, pt, false);
   if (rc) return rc;
+  if (c->persistent && (rc = persist_clear(c))) return rc;
   const int32_t D = 2 * p, E = 4 * p;
   std::vector<double> theta((size_t)count * D), wsum(count);
   for (int32_t s = 0; s < count; ++s) {
@@ -175,7 +177,7 @@ int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* i
     PQ_CUDA(cudaStreamSynchronize(c->stream));
     s0 += ns;
   }
-  return PARAQAOA_OK;
+  return c->persistent ? persist_status(c) : PARAQAOA_OK;
 }
 
 }  // extern "C"

@@ -90,6 +90,20 @@ struct SimPlan {
   // the layer passes' cut constants (functions of the parts and the pass
   // layouts only) are on the device from an earlier run of this plan
   bool cc_ready = false;
+  // persistent form: per tile shape used, its segments' range in the
+  // segment array, its work items and its control block (uploaded by the
+  // plan's first run)
+  struct PersistGroup {
+    int kind;
+    int32_t seg0, nseg;
+    int64_t items;
+    int32_t ctl_off;          // uint64 offset of its control block (2 words + counters)
+    std::vector<int> classes;  // qubit counts of its size classes
+    double bytes;
+  };
+  std::vector<PersistGroup> persist;
+  bool persist_used = false;
+  int64_t persist_ctl_words = 0;
 };
 
 constexpr int kSideStreams = 4;
@@ -140,6 +154,15 @@ struct paraqaoa_ctx {
   // limit in nanoseconds (paraqaoa_set_wait_limit)
   pqh::DevBuf d_tc_err;
   uint64_t wait_ns = 200000000ull;
+  // persistent layer passes (paraqaoa_set_persistent): segment table,
+  // control blocks and the sticky error word of their bounded waits
+  bool persistent = false;
+  pqh::DevBuf d_pseg, d_pctl, d_perr;
+  // exhaustive merge: start the walk deeper than the caller's L when that
+  // gives the GPU more starting paths (paraqaoa_set_merge_fill), and the
+  // starting level the last exhaustive merge used
+  bool merge_fill = true;
+  int32_t merge_levels_used = 0;
   // Adam step counter on the device (read by the update kernel)
   pqh::DevBuf o_step;
   // side streams for concurrent size classes, with their fork / join events
@@ -198,5 +221,9 @@ int upload_part(paraqaoa_ctx* c, const paraqaoa_part* pt, bool force);
 cudaError_t ensure_side_streams(paraqaoa_ctx* c);
 int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t p, uint32_t flags);
 int plan_run(paraqaoa_ctx* c);
+// Clear / read the sticky error word of the persistent layer passes' bounded
+// waits (PARAQAOA_E_TIMEOUT when one gave up since the last clear).
+int persist_clear(paraqaoa_ctx* c);
+int persist_status(paraqaoa_ctx* c);
 
 }  // namespace pqh

@@ -260,6 +260,71 @@ int plan_run(paraqaoa_ctx* c) {
     cc_total += q.nsets * q.elems;
   }
   if (!pl.cc_ready) PQ_CUDA(c->d_consts.ensure(sizeof(int32_t) * std::max<int64_t>(cc_total, 1)));
+  // Persistent form: the size classes of one tile shape share one launch
+  // over a work queue of (pass, instance, tile group) items, ordered pass by
+  // pass across the classes. The queue (segment table) is built and uploaded
+  // by the plan's first run, outside any stream capture; later runs (Adam
+  // steps, replayed graphs) only zero the control blocks and launch.
+  if (c->persistent && !pl.hbm.empty() && !pl.cc_ready) {
+    pl.persist.clear();
+    std::vector<PersistSeg> segs;
+    std::map<int, std::vector<int>> by_kind;
+    for (auto& kv : pl.hbm) by_kind[cs[kv.first].kind].push_back(kv.first);
+    int64_t ctl = 0;
+    for (auto& kk : by_kind) {
+      SimPlan::PersistGroup grp;
+      grp.kind = kk.first;
+      grp.classes = kk.second;
+      grp.seg0 = (int32_t)segs.size();
+      grp.ctl_off = (int32_t)ctl;
+      grp.bytes = 0.0;
+      int64_t item = 0, done = 0;
+      size_t maxp = 0;
+      for (int n : kk.second) maxp = std::max(maxp, cs[n].sched.size());
+      std::map<int, int32_t> last;  // class -> its previous pass's segment
+      for (size_t j = 0; j < maxp; ++j)
+        for (int n : kk.second) {
+          const ClassSched& q = cs[n];
+          if (j >= q.sched.size()) continue;
+          const auto& lst = pl.hbm[n];
+          PersistSeg sg;
+          std::memset(&sg, 0, sizeof(sg));
+          sg.pd = q.sched[j];
+          sg.pd.tpc_log2 = std::min<int>(c->tpc_log2[n], n - q.tb);
+          sg.n = n;
+          sg.nr = layer_pass_rounds(q.kind, sg.pd);
+          sg.list_off = lst.first;
+          sg.nlist = lst.second;
+          sg.per = (n - q.tb) - sg.pd.tpc_log2;
+          sg.prev = j == 0 ? -1 : last[n] - grp.seg0;  // the kernel indexes its group's segments
+          sg.done_off = (int32_t)done;
+          sg.item0 = item;
+          sg.cc_off = q.off + (int64_t)std::max(q.set[j], 0) * q.elems;
+          layer_pass_masks(q.kind, sg.pd, sg.mm);
+          last[n] = (int32_t)segs.size();
+          segs.push_back(sg);
+          item += (int64_t)lst.second << sg.per;
+          done += lst.second;
+          grp.bytes += (double)lst.second * (double)(int64_t(1) << n) *
+                       ((sg.pd.init ? 0.0 : 8.0) + (sg.pd.store ? 8.0 : 0.0));
+        }
+      grp.nseg = (int32_t)segs.size() - grp.seg0;
+      grp.items = item;
+      ctl += 2 + (done + 1) / 2;  // head and error words, then 32-bit counters packed two per word
+      pl.persist.push_back(grp);
+    }
+    pl.persist_ctl_words = ctl;
+    if (!c->d_perr.p) {
+      PQ_CUDA(c->d_perr.ensure(sizeof(uint64_t)));
+      PQ_CUDA(cudaMemsetAsync(c->d_perr.p, 0, sizeof(uint64_t), c->stream));
+    }
+    PQ_CUDA(c->d_pseg.ensure(sizeof(PersistSeg) * segs.size()));
+    PQ_CUDA(c->d_pctl.ensure(sizeof(uint64_t) * std::max<int64_t>(ctl, 1)));
+    PQ_CUDA(cudaMemcpyAsync(c->d_pseg.p, segs.data(), sizeof(PersistSeg) * segs.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+    PQ_CUDA(cudaStreamSynchronize(c->stream));  // segs is a temporary
+    pl.persist_used = true;
+  }
   if (pl.tiny.second > 0) {
     cudaStream_t st = cls_stream();
     ProfScope ps(c, PARAQAOA_KCLASS_SMEM_SIM, 0);
@@ -272,7 +337,48 @@ int plan_run(paraqaoa_ctx* c) {
     PQ_CUDA(launch_smem_sim(kv.first, inst, lists + kv.second.first, kv.second.second, p, subs,
                             planes, tables, states, expect, keep, want, pl.tabcap, st));
   }
+  if (pl.persist_used) {
+    for (const auto& grp : pl.persist) {
+      cudaStream_t st = cls_stream();
+      uint64_t* ctl = c->d_pctl.as<uint64_t>() + grp.ctl_off;
+      uint32_t* done = reinterpret_cast<uint32_t*>(ctl + 2);
+      const size_t ctl_bytes = sizeof(uint64_t) * (size_t)(
+          (&grp == &pl.persist.back() ? pl.persist_ctl_words : (&grp + 1)->ctl_off) - grp.ctl_off);
+      PQ_CUDA(cudaMemsetAsync(ctl, 0, ctl_bytes, st));
+      for (int n : grp.classes) {
+        const ClassSched& q = cs[n];
+        std::vector<char> done_cc(q.nsets, pl.cc_ready ? 1 : 0);
+        const auto reps = pl.hbm_reps[n];
+        for (size_t ip = 0; ip < q.sched.size(); ++ip) {
+          const int k = q.set[ip];
+          if (k < 0 || done_cc[k]) continue;
+          PassDesc pd = q.sched[ip];
+          int32_t* consts = c->d_consts.as<int32_t>() + q.off + (int64_t)k * q.elems;
+          ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+          PQ_CUDA(launch_cut_consts(q.kind, n, pd, inst, lists + reps.first, reps.second, subs, planes, consts, st));
+          done_cc[k] = 1;
+        }
+      }
+      {
+        ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, grp.bytes);
+        PQ_CUDA(launch_layer_persist(grp.kind, c->d_pseg.as<PersistSeg>() + grp.seg0, grp.nseg, grp.items, ctl, done,
+                                     inst, lists, subs, planes, tables, states, partials, pl.tabcap,
+                                     c->d_consts.as<int32_t>(), c->wait_ns, c->num_sms, st));
+      }
+      {  // a wait that gave up in this run stays reported until the next clear
+        ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+        PQ_CUDA(launch_flag_or(ctl + 1, c->d_perr.as<uint64_t>(), st));
+      }
+      if (want)
+        for (int n : grp.classes) {
+          ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
+          const auto& lst = pl.hbm[n];
+          PQ_CUDA(launch_expect_reduce(inst, lists + lst.first, lst.second, 1 << (n - cs[n].tb), partials, expect, st));
+        }
+    }
+  }
   for (auto& kv : pl.hbm) {
+    if (pl.persist_used) break;
     cudaStream_t st = cls_stream();
     const int n = kv.first;
     const ClassSched& q = cs[n];
@@ -308,6 +414,20 @@ int plan_run(paraqaoa_ctx* c) {
     }
   pl.cc_ready = true;
   return PARAQAOA_OK;
+}
+
+int persist_clear(paraqaoa_ctx* c) {
+  PQ_CUDA(c->d_perr.ensure(sizeof(uint64_t)));
+  PQ_CUDA(cudaMemsetAsync(c->d_perr.p, 0, sizeof(uint64_t), c->stream));
+  return PARAQAOA_OK;
+}
+
+int persist_status(paraqaoa_ctx* c) {
+  if (!c->d_perr.p) return PARAQAOA_OK;
+  uint64_t e = 0;
+  PQ_CUDA(cudaMemcpyAsync(&e, c->d_perr.p, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+  PQ_CUDA(cudaStreamSynchronize(c->stream));
+  return e ? PARAQAOA_E_TIMEOUT : PARAQAOA_OK;
 }
 
 }  // namespace pqh

@@ -91,26 +91,45 @@ __global__ void __launch_bounds__(1 << (TB - R))
 }
 
 // Occupancy target of a tile shape: resident CTAs per SM. The 16-register
-// shape fits 64 registers per thread (four CTAs of 256 threads); the 2^12 x 32
+// shapes fit 64 registers per thread: four CTAs of 256 threads (2^12), two of
+// 512 (2^13) or one of 1024 (2^14), 32 warps per SM each; the 2^12 x 32
 // shape is held to 96 registers for five CTAs of 128 threads (a few bytes of
-// spills, measured 3% faster than four CTAs at 128 registers).
-__host__ __device__ constexpr int layer_min_blocks(int tb, int r) { return r == 4 ? 4 : (tb >= 13 ? 2 : 5); }
+// spills, measured 3% faster than four CTAs at 128 registers); the 2^13 x 32
+// shape runs two CTAs of 256 threads.
+__host__ __device__ constexpr int layer_min_blocks(int tb, int r) {
+  return r == 4 ? (1 << (14 - tb)) : (tb >= 13 ? 2 : 5);
+}
 
+// State loads of a layer pass. CG: through L2 only (the persistent kernel
+// reads, in one launch, amplitudes that other SMs wrote earlier in the same
+// launch, which a stale L1 line must not serve).
+template <bool CG>
+__device__ __forceinline__ float2 ld_state(const float2* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// One CTA's share of a layer pass, work unit `bid` of the pass: instance
+// list[bid >> per] and its tiles tj, tj + 2^per, ... with tj = bid mod 2^per
+// (per = tiles_log2 - tpc_log2, 2^tpc_log2 tiles).
 // CONTIG: the pass's tile is 2^TB contiguous amplitudes (the low qubit
 // group, c = s = TB), so every register slot's offset is a compile-time
 // constant and loads and stores take immediate offsets from one base.
-template <int TB, int R, int NR, bool SPLIT, bool CONTIG>
-__global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
-    k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
-                 const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
-                 const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
-                 float2* __restrict__ states, double* __restrict__ partials, int32_t tabcap,
-                 const int32_t* __restrict__ consts, uint32_t mm0, uint32_t mm1, uint32_t mm2) {
+template <int TB, int R, int NR, bool SPLIT, bool CONTIG, bool CG>
+__device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_t tiles_log2, uint32_t bid,
+                                            const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list,
+                                            const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes_all,
+                                            const float2* __restrict__ tables, float2* __restrict__ states,
+                                            double* __restrict__ partials, int32_t tabcap,
+                                            const int32_t* __restrict__ consts, uint32_t mm0, uint32_t mm1,
+                                            uint32_t mm2, uint32_t mm3) {
   constexpr uint32_t NT = 1u << (TB - R);
   constexpr int KQ = 1 << R;  // registers per thread
-  constexpr int O0 = lay_off(TB, R, SPLIT, 0), O1 = lay_off(TB, R, SPLIT, 1), O2 = lay_off(TB, R, SPLIT, 2);
+  constexpr int O0 = lay_off(TB, R, SPLIT, 0), O1 = lay_off(TB, R, SPLIT, 1), O2 = lay_off(TB, R, SPLIT, 2),
+                O3 = lay_off(TB, R, SPLIT, 3);
   constexpr int OC = lay_off(TB, R, SPLIT, NR - 1);  // layout of the cut step (phase / <C>)
   static_assert(!SPLIT || NR == 2, "split passes mix two rounds");
+  static_assert(NR <= full_rounds(TB, R) || SPLIT, "no more rounds than the tile has register groups");
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* tab = reinterpret_cast<float2*>(smraw);
   float2* sm = tab + tabcap;
@@ -126,8 +145,8 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   // tiles, which keeps the DRAM pages of a pass with short contiguous runs
   // (a high qubit group) busy together
   const uint32_t per = (uint32_t)(tiles_log2 - pd.tpc_log2);
-  const int li_idx = (int)(blockIdx.x >> per);
-  const uint32_t tj = blockIdx.x & ((1u << per) - 1u);
+  const int li_idx = (int)(bid >> per);
+  const uint32_t tj = bid & ((1u << per) - 1u);
   const InstDev* Ip = inst_all + list[li_idx];
   const int P = Ip->P, W = Ip->W;
   const uint32_t* pl = planes_all + subs[Ip->sub].plane_off;
@@ -190,12 +209,12 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
 #pragma unroll
     for (int j = 0; j < R; ++j) e[j] = zmap(1u << (O0 + j));
     uint32_t off = 0;
-    a[0] = base[0];
+    a[0] = ld_state<CG>(base);
 #pragma unroll
     for (int i = 1; i < KQ; ++i) {
       const int k = gray(i), b = gray_bit(i);
       off = ((k >> b) & 1) ? off + e[b] : off - e[b];
-      a[k] = base[off];
+      a[k] = ld_state<CG>(base + off);
     }
   }
   // Set-up visible (first tile); later, this barrier keeps warp 0 from
@@ -235,19 +254,24 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
 #pragma unroll
     for (int j = 0; j < R; ++j) kap[j] = tc->lam[OC + j] + ccB[j];
   }
-  // round 2 (layout 2) only ever mixes slots below TB - 2R (the others repeat layout 1's)
-  constexpr uint32_t kAll = (1u << R) - 1u;
-  constexpr uint32_t kLow2 = SPLIT || (TB - 2 * R) >= R ? kAll : ((1u << (TB - 2 * R > 0 ? TB - 2 * R : 0)) - 1u);
+  // the last round of a classic pass overlaps the one before it when R does
+  // not divide TB: only its slots below the previous offset ever mix
+  constexpr uint32_t kS0 = round_slots(TB, R, SPLIT, 0), kS1 = round_slots(TB, R, SPLIT, 1),
+                     kS2 = round_slots(TB, R, SPLIT, 2), kS3 = round_slots(TB, R, SPLIT, 3);
   if (pd.layerA >= 0) {
     const float muA = Ip->mu[pd.layerA];
-    mix_regs_sel<R, kAll>(a, muA, mm0);
+    mix_regs_sel<R, kS0>(a, muA, mm0);
     if constexpr (NR > 1) {
       transposer_o<TB, R, O0, O1>(a, sm, tid);
-      mix_regs_sel<R, kAll>(a, muA, mm1);
+      mix_regs_sel<R, kS1>(a, muA, mm1);
     }
     if constexpr (NR > 2) {
       transposer_o<TB, R, O1, O2>(a, sm, tid);
-      mix_regs_sel<R, kLow2>(a, muA, mm2);
+      mix_regs_sel<R, kS2>(a, muA, mm2);
+    }
+    if constexpr (NR > 3) {
+      transposer_o<TB, R, O2, O3>(a, sm, tid);
+      mix_regs_sel<R, kS3>(a, muA, mm3);
     }
   }
   if (pd.layerP >= 0) {
@@ -262,15 +286,19 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   }
   if (pd.layerB >= 0) {
     const float muB = Ip->mu[pd.layerB];
+    if constexpr (NR > 3) {
+      mix_regs_sel<R, kS3>(a, muB, mm3);
+      transposer_o<TB, R, O3, O2>(a, sm, tid);
+    }
     if constexpr (NR > 2) {
-      mix_regs_sel<R, kLow2>(a, muB, mm2);
+      mix_regs_sel<R, kS2>(a, muB, mm2);
       transposer_o<TB, R, O2, O1>(a, sm, tid);
     }
     if constexpr (NR > 1) {
-      mix_regs_sel<R, kAll>(a, muB, mm1);
+      mix_regs_sel<R, kS1>(a, muB, mm1);
       transposer_o<TB, R, O1, O0>(a, sm, tid);
     }
-    mix_regs_sel<R, kAll>(a, muB, mm0);
+    mix_regs_sel<R, kS0>(a, muB, mm0);
   }
   if (pd.expect) {
     float acc = 0.f;
@@ -288,8 +316,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   }
   if (pd.store) {
     if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
-      if constexpr (NR == 3) transposer_o<TB, R, O2, O0>(a, sm, tid);
-      if constexpr (NR == 2) transposer_o<TB, R, O1, O0>(a, sm, tid);
+      if constexpr (NR > 1) transposer_o<TB, R, OC, O0>(a, sm, tid);
     }
     if (pd.last) {  // back from the gauge, times lambda_p
       const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zmap(lt)));
@@ -322,11 +349,23 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
   }
 }
 
+// One launch per pass: CTA b takes work unit b.
+template <int TB, int R, int NR, bool SPLIT, bool CONTIG>
+__global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
+    k_layer_pass(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
+                 const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
+                 const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
+                 float2* __restrict__ states, double* __restrict__ partials, int32_t tabcap,
+                 const int32_t* __restrict__ consts, uint32_t mm0, uint32_t mm1, uint32_t mm2, uint32_t mm3) {
+  layer_tiles<TB, R, NR, SPLIT, CONTIG, false>(pd, n, tiles_log2, blockIdx.x, inst_all, list, subs, planes_all,
+                                               tables, states, partials, tabcap, consts, mm0, mm1, mm2, mm3);
+}
+
 size_t layer_pass_smem(int kind, int tabcap) {
   const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
   const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - r));
   return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
-         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 16 * sizeof(double);
+         PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * sizeof(double);
 }
 
 
@@ -335,9 +374,30 @@ int64_t cut_consts_elems(int kind, int32_t nlist) {
   return (int64_t)nlist * cut_consts_stride(kTileShapes[kind].tb, kTileShapes[kind].r);
 }
 
+// Rounds a pass needs: enough that the last one's offset is at or below the
+// lowest local bit it mixes.
 static int pass_rounds(int tb, int r, const PassDesc& pd) {
   if (pd.split) return 2;
-  return 1 + (pd.mix_lo < tb - r) + (pd.mix_lo < tb - 2 * r);
+  int k = 1;
+  while (k < full_rounds(tb, r) && pd.mix_lo < lay_off(tb, r, false, k - 1)) ++k;
+  return k;
+}
+
+int layer_pass_rounds(int kind, const PassDesc& pd) {
+  return pass_rounds(kTileShapes[kind].tb, kTileShapes[kind].r, pd);
+}
+
+void layer_pass_masks(int kind, const PassDesc& pd, uint32_t mm[4]) {
+  const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
+  const int nr = pass_rounds(tb, r, pd);
+  const bool split = pd.split != 0;
+  for (int k = 0; k < 4; ++k) {
+    mm[k] = 0;
+    if (k >= nr) continue;
+    for (int j = 0; j < r; ++j)
+      if (((round_slots(tb, r, split, k) >> j) & 1u) && (split || lay_off(tb, r, split, k) + j >= pd.mix_lo))
+        mm[k] |= 1u << j;
+  }
 }
 
 template <int TB, int R, int OC>
@@ -354,19 +414,24 @@ cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev
   if (nlist <= 0 || !(pd.layerP >= 0 || pd.expect)) return cudaSuccess;
   const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
   const int rc = pass_rounds(tb, r, pd) - 1;
+#define PQ_CCA n, pd, inst, list, nlist, subs, planes, consts, st
 #define PQ_CC(TBV, RV) \
   do { \
     if (tb == TBV && r == RV) { \
-      if (pd.split) return launch_cc_t<TBV, RV, lay_off(TBV, RV, true, 1)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
-      if (rc == 0) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 0)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
-      if (rc == 1) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 1)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
-      return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 2)>(n, pd, inst, list, nlist, subs, planes, consts, st); \
+      if (pd.split) return launch_cc_t<TBV, RV, lay_off(TBV, RV, true, 1)>(PQ_CCA); \
+      if (rc == 0) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 0)>(PQ_CCA); \
+      if (rc == 1) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 1)>(PQ_CCA); \
+      if (rc == 2) return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 2)>(PQ_CCA); \
+      return launch_cc_t<TBV, RV, lay_off(TBV, RV, false, 3)>(PQ_CCA); \
     } \
   } while (0)
   PQ_CC(12, 5);
   PQ_CC(12, 4);
   PQ_CC(13, 5);
+  PQ_CC(13, 4);
+  PQ_CC(14, 4);
 #undef PQ_CC
+#undef PQ_CCA
   return cudaErrorInvalidValue;
 }
 
@@ -385,15 +450,16 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
   if (tpc < 0 || tpc > tiles_log2 || tpc > kMaxTpcLog2) return cudaErrorInvalidValue;
   const int64_t blocks = (int64_t)nlist << (tiles_log2 - tpc);
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-  // register slots each round mixes (mm0: layout 0, mm1: layout 1, mm2: layout 2)
-  uint32_t mm0 = 0, mm1 = 0, mm2 = 0;
-  for (int j = 0; j < R; ++j) {
-    if (SPLIT || TB - R + j >= pd.mix_lo) mm0 |= 1u << j;
-    if (SPLIT || TB - 2 * R + j >= pd.mix_lo) mm1 |= 1u << j;
-    if (!SPLIT && j >= pd.mix_lo && j < TB - 2 * R) mm2 |= 1u << j;
-  }
+  // register slots each round mixes: its slots at or above mix_lo that no
+  // earlier round covered (split passes mix every slot of both rounds)
+  uint32_t mm[4] = {0, 0, 0, 0};
+  for (int k = 0; k < NR; ++k)
+    for (int j = 0; j < R; ++j)
+      if (((round_slots(TB, R, SPLIT, k) >> j) & 1u) && (SPLIT || lay_off(TB, R, SPLIT, k) + j >= pd.mix_lo))
+        mm[k] |= 1u << j;
   k_layer_pass<TB, R, NR, SPLIT, CONTIG><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
-      pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts, mm0, mm1, mm2);
+      pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts, mm[0], mm[1], mm[2],
+      mm[3]);
   return cudaGetLastError();
 }
 
@@ -411,21 +477,150 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
   const bool contig = pd.c == tb && pd.s == tb;
   if (pd.split && !contig) return cudaErrorInvalidValue;
 #define PQ_ARGS kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st
+  // instantiated: split passes; the contiguous low group in all its rounds;
+  // other groups in one to three rounds (every high group carries at least
+  // two contiguous qubits, and the third round's offset is at most 2)
 #define PQ_LAUNCH(TBV, RV) \
   do { \
     if (tb == TBV && r == RV) { \
+      constexpr int kFull = full_rounds(TBV, RV); \
       if (pd.split) return launch_layer_t<TBV, RV, 2, true, true>(PQ_ARGS); \
-      if (contig && nr == 3) return launch_layer_t<TBV, RV, 3, false, true>(PQ_ARGS); \
+      if (contig && nr == kFull) return launch_layer_t<TBV, RV, kFull, false, true>(PQ_ARGS); \
+      if (contig) return cudaErrorInvalidValue; \
       if (nr == 1) return launch_layer_t<TBV, RV, 1, false, false>(PQ_ARGS); \
       if (nr == 2) return launch_layer_t<TBV, RV, 2, false, false>(PQ_ARGS); \
-      return launch_layer_t<TBV, RV, 3, false, false>(PQ_ARGS); \
+      if (nr == 3) return launch_layer_t<TBV, RV, 3, false, false>(PQ_ARGS); \
+      return cudaErrorInvalidValue; \
     } \
   } while (0)
   PQ_LAUNCH(12, 5);
   PQ_LAUNCH(12, 4);
   PQ_LAUNCH(13, 5);
+  PQ_LAUNCH(13, 4);
+  PQ_LAUNCH(14, 4);
 #undef PQ_LAUNCH
 #undef PQ_ARGS
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ persistent form
+// Every pass of every size class of one tile shape in one launch. Work items
+// are ordered pass by pass (all classes' first passes, then their second
+// passes, ...), instance by instance within a pass; a CTA takes the next item
+// from a global counter, waits until every item of its instance's previous
+// pass is done, runs the tile group and counts it done. An item only ever
+// waits for items taken before it, and those belong to CTAs that are
+// running, so the queue always progresses; every wait is bounded all the
+// same (the global nanosecond timer), and one that gives up raises the
+// error flag and lets the item through, so the launch ends.
+__device__ __forceinline__ uint64_t pq_global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int TB, int R>
+__global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
+    k_layer_persist(const PersistSeg* __restrict__ segs, int32_t nseg, int64_t items, uint64_t* ctrl,
+                    uint32_t* done, const InstDev* __restrict__ inst_all, const int32_t* __restrict__ lists,
+                    const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes_all,
+                    const float2* __restrict__ tables, float2* __restrict__ states, double* __restrict__ partials,
+                    int32_t tabcap, const int32_t* __restrict__ consts, uint64_t wait_ns) {
+  constexpr int kFull = full_rounds(TB, R);
+  __shared__ int64_t s_item;
+  __shared__ int32_t s_seg;
+  const uint32_t tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      const int64_t it = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctrl), 1ull);
+      int sg = 0;
+      if (it < items) {
+        while (sg + 1 < nseg && segs[sg + 1].item0 <= it) ++sg;
+        const PersistSeg& S = segs[sg];
+        if (S.prev >= 0 && S.prev < nseg) {  // this instance's previous pass, all of its tile groups
+          const PersistSeg& Pv = segs[S.prev];
+          const uint32_t* ctr = done + Pv.done_off + ((it - S.item0) >> S.per);
+          const uint32_t need = 1u << Pv.per;
+          const uint64_t t0 = pq_global_ns();
+          while (ld_acquire_gpu(ctr) < need) {
+            if (pq_global_ns() - t0 >= wait_ns) {
+              atomicExch(reinterpret_cast<unsigned long long*>(ctrl) + 1, 1ull);
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+      }
+      s_item = it;
+      s_seg = sg;
+    }
+    __syncthreads();
+    const int64_t it = s_item;
+    if (it >= items) break;
+    const PersistSeg& S = segs[s_seg];
+    const PassDesc pd = S.pd;
+    const uint32_t bid = (uint32_t)(it - S.item0);
+    const int32_t* cc = consts + S.cc_off;
+    const int32_t* lst = lists + S.list_off;
+    const int tl = S.n - TB;
+#define PQ_TILES(NRV, SPV, CTV)                                                                                  \
+  layer_tiles<TB, R, NRV, SPV, CTV, true>(pd, S.n, tl, bid, inst_all, lst, subs, planes_all, tables, states, \
+                                          partials, tabcap, cc, S.mm[0], S.mm[1], S.mm[2], S.mm[3])
+    if (pd.split) PQ_TILES(2, true, true);
+    else if (pd.c == TB && pd.s == TB) PQ_TILES(kFull, false, true);
+    else if (S.nr == 1) PQ_TILES(1, false, false);
+    else if (S.nr == 2) PQ_TILES(2, false, false);
+    else PQ_TILES(3, false, false);
+#undef PQ_TILES
+    // the tile group's stores, then its completion count (release)
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(done + S.done_off + (bid >> S.per), 1u);
+  }
+}
+
+template <int TB, int R>
+static cudaError_t launch_persist_t(int kind, const PersistSeg* segs, int32_t nseg, int64_t items, uint64_t* ctrl,
+                                    uint32_t* done, const InstDev* inst, const int32_t* lists, const SubDev* subs,
+                                    const uint32_t* planes, const float2* tables, float2* states, double* partials,
+                                    int32_t tabcap, const int32_t* consts, uint64_t wait_ns, int num_sms,
+                                    cudaStream_t st) {
+  const size_t smem = layer_pass_smem(kind, tabcap);
+  cudaError_t e = cudaFuncSetAttribute(k_layer_persist<TB, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_layer_persist<TB, R>, 1 << (TB - R), smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t grid = std::min<int64_t>(items, (int64_t)per_sm * std::max(num_sms, 1));
+  k_layer_persist<TB, R><<<(unsigned)grid, 1 << (TB - R), smem, st>>>(segs, nseg, items, ctrl, done, inst, lists, subs,
+                                                                    planes, tables, states, partials, tabcap, consts,
+                                                                    wait_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_persist(int kind, const PersistSeg* segs, int32_t nseg, int64_t items, uint64_t* ctrl,
+                                 uint32_t* done, const InstDev* inst, const int32_t* lists, const SubDev* subs,
+                                 const uint32_t* planes, const float2* tables, float2* states, double* partials,
+                                 int32_t tabcap, const int32_t* consts, uint64_t wait_ns, int num_sms,
+                                 cudaStream_t st) {
+  if (items <= 0) return cudaSuccess;
+  if (kind < 0 || kind >= kTileKinds || nseg < 1) return cudaErrorInvalidValue;
+#define PQ_PERSIST(TBV, RV)                                                                                         \
+  if (kTileShapes[kind].tb == TBV && kTileShapes[kind].r == RV)                                                     \
+    return launch_persist_t<TBV, RV>(kind, segs, nseg, items, ctrl, done, inst, lists, subs, planes, tables, states, \
+                                     partials, tabcap, consts, wait_ns, num_sms, st);
+  PQ_PERSIST(12, 5)
+  PQ_PERSIST(12, 4)
+  PQ_PERSIST(13, 5)
+  PQ_PERSIST(13, 4)
+  PQ_PERSIST(14, 4)
+#undef PQ_PERSIST
   return cudaErrorInvalidValue;
 }
 

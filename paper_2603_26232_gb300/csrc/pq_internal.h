@@ -17,8 +17,8 @@ namespace pq {
 struct TileShape {
   int tb, r;
 };
-constexpr int kTileKinds = 3;
-constexpr TileShape kTileShapes[kTileKinds] = {{12, 5}, {12, 4}, {13, 5}};
+constexpr int kTileKinds = 5;
+constexpr TileShape kTileShapes[kTileKinds] = {{12, 5}, {12, 4}, {13, 5}, {13, 4}, {14, 4}};
 constexpr int kSmemMaxQubits = 14;  // states of <= 14 qubits stay on chip
 constexpr int kTinyMaxQubits = 9;   // n <= 9: one small CTA, plain loops
 constexpr int kMaxPlanes = 16;      // weight bit-planes (weights < 2^16)
@@ -63,6 +63,22 @@ struct PassDesc {
   int32_t tpc_log2; // each CTA processes 2^tpc_log2 tiles of one instance (strided by the CTAs per instance)
 };
 
+// One segment of the persistent layer-pass kernel's work queue: one pass of
+// one size class, its instances' tile groups as consecutive work items.
+struct PersistSeg {
+  PassDesc pd;
+  int32_t n, nr;       // qubits; register rounds of the pass
+  int32_t list_off;    // instances: lists[list_off .. list_off + nlist)
+  int32_t nlist;
+  int32_t per;         // log2 of the tile groups per instance (work items per instance)
+  int32_t prev;        // segment of the same class's previous pass (-1: none)
+  int32_t done_off;    // this segment's per-instance completion counters
+  int32_t pad;
+  int64_t item0;       // first work item of the segment
+  int64_t cc_off;      // cut constants of the pass (int32 offset into the consts array)
+  uint32_t mm[4];      // register slots each round mixes
+};
+
 // Kernel launchers (sim_kernels.cu). All enqueue on `st` and return the
 // launch error (cudaSuccess when queued).
 cudaError_t launch_prep_layers(const InstDev* inst, int32_t count, int32_t p, const double* gamma,
@@ -81,6 +97,20 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
 int64_t cut_consts_elems(int kind, int32_t nlist);
+// Register rounds of a pass and the slots each mixes (as launch_layer_pass uses them).
+int layer_pass_rounds(int kind, const PassDesc& pd);
+void layer_pass_masks(int kind, const PassDesc& pd, uint32_t mm[4]);
+// The persistent form: every pass of every size class of one tile shape in a
+// single launch over a work queue (ctrl[0]: next item, ctrl[1]: error flag;
+// done: per-segment, per-instance completion counters; both zeroed by the
+// caller). A work item waits for its instance's previous pass, at most
+// wait_ns per wait; a wait that gives up sets ctrl[1] and lets the item
+// through. Returns the launch error.
+cudaError_t launch_layer_persist(int kind, const PersistSeg* segs, int32_t nseg, int64_t items, uint64_t* ctrl,
+                                 uint32_t* done, const InstDev* inst, const int32_t* lists, const SubDev* subs,
+                                 const uint32_t* planes, const float2* tables, float2* states, double* partials,
+                                 int32_t tabcap, const int32_t* consts, uint64_t wait_ns, int num_sms,
+                                 cudaStream_t st);
 // `list`: one instance per distinct part, in cc_slot order
 cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev* inst, const int32_t* list,
                               int32_t nlist, const SubDev* subs, const uint32_t* planes,
@@ -90,6 +120,7 @@ cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32
                                  cudaStream_t st);
 cudaError_t launch_cut_table(const SubDev* sub_dev_one, int n, const uint32_t* planes,
                              uint16_t* out, cudaStream_t st);
+cudaError_t launch_flag_or(const uint64_t* src, uint64_t* dst, cudaStream_t st);
 cudaError_t launch_topk_stages(const InstDev* inst, int32_t count, int32_t K, int32_t raw,
                                const int64_t* chunk_off_dev, int64_t total_chunks,
                                const float2* states, uint64_t* scratch, uint32_t* out_z,
@@ -110,6 +141,7 @@ struct MergeDev {
   const int32_t* ew;
 };
 constexpr int kMaxExhaustiveLevels = 64;
+constexpr int64_t kMergeFillThreads = int64_t(1) << 17;  // starting paths that fill the GPU
 constexpr int kBeamSortCap = 8192;
 cudaError_t launch_cand_intra(const SubDev* subs, const uint32_t* planes, const uint32_t* cand,
                               int32_t M, int32_t K, int64_t* intra, cudaStream_t st);

@@ -128,12 +128,24 @@ __device__ __forceinline__ uint32_t lir_o(uint32_t tid, uint32_t k) {
 template <int R, int O>
 __host__ __device__ constexpr int thread_bit_local_o(int b) { return b < O ? b : b + R; }
 
-// Layout offsets of the layer passes. Classic passes mix up to three rounds
-// through layouts O = TB - R, TB - 2R, 0. Split passes (the low qubit group of
-// 2R qubits) mix local bits [R, 2R) and [0, R) in two rounds with a single
-// transpose, loading and storing in O = R.
+// Layout offsets of the layer passes. Classic passes mix up to ceil(TB / R)
+// rounds through layouts O = TB - R, TB - 2R, ..., and finally O = 0 (which
+// overlaps the previous round's bits when R does not divide TB; only the
+// bits below that round's offset mix there). Split passes (the low qubit
+// group of 2R qubits) mix local bits [R, 2R) and [0, R) in two rounds with a
+// single transpose, loading and storing in O = R.
+__host__ __device__ constexpr int full_rounds(int TB, int R) { return (TB + R - 1) / R; }
 __host__ __device__ constexpr int lay_off(int TB, int R, bool split, int rho) {
-  return split ? (rho == 0 ? R : 0) : (rho == 0 ? TB - R : (rho == 1 ? TB - 2 * R : 0));
+  return split ? (rho == 0 ? R : 0) : (rho + 1 < full_rounds(TB, R) ? TB - (rho + 1) * R : 0);
+}
+// Register slots round rho may mix: those whose local bit the rounds before
+// it have not covered (every slot but in the last, overlapping round).
+__host__ __device__ constexpr uint32_t round_slots(int TB, int R, bool split, int rho) {
+  uint32_t m = 0;
+  const int prev = rho == 0 ? TB : lay_off(TB, R, split, rho - 1);
+  for (int j = 0; j < R; ++j)
+    if (split || lay_off(TB, R, split, rho) + j < prev) m |= 1u << j;
+  return m;
 }
 
 __host__ __device__ __forceinline__ int slot_lbr(int TB, int R, int rho, int j) {
@@ -166,7 +178,13 @@ __host__ __device__ constexpr bool warp_local_transpose() {
 static_assert(warp_local_transpose<12, 4, 4, 0>() && warp_local_transpose<12, 5, 2, 0>() &&
                   warp_local_transpose<13, 5, 3, 0>() && warp_local_transpose<12, 5, 5, 0>(),
               "the second transpose of a three-round pass and the split pass's transpose stay in a warp");
+static_assert(warp_local_transpose<13, 4, 5, 1>() && warp_local_transpose<13, 4, 1, 0>() &&
+                  warp_local_transpose<14, 4, 2, 0>() && !warp_local_transpose<14, 4, 6, 2>(),
+              "four-round passes: which transposes stay in a warp");
 static_assert(!warp_local_transpose<12, 4, 8, 4>(), "load/store-layout transposes cross warps");
+static_assert(lay_off(13, 4, false, 2) == 1 && lay_off(13, 4, false, 3) == 0 && round_slots(13, 4, false, 3) == 1u &&
+                  round_slots(12, 5, false, 2) == 3u && round_slots(12, 4, false, 2) == 15u,
+              "round offsets and slot masks");
 
 template <int TB, int R, int OF, int OT>
 __device__ __forceinline__ void transposer_o(float2 (&a)[1 << R], float2* sm, uint32_t tid) {

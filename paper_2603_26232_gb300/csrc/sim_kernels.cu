@@ -396,6 +396,16 @@ cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32
   return cudaGetLastError();
 }
 
+// *dst |= *src (one thread): folds a launch's error word into a sticky one.
+__global__ void k_flag_or(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *src) *dst = 1;
+}
+
+cudaError_t launch_flag_or(const uint64_t* src, uint64_t* dst, cudaStream_t st) {
+  k_flag_or<<<1, 32, 0, st>>>(src, dst);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Cut table (Sec. 2.1) of one subgraph: out[z] = C(z), one thread per z.
 __global__ void k_cut_table(const SubDev* __restrict__ sub, const uint32_t* __restrict__ planes_all,

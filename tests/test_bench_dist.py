@@ -31,7 +31,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_gloo_ranks_reduce_timing_by_maximum():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)

@@ -86,3 +86,23 @@ def test_create_fails_loudly_without_gpu(capi):
         capi.paraqaoa_create(0)
     assert e.value.code in (capi.E_CUDA, capi.E_INVAL)
 
+
+
+def test_pei_efficiency_factor(capi):
+    """Sec. 3.5: EF = 0.5 at T_ALG = T_Base (the paper's worked fact, stored
+    in tests/golden/paper_examples.json), EF -> 1 when the run is far faster
+    than the baseline and -> 0 when far slower, and PEI = AR x EF x 100."""
+    import json
+    import math
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_examples.json")))
+    ef, pei = capi.paraqaoa_pei(0.9, 12.0, 12.0, 1e-3)
+    assert ef == gold["efficiency_factor"]["ef_at_parity"] and pei == pytest.approx(45.0)
+    ef_fast, _ = capi.paraqaoa_pei(1.0, 0.0, 1e5, 1e-3)
+    ef_slow, _ = capi.paraqaoa_pei(1.0, 1e5, 0.0, 1e-3)
+    assert ef_fast > 1 - 1e-12 and ef_slow < 1e-12
+    # alpha 0.001 per second: a run 1000 s faster than the baseline gets 1 / (1 + e^-1)
+    ef, pei = capi.paraqaoa_pei(0.8, 0.0, 1000.0, 1e-3)
+    assert ef == pytest.approx(1 / (1 + math.exp(-1))) and pei == pytest.approx(80 * ef)
+    with pytest.raises(capi.ParaQAOAError):
+        capi.paraqaoa_pei(0.9, -1.0, 1.0, 1e-3)

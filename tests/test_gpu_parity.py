@@ -406,7 +406,8 @@ def test_autotune_choices_keep_parity(api, orc):
         choice = capi.paraqaoa_autotune(ctx, part, 2)
         for n in sizes:
             tb, rb, cm, sp, tp = choice[n]
-            assert (tb, rb) in ((12, 5), (12, 4), (13, 5)) and cm in (2, 3, 4) and sp in (0, 1) and 0 <= tp <= 3
+            assert (tb, rb) in ((12, 5), (12, 4), (13, 5), (13, 4), (14, 4)) and cm in (2, 3, 4) and sp in (0, 1)
+            assert 0 <= tp <= 4
         subs = oracle_parts(orc, g, sizes)
         ids = np.arange(len(sizes), dtype=np.int32)
         gam, bet = synth.random_angles(len(sizes), 2, 99)
@@ -422,7 +423,9 @@ def test_autotune_choices_keep_parity(api, orc):
 
 @pytest.mark.parametrize("tb,rb,split,tpc", [(12, 5, 0, 0), (12, 4, 0, 0), (13, 5, 0, 0), (12, 5, 1, 0), (12, 4, 1, 0),
                                              (13, 5, 1, 0), (12, 4, 0, 3), (12, 4, 1, 2), (12, 5, 0, 2),
-                                             (12, 5, 1, 3), (13, 5, 0, 1), (13, 5, 1, 2)])
+                                             (12, 5, 1, 3), (13, 5, 0, 1), (13, 5, 1, 2), (13, 4, 0, 0),
+                                             (13, 4, 0, 2), (13, 4, 1, 1), (14, 4, 0, 0), (14, 4, 0, 3),
+                                             (14, 4, 1, 0)])
 def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
     """Every tile shape in classic and split schedules, one or several tiles
     per CTA, on parts of 15..24 qubits (two and three qubit groups), depth 3,
@@ -483,7 +486,8 @@ def test_set_schedule_rejects_out_of_range(api):
     tiles per CTA above 2^4, split schedules that do not fit the part."""
     capi, ctx = api
     for args in [(20, 12, 3, 2, 0, 0), (20, 12, 4, 9, 0, 0), (20, 12, 4, 2, 2, 0), (20, 12, 4, 2, 0, 5),
-                 (20, 13, 5, 2, 0, 5), (8, 12, 4, 2, 0, 0), (20, 14, 5, 2, 0, 0)]:
+                 (20, 13, 5, 2, 0, 5), (8, 12, 4, 2, 0, 0), (20, 14, 5, 2, 0, 0), (20, 14, 4, 1, 0, 0),
+                 (20, 13, 4, 0, 0, 0)]:
         with pytest.raises(capi.ParaQAOAError):
             capi.paraqaoa_set_schedule(ctx, *args)
     capi.paraqaoa_set_schedule(ctx, 20, 12, 4, 2, 0, 4)   # the largest walk is accepted
@@ -506,7 +510,9 @@ def test_large_parts_full_size(api, orc):
     oex = [orc.expect_state(s, r) for s, r in zip(subs, refs)]
     rng = np.random.default_rng(5)
     try:
-        for sched in [(12, 5, 2, 1, 2), (13, 5, 2, 0)]:   # the default from 25 qubits, and a classic one
+        # three groups in the split 2^12 x 32 schedule, a classic 2^13 one, and
+        # two groups on the 2^14 x 16 tile (four register rounds in the low group)
+        for sched in [(12, 5, 2, 1, 2), (13, 5, 2, 0), (14, 4, 2, 0, 2)]:
             for n in sizes:
                 capi.paraqaoa_set_schedule(ctx, n, *sched)
             ids = np.arange(2, dtype=np.int32)
@@ -597,5 +603,131 @@ def test_size_classes_on_side_streams_match_serial(api, orc):
         oex = orc.expect_batch(orc.Batch(subs), ids, gam, bet)
         W = np.array([s.total_weight for s in subs], float)
         assert np.all(np.abs(out[0] - oex) / W <= EXP_TOL)
+    finally:
+        capi.paraqaoa_part_free(part)
+
+
+def test_persistent_layer_passes_match_per_pass_launches(api, orc):
+    """The persistent form (every pass of every size class of one tile shape
+    in one launch over a work queue) on uneven parts of 9..24 qubits and two
+    tile shapes: states and <C> bit-identical to the per-pass launches, and
+    within the tolerances of the oracle."""
+    capi, ctx = api
+    sizes = [9, 13, 15, 16, 18, 20, 21, 22, 24, 17]
+    g = chain_graph(sizes, 0.3, 303, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        for n, sc in {15: (12, 5, 2, 1, 1), 16: (12, 4, 2, 0, 2), 17: (12, 4, 2, 0, 0), 18: (12, 4, 3, 1, 1),
+                      20: (12, 4, 2, 0, 3), 21: (13, 4, 2, 0, 2), 22: (13, 4, 2, 0, 1), 24: (13, 4, 2, 0, 0)}.items():
+            capi.paraqaoa_set_schedule(ctx, n, *sc)
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), 3, 304)
+        out = []
+        for persistent in (False, True):
+            capi.paraqaoa_set_persistent(ctx, persistent)
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE)
+            ex = capi.paraqaoa_expect(ctx, len(ids))
+            out.append((ex, [capi.paraqaoa_state(ctx, i, n) for i, n in enumerate(sizes)]))
+            # repeated runs of one plan (the queue and counters are reset per run)
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
+            assert np.array_equal(capi.paraqaoa_expect(ctx, len(ids)), ex)
+        assert np.array_equal(out[0][0], out[1][0])
+        for a, b in zip(out[0][1], out[1][1]):
+            assert np.array_equal(a, b)
+        subs = oracle_parts(orc, g, sizes)
+        for i, s in enumerate(subs):
+            if s.n > 20:
+                continue
+            ref = orc.simulate(s, gam[i], bet[i])
+            assert np.max(np.abs(out[1][1][i] - ref)) <= AMP_TOL, s.n
+            assert abs(out[1][0][i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL, s.n
+    finally:
+        capi.paraqaoa_set_persistent(ctx, False)
+        for n in (15, 16, 17, 18, 20, 21, 22, 24):
+            capi.paraqaoa_set_schedule(ctx, n, 12, 4, 3, 0)
+        capi.paraqaoa_part_free(part)
+
+
+def test_persistent_adam_graph_replay_and_wait_timeout(api):
+    """Adam steps replayed from one captured CUDA graph around the persistent
+    launch give the per-pass launches' angles bit for bit. A wait limit of 0
+    makes every queue wait give up at once: the results call returns
+    PARAQAOA_E_TIMEOUT, and with the limit restored the context computes the
+    earlier results again."""
+    capi, ctx = api
+    g = synth.erdos_renyi(70, 0.3, 71, wmax=10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), 4)
+    try:
+        ids = np.arange(4, dtype=np.int32)
+        g0, b0 = synth.random_angles(4, 2, 72)
+        out = []
+        for persistent in (False, True):
+            capi.paraqaoa_set_persistent(ctx, persistent)
+            out.append(capi.paraqaoa_optimize(ctx, part, ids, 2, g0, b0, 5))
+        for a, b in zip(out[0], out[1]):
+            assert np.array_equal(a, b)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, g0, b0, capi.SIM_EXPECT)
+        ref = capi.paraqaoa_expect(ctx, 4)
+        capi.paraqaoa_set_wait_limit(ctx, 0)
+        try:
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, g0, b0, capi.SIM_EXPECT)
+            with pytest.raises(capi.ParaQAOAError) as e:
+                capi.paraqaoa_expect(ctx, 4)
+            assert e.value.code == capi.E_TIMEOUT
+        finally:
+            capi.paraqaoa_set_wait_limit(ctx, 200_000_000)
+        capi.paraqaoa_simulate_batch(ctx, part, ids, 2, g0, b0, capi.SIM_EXPECT)
+        assert np.array_equal(capi.paraqaoa_expect(ctx, 4), ref)
+    finally:
+        capi.paraqaoa_set_persistent(ctx, False)
+        capi.paraqaoa_part_free(part)
+
+
+def test_merge_fill_matches_paper_worker_split(api, orc):
+    """The exhaustive merge's GPU walk started deeper than L (2^17 starting
+    paths) against exactly K^L walkers and against the oracle's DFS: cut and
+    assignment bit-exact for L = 1..3 on 12 parts (4096 paths), and the
+    starting level each used."""
+    capi, ctx = api
+    g = synth.erdos_renyi(12 * 25 + 1, 0.1, 12, wmax=3)
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, 12)
+    try:
+        first, size, _, _ = capi.paraqaoa_part_info(part)
+        rng = np.random.default_rng(12)
+        cand = np.array([rng.integers(0, 1 << int(s), 2) for s in size], dtype=np.uint32)
+        oside, ocut, leaves = orc.merge_exhaustive(g, first, size, cand, 2, 1)
+        assert leaves == 4096
+        for fill in (1, 0):
+            capi.paraqaoa_set_merge_fill(ctx, fill)
+            for L in (1, 2, 3):
+                side, cut = capi.paraqaoa_merge(ctx, G, part, cand, 2, L, 0)
+                assert cut == ocut and np.array_equal(side, oside), (fill, L)
+                assert capi.paraqaoa_set_merge_fill(ctx, -1) == (12 if fill else L)
+    finally:
+        capi.paraqaoa_set_merge_fill(ctx, 1)
+        capi.paraqaoa_part_free(part)
+
+
+def test_merge_exhaustive_600_vertices_two_candidates(api, orc):
+    """The paper's merge scale (600 vertices, 24 parts, K = 2: 2^24 paths)
+    with a filled GPU walk: the same cut and assignment for L = 1, 2, 3, the
+    cut is CutVal of the assignment, and no beam of width up to 4096 finds a
+    larger cut."""
+    capi, ctx = api
+    g = synth.erdos_renyi(600, 0.1, 0, wmax=1)
+    G = capi.Graph.of(g)
+    part = capi.paraqaoa_partition(G, 24)
+    try:
+        _, size, _, _ = capi.paraqaoa_part_info(part)
+        rng = np.random.default_rng(600)
+        cand = np.array([rng.integers(0, 1 << int(s), 2) for s in size], dtype=np.uint32)
+        res = [capi.paraqaoa_merge(ctx, G, part, cand, 2, L, 0) for L in (1, 2, 3)]
+        for side, cut in res[1:]:
+            assert cut == res[0][1] and np.array_equal(side, res[0][0])
+        assert orc.cutval(g, res[0][0]) == res[0][1]
+        for B in (16, 4096):
+            _, cb = capi.paraqaoa_merge(ctx, G, part, cand, 2, 1, B)
+            assert cb <= res[0][1]
     finally:
         capi.paraqaoa_part_free(part)

@@ -12,7 +12,22 @@ import pytest
 
 from paper_2603_26232_gb300 import _capi as capi
 
-SHAPES = [(12, 5), (12, 4), (13, 5)]
+SHAPES = [(12, 5), (12, 4), (13, 5), (13, 4), (14, 4)]
+
+
+def _lay_off(tb, r, rho):
+    """Register-bit offset of round rho of a classic pass: tb - r, tb - 2r, ...,
+    then 0 for the last of ceil(tb / r) rounds."""
+    full = -(-tb // r)
+    return tb - (rho + 1) * r if rho + 1 < full else 0
+
+
+def _rounds(pd, tb, r):
+    """Register rounds a classic pass needs to reach its lowest mixed local bit."""
+    k, full = 1, -(-tb // r)
+    while k < full and pd["mix_lo"] < _lay_off(tb, r, k - 1):
+        k += 1
+    return k
 
 
 def _tile_qubits(pd, tb):
@@ -43,6 +58,13 @@ def _replay(n, p, tb, r, c_min, split, keep, expect):
         assert pd["split"] == (1 if split and pd["c"] == tb else 0)
         mq = _mixed_qubits(pd, tb, r)
         assert mq
+        if not pd["split"]:
+            # the rounds cover the mixed local bits [mix_lo, tb) and nothing
+            # below; passes over a high group fit in at most three rounds
+            k = _rounds(pd, tb, r)
+            assert _lay_off(tb, r, k - 1) <= pd["mix_lo"] or k == -(-tb // r)
+            if pd["c"] < tb:
+                assert k <= 3, (n, tb, r, pd)
         groups.add(frozenset(mq))
         initialised = initialised or bool(pd["init"])
         assert initialised
@@ -92,6 +114,13 @@ def test_pass_counts_of_the_measured_schedules():
     # n = 24 on the 2^13 tile: 13 + 11 qubits (2 contiguous carried), three passes
     passes, G = _replay(24, 2, 13, 5, 2, 0, 0, 1)
     assert G == 2 and passes[1]["c"] == 2
+    # n = 26 on the 2^14 x 16 tile: 14 + 12 qubits (2 carried): two groups, three passes;
+    # its low group takes four register rounds
+    passes, G = _replay(26, 2, 14, 4, 2, 0, 0, 1)
+    assert G == 2 and len(passes) == 3 and passes[1]["c"] == 2 and _rounds(passes[0], 14, 4) == 4
+    # n = 22 on the 2^13 x 16 tile: 13 + 9 qubits, four carried (128-byte runs)
+    passes, G = _replay(22, 2, 13, 4, 2, 0, 0, 1)
+    assert G == 2 and passes[1]["c"] == 4 and _rounds(passes[1], 13, 4) == 3
 
 
 def test_schedule_rejects_invalid_arguments():

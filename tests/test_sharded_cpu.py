@@ -129,7 +129,7 @@ def _free_port() -> int:
 
 def test_two_gloo_ranks_match_single_process(capi, orc):
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
