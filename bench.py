@@ -284,10 +284,11 @@ def train_large_model(capi, ctx, depth=LARGE_DEPTH, count=2048, epochs=100, seed
     return net, time.perf_counter() - t0, float(losses[-1])
 
 
-def large_learned(capi, pkg):
+def large_learned(capi, pkg, plain: bool = True):
     """16,000-vertex time-to-cut of the learned form (network trained first,
-    outside the clock); the plain form's time on the same workload takes
-    minutes and is measured by --case large."""
+    outside the clock) and, unless plain is False, of the plain form (grid +
+    Adam + INTERP + Adam, about three and a half minutes) on the same GPU,
+    with their cut and time ratios."""
     import torch
     free, _ = torch.cuda.mem_get_info()
     solver = pkg.Solver(device=torch.cuda.current_device(), hbm_budget=int(0.6 * free))
@@ -302,14 +303,27 @@ def large_learned(capi, pkg):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     capi.paraqaoa_mlp_free(net)
+    out = {"workload": f"G({LARGE_N},{LARGE_P_EDGE}) unit weights, seed 0; {LARGE_M} parts of 25-26 qubits; "
+                       f"p={LARGE_DEPTH}; top-{LARGE_K}; beam-{LARGE_BEAM}",
+           "form": "learned angles + judge + plain fallback", "time_to_cut_s": dt, "cut": int(r.cut),
+           "train_s": train_s, "verdicts": {"network": int(np.sum(r.fallback == 0)),
+                                            "plain_fallback": int(np.sum(r.fallback == 1)),
+                                            "reference": int(np.sum(r.fallback == 2))}}
+    if plain:
+        cfg_p = pkg.SolveConfig(M=LARGE_M, K=LARGE_K, p=LARGE_DEPTH, grid_points=GRID, adam_steps=STEPS_ADAM,
+                                beam=LARGE_BEAM)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp = solver.solve(G, cfg_p)
+        torch.cuda.synchronize()
+        dtp = time.perf_counter() - t0
+        out["plain_form"] = {"time_to_cut_s": dtp, "cut": int(rp.cut)}
+        out["cut_ratio_learned_over_plain"] = int(r.cut) / int(rp.cut)
+        out["time_ratio_plain_over_learned"] = dtp / dt
+    else:
+        out["plain_form"] = "skipped (--no-large-plain); bench.py --case large measures it"
     solver.close()
-    return {"workload": f"G({LARGE_N},{LARGE_P_EDGE}) unit weights, seed 0; {LARGE_M} parts of 25-26 qubits; "
-                        f"p={LARGE_DEPTH}; top-{LARGE_K}; beam-{LARGE_BEAM}",
-            "form": "learned angles + judge + plain fallback", "time_to_cut_s": dt, "cut": int(r.cut),
-            "train_s": train_s, "verdicts": {"network": int(np.sum(r.fallback == 0)),
-                                             "plain_fallback": int(np.sum(r.fallback == 1)),
-                                             "reference": int(np.sum(r.fallback == 2))},
-            "plain_form": "measured by bench.py --case large"}
+    return out
 
 
 def batching_measure(capi, ctx, reps: int = 5):
@@ -317,7 +331,8 @@ def batching_measure(capi, ctx, reps: int = 5):
     12..24 vertices (about 120), p = 3, random angles, <C> of every part in one
     simulate call, schedules autotuned; amplitude-layers/s over the wall time
     of simulate + expect, with the size classes on side streams (profiling
-    off) and in order (profiling on), and the 16 B roofline fraction."""
+    off), in order (profiling on), and in the persistent form (one launch per
+    tile shape), and the 16 B roofline fraction."""
     import torch
     g = synth.erdos_renyi(2000, 0.05, 0, wmax=1)
     sizes = synth.uneven_sizes(2000, 12, 24, 1)
@@ -329,8 +344,10 @@ def batching_measure(capi, ctx, reps: int = 5):
     peak, _ = read_peaks()
     out = {"workload": "G(2000,0.05) unit weights, seed 0; uneven parts of 12..24 vertices; p=3",
            "parts": int(len(sizes)), "amplitude_layers": amp_layers}
-    for name, prof in (("side_streams", False), ("serial", True)):
+    for name, prof, persistent in (("side_streams", False, False), ("serial", True, False),
+                                   ("persistent", False, True)):
         capi.paraqaoa_profile_enable(ctx, prof)
+        capi.paraqaoa_set_persistent(ctx, persistent)
         capi.paraqaoa_simulate_batch(ctx, part, ids, 3, gam, bet, capi.SIM_EXPECT)
         capi.paraqaoa_expect(ctx, len(ids))
         torch.cuda.synchronize()
@@ -342,6 +359,7 @@ def batching_measure(capi, ctx, reps: int = 5):
         rate = amp_layers / dt
         out[name] = {"s_per_batch": dt, "amp_layers_per_s": rate, "frac_16B_roofline": rate * 16 / (peak * 1e9)}
     capi.paraqaoa_profile_enable(ctx, False)
+    capi.paraqaoa_set_persistent(ctx, False)
     out["mean_expect"] = float(np.mean(ex))
     capi.paraqaoa_part_free(part)
     return out
@@ -829,7 +847,9 @@ def main():
                                                              "grid batches' two half passes, 2: the Adam batches)")
     ap.add_argument("--sched", default="", help="fixed schedule of the 20-qubit parts instead of the autotuner: "
                                                 "tile_bits,reg_bits,c_min,split[,tiles_per_cta_log2]")
-    ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex learned-form time-to-cut")
+    ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex time-to-cut")
+    ap.add_argument("--no-large-plain", action="store_true",
+                    help="16k-vertex time-to-cut: the learned form only (the plain form takes minutes)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batching configuration and the n = 22 / 26 sweep points of the default line")
     ap.add_argument("--no-autotune", action="store_true",
@@ -976,7 +996,7 @@ def main():
         finally:
             capi.paraqaoa_destroy(xctx)
     if rank == 0 and not args.no_large:
-        large = large_learned(capi, pkg)
+        large = large_learned(capi, pkg, plain=not args.no_large_plain)
     amps_step = amp_layers_per_graph() * len(graphs)
     copies = 1 if sharded else world  # sharded: one workload in all; replicas: one per rank
     value = job_value(amps_step, args.steps, copies, ms)

@@ -209,8 +209,11 @@ int paraqaoa_optimize(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_
                       double *gamma_io, double *beta_io, double *out_value);
 
 /* The plain angle search with its grid size, learning rate and difference
- * step as arguments: the p = 1 grid of points x points
- * (paraqaoa_grid_search), `steps` Adam steps of learning
+ * step as arguments: the p = 1 grid of points x points (as
+ * paraqaoa_grid_search, except that part i's gamma axis is divided by
+ * s_i = max(1, W_i / |E_i|), its mean edge weight: gamma_a = pi a /
+ * (points s_i); the first maximum of <C> in gamma for integer weights lies
+ * near 0.5 / s_i, inside one unscaled grid step), `steps` Adam steps of learning
  * rate lr and central-difference step h (paraqaoa_optimize), then for
  * d = 2..p INTERP (Zhou et al., PRX 10, 021067, 2020) from depth d-1 and
  * `steps` Adam steps at depth d; angles folded as in paraqaoa_solve_plain
@@ -295,7 +298,8 @@ int paraqaoa_features(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_
                       float *out_host);
 
 /* Plain form of the angle search for depth p: the p = 1 grid search
- * (16 x 16 points), `steps` Adam steps (lr 0.02, central differences h =
+ * (16 x 16 points, gamma axis divided by the part's mean edge weight as in
+ * paraqaoa_angle_search), `steps` Adam steps (lr 0.02, central differences h =
  * 1e-3), then for d = 2..p INTERP (Zhou et al., PRX 10, 021067, 2020) from
  * depth d-1 and `steps` Adam steps at depth d. gamma_out / beta_out receive
  * count x p angles folded into the fundamental domain (gamma_0 in [0, pi],

@@ -233,7 +233,8 @@ def merge_beam(g, first, size, cand, K: int, beam: int):
 # ---------------------------------------------------------------- angle search
 # The paper leaves the optimiser open (Sec. 2.2 names gradient descent or
 # evolutionary strategies; Sec. 2.2 also notes initialisation matters). The
-# reading used here: a fixed grid for p = 1, INTERP initialisation for p > 1
+# reading used here: a fixed grid for p = 1 (gamma axis divided by the mean
+# edge weight in the plain form), INTERP initialisation for p > 1
 # (Zhou et al., PRX 10, 021067, 2020), then a fixed number of Adam steps on
 # -<C>/W with central-difference gradients; all scalars FP64.
 
@@ -242,16 +243,27 @@ def grid_points(points: int = 16):
     return np.repeat(np.pi * a / points, points), np.tile((np.pi / 2) * a / points, points)
 
 
-def grid_search(batch: Batch, points: int = 16):
+def grid_scale(s: Subgraph) -> float:
+    """The plain form's gamma-axis divisor of one subgraph: its mean edge
+    weight, at least 1 (1 for an edgeless subgraph)."""
+    return max(1.0, float(np.mean(s.ew))) if len(s.ew) else 1.0
+
+
+def grid_search(batch: Batch, points: int = 16, weight_scaled: bool = False):
     """For every subgraph: <C> at every grid point and the first maximum in
-    row-major (gamma index, beta index) order."""
+    row-major (gamma index, beta index) order. Grid gamma_a = pi a / points,
+    beta_b = (pi/2) b / points; with weight_scaled (the plain form's grid)
+    subgraph i's gamma axis is divided by grid_scale: gamma_a = pi a /
+    (points s_i)."""
     g, b = grid_points(points)
     S = len(batch.subs)
     G = g.size
+    sc = np.array([grid_scale(s) if weight_scaled else 1.0 for s in batch.subs])
+    gam = (g[None, :] / sc[:, None]).reshape(-1)
     sub_idx = np.repeat(np.arange(S, dtype=np.int32), G)
-    vals = expect_batch(batch, sub_idx, np.tile(g, S), np.tile(b, S)).reshape(S, G)
+    vals = expect_batch(batch, sub_idx, gam, np.tile(b, S)).reshape(S, G)
     arg = np.argmax(vals, axis=1)  # numpy argmax returns the first maximum
-    return vals, arg, g[arg], b[arg]
+    return vals, arg, g[arg] / sc, b[arg]
 
 
 def interp(gamma: np.ndarray, beta: np.ndarray):

@@ -7,11 +7,18 @@ using namespace pqh;
 
 extern "C" {
 
-int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids,
-                         int32_t count, int32_t points, double* out_gamma, double* out_beta,
-                         double* out_best, double* out_values) {
+}  // extern "C"
+
+namespace pqh {
+
+// The p = 1 grid of paraqaoa_grid_search; with weight_scaled, part s's gamma
+// axis is divided by s_i = max(1, W_i / |E_i|), its mean edge weight.
+int grid_search_impl(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t points,
+                     bool weight_scaled, double* out_gamma, double* out_beta, double* out_best, double* out_values) {
   if (!c || !pt || !ids || count < 1 || points < 1 || points > 1024 || !out_gamma || !out_beta || !out_best)
     return PARAQAOA_E_INVAL;
+  for (int32_t s = 0; s < count; ++s)
+    if (ids[s] < 0 || ids[s] >= pt->M) return PARAQAOA_E_INVAL;
   PQ_CUDA(cudaSetDevice(c->device));
   int rc = upload_part(c, pt, false);
   if (rc) return rc;
@@ -20,16 +27,22 @@ int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   const int64_t total = (int64_t)count * G;
   if (total > 0x7fffffff) return PARAQAOA_E_INVAL;
   std::vector<int32_t> inst_ids(total);
-  std::vector<double> gam(total), bet(total);
+  std::vector<double> gam(total), bet(total), gsc(count, 1.0);
   const double pi = 3.14159265358979323846;
-  for (int32_t s = 0; s < count; ++s)
+  for (int32_t s = 0; s < count; ++s) {
+    const int32_t id = ids[s];
+    const int64_t ne = pt->eoff[id + 1] - pt->eoff[id];
+    if (weight_scaled && ne > 0) gsc[s] = std::max(1.0, (double)pt->weight[id] / (double)ne);
     for (int32_t k = 0; k < G; ++k) {
-      inst_ids[(int64_t)s * G + k] = ids[s];
-      gam[(int64_t)s * G + k] = pi * (double)(k / points) / (double)points;
+      inst_ids[(int64_t)s * G + k] = id;
+      gam[(int64_t)s * G + k] = pi * (double)(k / points) / ((double)points * gsc[s]);
       bet[(int64_t)s * G + k] = 0.5 * pi * (double)(k % points) / (double)points;
     }
+  }
   PQ_CUDA(c->o_vals.ensure(sizeof(double) * total));
-  PQ_CUDA(c->o_best.ensure(sizeof(double) * 3 * count));
+  PQ_CUDA(c->o_best.ensure(sizeof(double) * 4 * count));
+  PQ_CUDA(cudaMemcpyAsync(c->o_best.as<double>() + 3 * count, gsc.data(), sizeof(double) * count,
+                          cudaMemcpyHostToDevice, c->stream));
   // chunk subgraphs so that each batch passes admission
   int32_t s0 = 0;
   while (s0 < count) {
@@ -52,7 +65,8 @@ int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   double* ob = c->o_best.as<double>();
   {
     ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
-    PQ_CUDA(launch_grid_argmax(c->o_vals.as<double>(), count, points, ob, ob + count, ob + 2 * count, c->stream));
+    PQ_CUDA(launch_grid_argmax(c->o_vals.as<double>(), count, points, ob + 3 * count, ob, ob + count, ob + 2 * count,
+                               c->stream));
   }
   PQ_CUDA(cudaMemcpyAsync(out_gamma, ob, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaMemcpyAsync(out_beta, ob + count, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
@@ -62,6 +76,22 @@ int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   PQ_CUDA(cudaStreamSynchronize(c->stream));
   c->plan.valid = false;
   return c->persistent ? persist_status(c) : PARAQAOA_OK;
+}
+
+}  // namespace pqh
+
+namespace pq {
+int grid_search_weight_scaled(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
+                              int32_t points, double* out_gamma, double* out_beta, double* out_best) {
+  return grid_search_impl(c, pt, ids, count, points, true, out_gamma, out_beta, out_best, nullptr);
+}
+}  // namespace pq
+
+extern "C" {
+
+int paraqaoa_grid_search(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t points,
+                         double* out_gamma, double* out_beta, double* out_best, double* out_values) {
+  return grid_search_impl(c, pt, ids, count, points, false, out_gamma, out_beta, out_best, out_values);
 }
 
 int paraqaoa_optimize(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,

@@ -387,7 +387,7 @@ int paraqaoa_angle_search(paraqaoa_ctx* ctx, const paraqaoa_part* part, const in
       points < 1 || points > 1024 || !(h > 0.0) || !(lr > 0.0))
     return PARAQAOA_E_INVAL;
   std::vector<double> g(count), b(count), best(count), val(count);
-  LQ_RC(paraqaoa_grid_search(ctx, part, ids, count, points, g.data(), b.data(), best.data(), nullptr));
+  LQ_RC(grid_search_weight_scaled(ctx, part, ids, count, points, g.data(), b.data(), best.data()));
   if (steps > 0) LQ_RC(paraqaoa_optimize(ctx, part, ids, count, 1, steps, lr, h, g.data(), b.data(), val.data()));
   else val = best;
   std::vector<double> x, y;

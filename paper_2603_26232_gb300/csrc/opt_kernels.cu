@@ -13,8 +13,8 @@ namespace pq {
 
 // vals[s*G + a*points + b] -> first maximum per subgraph (row-major order).
 __global__ void k_grid_argmax(const double* __restrict__ vals, int32_t S, int32_t points,
-                              double* __restrict__ gamma, double* __restrict__ beta,
-                              double* __restrict__ best) {
+                              const double* __restrict__ gscale, double* __restrict__ gamma,
+                              double* __restrict__ beta, double* __restrict__ best) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   const int G = points * points;
@@ -27,7 +27,7 @@ __global__ void k_grid_argmax(const double* __restrict__ vals, int32_t S, int32_
       arg = k;
     }
   const double pi = 3.14159265358979323846;
-  gamma[s] = pi * (double)(arg / points) / (double)points;
+  gamma[s] = pi * (double)(arg / points) / ((double)points * (gscale ? gscale[s] : 1.0));
   beta[s] = 0.5 * pi * (double)(arg % points) / (double)points;
   best[s] = bv;
 }
@@ -99,9 +99,9 @@ __global__ void k_theta_split(const double* __restrict__ theta, int32_t S, int32
 
 static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_grid_argmax(const double* vals, int32_t S, int32_t points, double* gamma,
+cudaError_t launch_grid_argmax(const double* vals, int32_t S, int32_t points, const double* gscale, double* gamma,
                                double* beta, double* best, cudaStream_t st) {
-  k_grid_argmax<<<nblk(S, 128), 128, 0, st>>>(vals, S, points, gamma, beta, best);
+  k_grid_argmax<<<nblk(S, 128), 128, 0, st>>>(vals, S, points, gscale, gamma, beta, best);
   return cudaGetLastError();
 }
 

@@ -156,7 +156,8 @@ cudaError_t launch_beam_level(const MergeDev& md, int32_t l, int32_t nb, int64_t
                               int32_t* nb_out, cudaStream_t st);
 
 // Angle loop (opt_kernels.cu).
-cudaError_t launch_grid_argmax(const double* vals, int32_t S, int32_t points, double* gamma,
+// gscale (device, S entries, or NULL for 1): part s's grid runs gamma_a = pi a / (points gscale[s])
+cudaError_t launch_grid_argmax(const double* vals, int32_t S, int32_t points, const double* gscale, double* gamma,
                                double* beta, double* best, cudaStream_t st);
 cudaError_t launch_adam_shifts(const double* theta, int32_t S, int32_t p, double h,
                                double* gamma, double* beta, int32_t* step, cudaStream_t st);
@@ -196,6 +197,11 @@ int tc_finish_blocks(int32_t n);
 cudaError_t launch_tc_finish(const InstDev* inst, const int32_t* list, int32_t nlist, int32_t n, const uint16_t* cuts,
                              int64_t cut_stride, float2* states, double* partials, int32_t keep, double* expect,
                              cudaStream_t st);
+
+// The plain angle search's p = 1 grid with each part's gamma axis divided by
+// its mean edge weight (capi_search.cpp).
+int grid_search_weight_scaled(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
+                              int32_t points, double* out_gamma, double* out_beta, double* out_best);
 
 // Context internals the learned-angle entry points share (capi.cpp).
 cudaStream_t ctx_stream(paraqaoa_ctx* c);

@@ -144,13 +144,15 @@ def test_solve_plain_matches_oracle_optimiser(api, orc):
     # another point of the same value)
     vals, arg, _, _ = orc.grid_search(batch)
     assert np.all(np.abs(best0 - vals.max(axis=1)) <= 1e-5 * W)
-    # the oracle's Adam -> INTERP -> Adam from the same grid point. Near an
-    # optimum Adam divides the gradient by its own running magnitude, so the
-    # GPU's FP32 central differences (noise ~1e-4 of W / W per unit angle at
+    # the oracle's plain form: its weight-scaled grid (gamma axis divided by
+    # the mean edge weight), then Adam -> INTERP -> Adam. Near an optimum
+    # Adam divides the gradient by its own running magnitude, so the GPU's
+    # FP32 central differences (noise ~1e-4 of W / W per unit angle at
     # h = 1e-3) make it jitter by up to ~lr = 0.02 in angle; on these small
     # parts that costs up to ~2e-3 W against the oracle's FP64 trajectory
     cfg = orc.AdamConfig(steps=8)
-    g1, b1, _ = orc.adam_optimize(batch, g0[:, None], b0[:, None], cfg)
+    _, _, gs0, bs0 = orc.grid_search(batch, 16, weight_scaled=True)
+    g1, b1, _ = orc.adam_optimize(batch, gs0[:, None], bs0[:, None], cfg)
     g2, b2 = orc.interp(g1, b1)
     g2, b2, f2 = orc.adam_optimize(batch, g2, b2, cfg)
     assert np.all(v >= f2 - 5e-3 * W)

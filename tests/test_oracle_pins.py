@@ -389,6 +389,27 @@ def test_small_case_end_to_end_below_optimum(orc):
 
 
 # ------------------------------------------------------------------ angle search
+def test_weight_scaled_grid_undoes_a_uniform_weight(orc):
+    """C_w = w C_1 for a graph whose edges all weigh w, so exp(-i (gamma / w)
+    C_w) = exp(-i gamma C_1): the plain form's grid (gamma axis divided by the
+    mean edge weight) on the weight-w graph must give, point for point, the
+    unscaled grid's <C> on the unit-weight graph times w, and pick the same
+    grid point; mixed weights get the divisor W / |E|."""
+    g1 = synth.erdos_renyi(9, 0.5, 4)
+    for w in (3, 7):
+        gw = synth.from_edges(g1.n, np.stack([g1.eu, g1.ev], 1), np.full(len(g1.eu), w))
+        v1, a1, ga1, _ = orc.grid_search(orc.Batch([sub_of(g1, orc)]), 8)
+        vw, aw, gaw, _ = orc.grid_search(orc.Batch([sub_of(gw, orc)]), 8, weight_scaled=True)
+        np.testing.assert_allclose(vw, w * v1, rtol=1e-12, atol=1e-12)
+        assert aw[0] == a1[0] and gaw[0] == pytest.approx(ga1[0] / w)
+        # unit weights: the scaled grid is the unscaled one
+        vs, _, _, _ = orc.grid_search(orc.Batch([sub_of(g1, orc)]), 8, weight_scaled=True)
+        np.testing.assert_array_equal(vs, v1)
+    gm = synth.from_edges(3, [(0, 1), (1, 2)], [2, 7])
+    assert orc.grid_scale(sub_of(gm, orc)) == 4.5
+    assert orc.grid_scale(sub_of(synth.from_edges(3, []), orc)) == 1.0
+
+
 def test_interp_and_canonicalize(orc):
     g2, b2 = orc.interp(np.array([[0.6]]), np.array([[-0.3]]))
     assert np.allclose(g2, [[0.6, 0.6]]) and np.allclose(b2, [[-0.3, -0.3]])
