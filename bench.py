@@ -716,6 +716,64 @@ def run_ksweep_case(args):
     print(json.dumps(out), flush=True)
 
 
+def run_halved_case(args):
+    """Halved states (PARAQAOA_SIM_HALVED: z < 2^(n-1) stored, the top qubit's
+    mixer fused into the low-group passes) against full states, on the
+    sweep's batches (sum 2^n >= 2^28 amplitudes, p = 2, <C> only) for n = 20,
+    22, 24, 26 and on one Adam batch of the paper-scale workload (168 x 2^20):
+    amplitude-layers/s counting every one of the 2^n amplitudes (reported
+    apart from the 16 B roofline metric: a halved state moves 8 B per
+    amplitude-layer), the layer passes' streamed bytes per amplitude-layer and
+    their fraction of the measured copy bandwidth, and the largest |d<C>| / W
+    between the two forms."""
+    import torch
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    peak, _ = read_peaks()
+    ctx = capi.paraqaoa_create(0)
+    cases = []
+    for n in (20, 22, 24, 26):
+        count = max(1, (1 << 28) >> n)
+        sizes = [n] * min(count, 64)
+        nv = int(sum(sizes) - (len(sizes) - 1))
+        g = synth.erdos_renyi(nv, 0.3 if n < 24 else 0.2, 7, wmax=10)
+        cases.append((f"{count} x G(*,{0.3 if n < 24 else 0.2}) parts of {n}", g, sizes,
+                      np.resize(np.arange(len(sizes), dtype=np.int32), count), n))
+    g400 = synth.erdos_renyi(NV, 0.1, 0, wmax=WMAX)
+    cases.append(("168 x 2^20: 21 parts of G(400,0.1) x 8 angle sets", g400, None,
+                  np.repeat(np.arange(M, dtype=np.int32), 8), 20))
+    for name, g, sizes, ids, n in cases:
+        part = (capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes) if sizes
+                else capi.paraqaoa_partition(capi.Graph.of(g), M))
+        gam, bet = synth.random_angles(len(ids), 2, 13)
+        W = np.array([max(1, int(w)) for w in capi.paraqaoa_part_info(part)[3][ids]], float)
+        row = {"case": "halved", "workload": name, "qubits": n, "instances": int(len(ids)), "p": 2}
+        res = {}
+        for label, flags in (("full", 0), ("halved", capi.SIM_HALVED)):
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT | flags)
+            capi.paraqaoa_expect(ctx, len(ids))
+            capi.paraqaoa_profile_enable(ctx, True)
+            reps = 3
+            for _ in range(reps):
+                capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet, capi.SIM_EXPECT | flags)
+                ex = capi.paraqaoa_expect(ctx, len(ids))
+            lp = capi.paraqaoa_profile_read(ctx, capi.KCLASS_LAYER_PASS)
+            dev_ms = sum(capi.paraqaoa_profile_read(ctx, k)[1] for k in range(6))
+            capi.paraqaoa_profile_enable(ctx, False)
+            amp_layers = reps * len(ids) * (1 << n) * 2
+            res[label] = ex
+            row[label] = {"amp_layers_per_s": amp_layers / (dev_ms / 1e3),
+                          "layer_pass_bytes_per_amp_layer": lp[2] / amp_layers,
+                          "layer_pass_frac_of_copy": lp[2] / (lp[1] / 1e3) / 1e9 / peak}
+        row["speedup"] = row["halved"]["amp_layers_per_s"] / row["full"]["amp_layers_per_s"]
+        row["max_dC_over_W"] = float(np.max(np.abs(res["halved"] - res["full"]) / W))
+        print(json.dumps(row), flush=True)
+        capi.paraqaoa_part_free(part)
+    capi.paraqaoa_destroy(ctx)
+
+
 def run_learned_case(args):
     """Learned-angle configuration: random subgraphs of 12..20 vertices from
     G(n, P), P in [0.05, 0.5], weights in {1..10} (and the same with unit
@@ -839,7 +897,7 @@ def main():
     ap.add_argument("--sweep-hi", type=int, default=26)
     ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large", "learned", "sweep",
                                                         "batching", "tc", "shapes", "onchip", "merge_levels",
-                                                        "ksweep"],
+                                                        "ksweep", "halved"],
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
     ap.add_argument("--iters", type=int, default=3)
@@ -888,6 +946,8 @@ def main():
         return run_merge_levels_case(args)
     if args.case == "ksweep":
         return run_ksweep_case(args)
+    if args.case == "halved":
+        return run_halved_case(args)
 
     import torch
     import paper_2603_26232_gb300 as pkg

@@ -63,6 +63,7 @@ extern "C" {
 /* simulate_batch flags */
 #define PARAQAOA_SIM_EXPECT 0x1u     /* reduce <C> for every instance (paraqaoa_expect) */
 #define PARAQAOA_SIM_KEEP_STATE 0x2u /* keep the final states (paraqaoa_topk, paraqaoa_state) */
+#define PARAQAOA_SIM_HALVED 0x4u     /* parts of >= 16 qubits keep z < 2^(n-1) only (psi_z = psi_(not z)) */
 
 /* topk flags */
 #define PARAQAOA_TOPK_CANONICAL 0x0u /* rank only z with bit n-1 = 0 (P(z) = P(not z)) */
@@ -143,8 +144,17 @@ int paraqaoa_cut_table(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t id,
  * expectation <C> is reduced (per-thread FP32 sums of a few hundred
  * terms at most, FP64 across threads and tiles); with
  * PARAQAOA_SIM_KEEP_STATE the final states stay on the device for
- * paraqaoa_topk / paraqaoa_state. Results replace those of the previous
- * call. Returns PARAQAOA_E_ADMISSION if the states would exceed the budget. */
+ * paraqaoa_topk / paraqaoa_state. With PARAQAOA_SIM_HALVED, instances of
+ * parts of at least 16 vertices store only the amplitudes of z < 2^(n-1)
+ * (the circuit keeps psi_z = psi_(not z), since |+>^n and both unitaries
+ * commute with the global flip): half the memory and half the HBM traffic
+ * per layer; the mixer of qubit n-1 then pairs each stored z with its
+ * complement over the other n-1 bits and is applied in the passes over the
+ * lowest qubit group (classic schedules; the persistent form is not used).
+ * <C> counts both halves; paraqaoa_topk ranks the canonical half (RAW is
+ * refused) and paraqaoa_state returns the whole state. Results replace those
+ * of the previous call. Returns PARAQAOA_E_ADMISSION if the states would
+ * exceed the budget. */
 int paraqaoa_simulate_batch(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int32_t *ids,
                             int32_t count, int32_t p, const double *gamma, const double *beta,
                             uint32_t flags);

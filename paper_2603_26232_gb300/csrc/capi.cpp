@@ -352,6 +352,7 @@ int paraqaoa_topk(paraqaoa_ctx* c, int32_t count, int32_t K, uint32_t* out_z, fl
   std::vector<int64_t> off(count + 1, 0);
   for (int32_t i = 0; i < count; ++i) {
     const int n = c->plan.inst[i].n;
+    if (raw && c->plan.inst[i].halved) return PARAQAOA_E_INVAL;  // a halved state holds the canonical half only
     const int64_t cnt = raw ? (int64_t(1) << n) : (n == 1 ? 1 : (int64_t(1) << (n - 1)));
     if (K > cnt) return PARAQAOA_E_INVAL;
     off[i + 1] = off[i] + topk_chunks_of(n, raw);
@@ -380,9 +381,17 @@ int paraqaoa_state(paraqaoa_ctx* c, int32_t i, float* out_host) {
   if (i < 0 || i >= c->plan.count) return PARAQAOA_E_INVAL;
   PQ_CUDA(cudaSetDevice(c->device));
   const InstDev& I = c->plan.inst[i];
-  PQ_CUDA(cudaMemcpyAsync(out_host, c->d_states.as<float2>() + I.state_off, sizeof(float2) << I.n,
+  const int nq = I.n - I.halved;
+  PQ_CUDA(cudaMemcpyAsync(out_host, c->d_states.as<float2>() + I.state_off, sizeof(float2) << nq,
                           cudaMemcpyDeviceToHost, c->stream));
   PQ_CUDA(cudaStreamSynchronize(c->stream));
+  if (I.halved) {  // psi_z = psi_(not z): the upper half mirrors the stored one
+    const int64_t full = int64_t(1) << I.n;
+    for (int64_t z = full / 2; z < full; ++z) {
+      out_host[2 * z] = out_host[2 * (full - 1 - z)];
+      out_host[2 * z + 1] = out_host[2 * (full - 1 - z) + 1];
+    }
+  }
   return PARAQAOA_OK;
 }
 

@@ -224,6 +224,7 @@ int plan_run(paraqaoa_ctx* c);
 // Clear / read the sticky error word of the persistent layer passes' bounded
 // waits (PARAQAOA_E_TIMEOUT when one gave up since the last clear).
 int persist_clear(paraqaoa_ctx* c);
+int class_kind(const paraqaoa_ctx* c, int n, bool halved);
 int grid_search_impl(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t points,
                      bool weight_scaled, double* out_gamma, double* out_beta, double* out_best, double* out_values);
 int persist_status(paraqaoa_ctx* c);

@@ -99,6 +99,16 @@ cudaError_t ensure_side_streams(paraqaoa_ctx* c) {
   return cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
 }
 
+// Tile shape of size class n: the context's choice, except that a halved
+// class uses the choice for its n - 1 stored qubits when that shape has a
+// halved low-group pass and leaves at least two tiles, else 2^12 x 16.
+int class_kind(const paraqaoa_ctx* c, int n, bool halved) {
+  if (!halved) return c->tile_kind[n];
+  const int k = c->tile_kind[n - 1];
+  if (layer_mirror_supported(k) && n - 1 - kTileShapes[k].tb >= 1) return k;
+  return 1;
+}
+
 // Build the plan of a batch (validation, admission, memory layout).
 int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count,
                int32_t p, uint32_t flags) {
@@ -110,6 +120,7 @@ int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int
   pl.flags = flags;
   pl.inst.resize(count);
   const bool keep = flags & PARAQAOA_SIM_KEEP_STATE;
+  const bool halve = flags & PARAQAOA_SIM_HALVED;
   std::vector<int32_t> tiny;
   std::map<int, std::vector<int32_t>> smem, hbm;
   for (int32_t i = 0; i < count; ++i) {
@@ -130,13 +141,16 @@ int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int
     I.state_off = -1;
     I.part_off = -1;
     const bool big = n > kSmemMaxQubits;
+    // halved: streaming parts of >= 16 qubits keep z < 2^(n-1) only
+    I.halved = (halve && n > kSmemMaxQubits + 1) ? 1 : 0;
+    const int nq = n - I.halved;
     if (big || keep) {
       I.state_off = pl.state_elems;
-      pl.state_elems += int64_t(1) << n;
+      pl.state_elems += int64_t(1) << nq;
     }
     if (big) {
       I.part_off = pl.partial_elems;
-      pl.partial_elems += int64_t(1) << (n - kTileShapes[c->tile_kind[n]].tb);
+      pl.partial_elems += int64_t(1) << (nq - kTileShapes[class_kind(c, n, I.halved)].tb);
       hbm[n].push_back(i);
     } else if (n >= 10) {
       smem[n].push_back(i);
@@ -230,7 +244,8 @@ int plan_run(paraqaoa_ctx* c) {
   // computed by the first run of the plan and reused by the later ones (Adam
   // steps, replayed graphs, the autotuner's timed runs).
   struct ClassSched {
-    int kind, tb;
+    int kind, tb, nq;  // nq: stored qubits (n - 1 for a halved class)
+    bool halved;
     std::vector<PassDesc> sched;
     std::vector<int> set;  // per pass: index of its cut layout (-1: no cut)
     int nsets = 0;
@@ -241,9 +256,23 @@ int plan_run(paraqaoa_ctx* c) {
   for (auto& kv : pl.hbm) {
     const int n = kv.first;
     ClassSched& q = cs[n];
-    q.kind = c->tile_kind[n];
+    q.halved = pl.inst[pl.lists[kv.second.first]].halved != 0;  // a class is halved or not as a whole
+    q.nq = n - (q.halved ? 1 : 0);
+    q.kind = class_kind(c, n, q.halved);
     q.tb = kTileShapes[q.kind].tb;
-    q.sched = make_schedule(n, p, q.tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[q.kind].r : 0);
+    if (q.halved) {
+      // classic schedule of the n - 1 stored qubits; every pass over the
+      // contiguous low group also applies the top qubit's mixer of each
+      // layer it mixes (each layer mixes the low group exactly once)
+      q.sched = make_schedule(q.nq, p, q.tb, c->c_min[q.nq], keep, want, 0);
+      for (PassDesc& pd : q.sched)
+        if (pd.c == q.tb && pd.s == q.tb) {
+          pd.mirrorA = pd.layerA >= 0;
+          pd.mirrorB = pd.layerB >= 0;
+        }
+    } else {
+      q.sched = make_schedule(n, p, q.tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[q.kind].r : 0);
+    }
     std::vector<std::array<int, 4>> keys;
     for (const PassDesc& pd : q.sched) {
       int k = -1;
@@ -265,7 +294,9 @@ int plan_run(paraqaoa_ctx* c) {
   // pass across the classes. The queue (segment table) is built and uploaded
   // by the plan's first run, outside any stream capture; later runs (Adam
   // steps, replayed graphs) only zero the control blocks and launch.
-  if (c->persistent && !pl.hbm.empty() && !pl.cc_ready) {
+  bool any_halved = false;
+  for (auto& kv : cs) any_halved = any_halved || kv.second.halved;
+  if (c->persistent && !any_halved && !pl.hbm.empty() && !pl.cc_ready) {
     pl.persist.clear();
     std::vector<PersistSeg> segs;
     std::map<int, std::vector<int>> by_kind;
@@ -383,12 +414,13 @@ int plan_run(paraqaoa_ctx* c) {
     const int n = kv.first;
     const ClassSched& q = cs[n];
     const int kind = q.kind, tb = q.tb;
-    const double amps = (double)kv.second.second * (double)(int64_t(1) << n);
+    const double amps = (double)kv.second.second * (double)(int64_t(1) << q.nq);
     const auto reps = pl.hbm_reps[n];
     std::vector<char> done(q.nsets, pl.cc_ready ? 1 : 0);
     for (size_t ip = 0; ip < q.sched.size(); ++ip) {
       PassDesc pd = q.sched[ip];
-      pd.tpc_log2 = std::min<int>(c->tpc_log2[n], n - tb);
+      // a halved class's low-group passes walk tile pairs: one tile bit fewer
+      pd.tpc_log2 = q.halved ? std::min<int>(c->tpc_log2[q.nq], q.nq - tb - 1) : std::min<int>(c->tpc_log2[n], n - tb);
       const int k = q.set[ip];
       int32_t* consts = c->d_consts.as<int32_t>() + q.off + (int64_t)std::max(k, 0) * q.elems;
       if (k >= 0 && !done[k]) {
@@ -398,13 +430,13 @@ int plan_run(paraqaoa_ctx* c) {
       }
       const double bytes = amps * ((pd.init ? 0.0 : 8.0) + (pd.store ? 8.0 : 0.0));
       ProfScope ps(c, PARAQAOA_KCLASS_LAYER_PASS, bytes);
-      PQ_CUDA(launch_layer_pass(kind, n, pd, inst, lists + kv.second.first, kv.second.second, subs,
+      PQ_CUDA(launch_layer_pass(kind, n, q.nq, pd, inst, lists + kv.second.first, kv.second.second, subs,
                                 planes, tables, states, partials, pl.tabcap, consts, st));
     }
     if (want) {
       ProfScope ps(c, PARAQAOA_KCLASS_OTHER, 0);
       PQ_CUDA(launch_expect_reduce(inst, lists + kv.second.first, kv.second.second,
-                                   1 << (n - tb), partials, expect, st));
+                                   1 << (q.nq - tb), partials, expect, st));
     }
   }
   if (fork)

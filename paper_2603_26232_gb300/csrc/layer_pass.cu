@@ -436,7 +436,7 @@ cudaError_t launch_cut_consts(int kind, int n, const PassDesc& pd, const InstDev
 }
 
 template <int TB, int R, int NR, bool SPLIT, bool CONTIG>
-static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const InstDev* inst,
+static cudaError_t launch_layer_t(int kind, int n, int nq, const PassDesc& pd, const InstDev* inst,
                                   const int32_t* list, int32_t nlist, const SubDev* subs,
                                   const uint32_t* planes, const float2* tables, float2* states,
                                   double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
@@ -445,7 +445,7 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
   cudaError_t e = cudaFuncSetAttribute(k_layer_pass<TB, R, NR, SPLIT, CONTIG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int tiles_log2 = n - TB;
+  const int tiles_log2 = nq - TB;
   const int tpc = pd.tpc_log2;
   if (tpc < 0 || tpc > tiles_log2 || tpc > kMaxTpcLog2) return cudaErrorInvalidValue;
   const int64_t blocks = (int64_t)nlist << (tiles_log2 - tpc);
@@ -463,20 +463,27 @@ static cudaError_t launch_layer_t(int kind, int n, const PassDesc& pd, const Ins
   return cudaGetLastError();
 }
 
-cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev* inst,
+static cudaError_t launch_mirror(int kind, int n, int nq, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                                 int32_t nlist, const SubDev* subs, const uint32_t* planes, const float2* tables,
+                                 float2* states, double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
+
+cudaError_t launch_layer_pass(int kind, int n, int nq, const PassDesc& pd, const InstDev* inst,
                               const int32_t* list, int32_t nlist, const SubDev* subs,
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
   if (nlist <= 0) return cudaSuccess;
   if (kind < 0 || kind >= kTileKinds) return cudaErrorInvalidValue;
   const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
-  if (n < tb) return cudaErrorInvalidValue;
+  if (nq < tb || nq > n) return cudaErrorInvalidValue;
+  if (pd.mirrorA || pd.mirrorB)
+    return launch_mirror(kind, n, nq, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts,
+                         st);
   const int nr = pass_rounds(tb, r, pd);
   // split passes always cover the contiguous low group; classic passes over
   // it mix all TB local bits in three rounds
   const bool contig = pd.c == tb && pd.s == tb;
   if (pd.split && !contig) return cudaErrorInvalidValue;
-#define PQ_ARGS kind, n, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st
+#define PQ_ARGS kind, n, nq, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts, st
   // instantiated: split passes; the contiguous low group in all its rounds;
   // other groups in one to three rounds (every high group carries at least
   // two contiguous qubits, and the third round's offset is at most 2)
@@ -501,6 +508,335 @@ cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev
 #undef PQ_LAUNCH
 #undef PQ_ARGS
   return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ halved states
+// A QAOA state keeps psi_z = psi_(not z) (|+>^n and both unitaries commute
+// with the global flip), so a halved state stores only y = z < 2^m, m = n - 1
+// (vertex m on side 0). The mixer of qubits j < m acts on the half as usual;
+// the mixer of qubit m pairs y with its complement y' = (2^m - 1) - y: in the
+// untransformed state (a, b) = (psi_y, psi_y') -> (a + i mu b, b + i mu a), and
+// with the gauge s_y = i^popc(y) psi_y that becomes
+//   s_y  <- s_y  + mu sigma kappa s_y'
+//   s_y' <- s_y' + mu sigma kappa (-1)^m s_y,   kappa = i^(1 - m), sigma = (-1)^popc(y).
+// The cut of the complement is C(y') = C(y | 2^m) = C(y) + Delta(y), Delta(y) =
+// d_m - 2 sum_u w_mu y_u: linear in y's bits, split like lam into a tile part,
+// a thread part and register slots.
+//
+// k_layer_mirror is the low-group pass (contiguous 2^TB tiles, classic
+// rounds) of a halved state: a CTA holds tile t (top tile bit 0) in a[] and
+// its mirror tile t' = t xor (2^(tiles) - 1) in b[], b's slot k of thread tid
+// being the complement of a's slot k in every layout, so the mirror butterfly
+// is register-local; b's butterflies on the other qubits take -mu (the
+// complemented pair swaps roles). Every step of the pass (phase, rounds,
+// transposes, <C>, store) runs on both halves.
+struct MirrorConst {
+  int cf, dfv;   // C(z_F); d_m - 2 sum_{u in F} w_mu z_u
+  int lam[16];   // lam_u per local bit
+  int del[16];   // -2 w_mu per local bit
+  int pad[2];
+};
+static_assert(sizeof(MirrorConst) % 16 == 0, "shared-memory carve-up needs 16-byte multiples");
+
+__host__ __device__ constexpr int mirror_min_blocks(int tb) { return tb >= 13 ? 1 : 2; }
+
+// mirror butterfly of one slot (f = mu sigma, the data a, b of the pair)
+__device__ __forceinline__ void mirror_bfly(float2& a, float2& b, float f, int m) {
+  const float2 kb = rot_i(b, 1 - m), ka = rot_i(a, 1 - m);
+  const float g = (m & 1) ? -f : f;
+  a = make_float2(fmaf(f, kb.x, a.x), fmaf(f, kb.y, a.y));
+  b = make_float2(fmaf(g, ka.x, b.x), fmaf(g, ka.y, b.y));
+}
+
+template <int TB, int R, int X>
+__device__ __forceinline__ void mirror_all(float2 (&a)[1 << R], float2 (&b)[1 << R], float mu, uint32_t zbase,
+                                           uint32_t tid, int m) {
+  const int par = __popc(zbase | lir_o<TB, R, X>(tid, 0)) & 1;
+#pragma unroll
+  for (int k = 0; k < (1 << R); ++k) {
+    const float f = ((par + popc_c(k)) & 1) ? -mu : mu;
+    mirror_bfly(a[k], b[k], f, m);
+  }
+}
+
+template <int TB, int R, int NR>
+__global__ void __launch_bounds__(1 << (TB - R), mirror_min_blocks(TB))
+    k_layer_mirror(PassDesc pd, int32_t n, int32_t tiles_log2, const InstDev* __restrict__ inst_all,
+                   const int32_t* __restrict__ list, const SubDev* __restrict__ subs,
+                   const uint32_t* __restrict__ planes_all, const float2* __restrict__ tables,
+                   float2* __restrict__ states, double* __restrict__ partials, int32_t tabcap,
+                   const int32_t* __restrict__ consts, uint32_t mm0, uint32_t mm1, uint32_t mm2, uint32_t mm3) {
+  constexpr uint32_t NT = 1u << (TB - R);
+  constexpr int KQ = 1 << R;
+  constexpr int O0 = lay_off(TB, R, false, 0), O1 = lay_off(TB, R, false, 1), O2 = lay_off(TB, R, false, 2),
+                O3 = lay_off(TB, R, false, 3);
+  constexpr int OC = lay_off(TB, R, false, NR - 1);
+  static_assert(NR == full_rounds(TB, R), "the low-group pass mixes all its rounds");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* tab = reinterpret_cast<float2*>(smraw);
+  float2* sm = tab + tabcap;
+  int* qk = reinterpret_cast<int*>(sm + padded_r<TB, R>());
+  MirrorConst* tc = reinterpret_cast<MirrorConst*>(qk + 32);
+  uint32_t* pls = reinterpret_cast<uint32_t*>(tc + 1);
+  double* red = reinterpret_cast<double*>(pls + PARAQAOA_MAX_QUBITS * kMaxPlanes);
+  const uint32_t tid = threadIdx.x;
+  const int m = n - 1;  // stored qubits; vertex m is the one left on side 0
+  // work unit: 2^tpc pairs of one instance, strided by the instance's CTA count
+  const uint32_t per = (uint32_t)(tiles_log2 - 1 - pd.tpc_log2);
+  const int li_idx = (int)(blockIdx.x >> per);
+  const uint32_t tj = blockIdx.x & ((1u << per) - 1u);
+  const uint32_t tmask = (1u << tiles_log2) - 1u, lmask = (1u << TB) - 1u;
+  const InstDev* Ip = inst_all + list[li_idx];
+  const int P = Ip->P, W = Ip->W;
+  const uint32_t* pl = planes_all + subs[Ip->sub].plane_off;
+  const bool need_cut = pd.layerP >= 0 || pd.expect;
+  if (pd.layerP >= 0) {
+    const float2* tl = tables + Ip->table_off + (int64_t)pd.layerP * (W + 1);
+    for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
+  }
+  const int32_t* cc_inst = consts + (int64_t)Ip->cc_slot * cut_consts_stride(TB, R);
+  int ccJ = 0, ccB[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) ccB[j] = 0;
+  if (need_cut) {
+    for (int q = tid; q < n * P; q += NT) pls[q] = pl[q];
+    if (tid < (uint32_t)KQ) qk[tid] = cc_inst[tid];
+    ccJ = cc_inst[KQ + tid];
+#pragma unroll
+    for (int j = 0; j < R; ++j) ccB[j] = cc_inst[KQ + (1 + j) * NT + tid];
+  }
+  const uint32_t lt = lir_o<TB, R, O0>(tid, 0);
+  const uint32_t ntiles = 1u << pd.tpc_log2;
+  float acc_cta = 0.f;
+  for (uint32_t tt = 0; tt < ntiles; ++tt) {
+  const uint32_t tile = tj | (tt << per), mtile = tile ^ tmask;
+  const uint32_t zbase = tile << TB;
+  float2* base = states + Ip->state_off + (zbase | lt);
+  float2* mbase = states + Ip->state_off + ((mtile << TB) | (lmask - lt));  // slot k at mbase - (k << O0)
+  float2 a[KQ], b[KQ];
+  if (pd.init) {  // layout OC: s_y = i^popc(y), s_y' = i^(m - popc(y))
+    const int r = __popc(zbase | lir_o<TB, R, OC>(tid, 0));
+    const float2 ba = rot_i(make_float2(1.f, 0.f), r), bb = rot_i(make_float2(1.f, 0.f), m - r);
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+      a[k] = rot_i(ba, popc_c(k));
+      b[k] = rot_i(bb, -popc_c(k));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+      a[k] = base[k << O0];
+      b[k] = mbase[-(int32_t)(k << O0)];
+    }
+  }
+  __syncthreads();  // set-up visible; the previous tile's constants read
+  int A = 0, kap[R], D = 0, dk[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) kap[j] = dk[j] = 0;
+  if (need_cut) {
+    if (tid < 32) {
+      int cfu = 0, dfu = 0;
+      const uint32_t* rv = pls + m * P;  // vertex m's neighbourhood
+      int wv = 0;                        // w_(m, lane)
+      for (int bb = 0; bb < P; ++bb) wv += (int)((rv[bb] >> tid) & 1u) << bb;
+      if ((int)tid < n && ((zbase >> tid) & 1u)) {
+        const uint32_t* row = pls + tid * P;
+        for (int bb = 0; bb < P; ++bb) cfu += __popc(row[bb] & ~zbase) << bb;
+        dfu = wv;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        cfu += __shfl_xor_sync(0xffffffffu, cfu, o);
+        dfu += __shfl_xor_sync(0xffffffffu, dfu, o);
+      }
+      if (tid < (uint32_t)TB) {
+        const uint32_t* row = pls + tid * P;
+        int d = 0, aa = 0;
+        for (int bb = 0; bb < P; ++bb) {
+          d += __popc(row[bb]) << bb;
+          aa += __popc(row[bb] & zbase) << bb;
+        }
+        tc->lam[tid] = d - 2 * aa;
+        tc->del[tid] = -2 * wv;
+      }
+      if (tid == 0) {
+        int dm = 0;
+        for (int bb = 0; bb < P; ++bb) dm += __popc(rv[bb]) << bb;
+        tc->cf = cfu;
+        tc->dfv = dm - 2 * dfu;
+      }
+    }
+    __syncthreads();
+    A = tc->cf + ccJ;
+    D = tc->dfv;
+#pragma unroll
+    for (int bb = 0; bb < TB - R; ++bb)
+      if ((tid >> bb) & 1u) {
+        A += tc->lam[thread_bit_local_o<R, OC>(bb)];
+        D += tc->del[thread_bit_local_o<R, OC>(bb)];
+      }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      kap[j] = tc->lam[OC + j] + ccB[j];
+      dk[j] = tc->del[OC + j];
+    }
+  }
+  constexpr uint32_t kS0 = round_slots(TB, R, false, 0), kS1 = round_slots(TB, R, false, 1),
+                     kS2 = round_slots(TB, R, false, 2), kS3 = round_slots(TB, R, false, 3);
+  if (pd.layerA >= 0) {
+    const float muA = Ip->mu[pd.layerA];
+    mix_regs_sel<R, kS0>(a, muA, mm0);
+    mix_regs_sel<R, kS0>(b, -muA, mm0);
+    if constexpr (NR > 1) {
+      transposer_o<TB, R, O0, O1>(a, sm, tid);
+      transposer_o<TB, R, O0, O1>(b, sm, tid);
+      mix_regs_sel<R, kS1>(a, muA, mm1);
+      mix_regs_sel<R, kS1>(b, -muA, mm1);
+    }
+    if constexpr (NR > 2) {
+      transposer_o<TB, R, O1, O2>(a, sm, tid);
+      transposer_o<TB, R, O1, O2>(b, sm, tid);
+      mix_regs_sel<R, kS2>(a, muA, mm2);
+      mix_regs_sel<R, kS2>(b, -muA, mm2);
+    }
+    if constexpr (NR > 3) {
+      transposer_o<TB, R, O2, O3>(a, sm, tid);
+      transposer_o<TB, R, O2, O3>(b, sm, tid);
+      mix_regs_sel<R, kS3>(a, muA, mm3);
+      mix_regs_sel<R, kS3>(b, -muA, mm3);
+    }
+    if (pd.mirrorA) mirror_all<TB, R, OC>(a, b, muA, zbase, tid, m);
+  }
+  if (pd.layerP >= 0) {
+    int S = A, T = D;
+    a[0] = cmul(a[0], tab[tix(S + qk[0], W)]);
+    b[0] = cmul(b[0], tab[tix(S + qk[0] + T, W)]);
+#pragma unroll
+    for (int i = 1; i < KQ; ++i) {
+      const int k = gray(i), bt = gray_bit(i);
+      S = ((k >> bt) & 1) ? S + kap[bt] : S - kap[bt];
+      T = ((k >> bt) & 1) ? T + dk[bt] : T - dk[bt];
+      a[k] = cmul(a[k], tab[tix(S + qk[k], W)]);
+      b[k] = cmul(b[k], tab[tix(S + qk[k] + T, W)]);
+    }
+  }
+  if (pd.layerB >= 0) {
+    const float muB = Ip->mu[pd.layerB];
+    if constexpr (NR > 3) {
+      mix_regs_sel<R, kS3>(a, muB, mm3);
+      mix_regs_sel<R, kS3>(b, -muB, mm3);
+      transposer_o<TB, R, O3, O2>(a, sm, tid);
+      transposer_o<TB, R, O3, O2>(b, sm, tid);
+    }
+    if constexpr (NR > 2) {
+      mix_regs_sel<R, kS2>(a, muB, mm2);
+      mix_regs_sel<R, kS2>(b, -muB, mm2);
+      transposer_o<TB, R, O2, O1>(a, sm, tid);
+      transposer_o<TB, R, O2, O1>(b, sm, tid);
+    }
+    if constexpr (NR > 1) {
+      mix_regs_sel<R, kS1>(a, muB, mm1);
+      mix_regs_sel<R, kS1>(b, -muB, mm1);
+      transposer_o<TB, R, O1, O0>(a, sm, tid);
+      transposer_o<TB, R, O1, O0>(b, sm, tid);
+    }
+    mix_regs_sel<R, kS0>(a, muB, mm0);
+    mix_regs_sel<R, kS0>(b, -muB, mm0);
+    if (pd.mirrorB) mirror_all<TB, R, O0>(a, b, muB, zbase, tid, m);
+  }
+  if (pd.expect) {
+    float acc = 0.f;
+    int S = A, T = D;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) {
+      const int k = gray(i);
+      if (i > 0) {
+        const int bt = gray_bit(i);
+        S = ((k >> bt) & 1) ? S + kap[bt] : S - kap[bt];
+        T = ((k >> bt) & 1) ? T + dk[bt] : T - dk[bt];
+      }
+      acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)(S + qk[k]), acc);
+      acc = fmaf(fmaf(b[k].x, b[k].x, b[k].y * b[k].y), (float)(S + qk[k] + T), acc);
+    }
+    acc_cta += acc;
+  }
+  if (pd.store) {
+    if (pd.layerB < 0) {
+      if constexpr (NR > 1) {
+        transposer_o<TB, R, OC, O0>(a, sm, tid);
+        transposer_o<TB, R, OC, O0>(b, sm, tid);
+      }
+    }
+    if (pd.last) {  // back from the gauge, times lambda_p
+      const int r = __popc(zbase | lt);
+      const float2 fa = rot_i(Ip->final_scale, -r), fb = rot_i(Ip->final_scale, r - m);
+#pragma unroll
+      for (int k = 0; k < KQ; ++k) {
+        a[k] = cmul(a[k], rot_i(fa, -popc_c(k)));
+        b[k] = cmul(b[k], rot_i(fb, popc_c(k)));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
+      base[k << O0] = a[k];
+      mbase[-(int32_t)(k << O0)] = b[k];
+    }
+  }
+  }  // pairs of this CTA
+  if (pd.expect) {
+    const double sum = block_sum((double)acc_cta, red, tid, NT);
+    if (tid == 0) {  // the sum in the slot of the CTA's first tile, 0 in every other slot it covers
+      for (uint32_t tt = 0; tt < ntiles; ++tt) {
+        const uint32_t tile = tj | (tt << per);
+        partials[Ip->part_off + tile] = tt == 0 ? sum : 0.0;
+        partials[Ip->part_off + (tile ^ tmask)] = 0.0;
+      }
+    }
+  }
+}
+
+bool layer_mirror_supported(int kind) {
+  return kind >= 0 && kind < kTileKinds && kTileShapes[kind].r == 4 && kTileShapes[kind].tb <= 13;
+}
+
+template <int TB, int R>
+static cudaError_t launch_mirror_t(int n, int nq, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                                   int32_t nlist, const SubDev* subs, const uint32_t* planes, const float2* tables,
+                                   float2* states, double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
+  constexpr int kFull = full_rounds(TB, R);
+  const size_t padded = (size_t(1) << TB) + (size_t(1) << (TB - R));
+  const size_t smem = (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(MirrorConst) +
+                      PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_layer_mirror<TB, R, kFull>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tiles_log2 = nq - TB;
+  const int tpc = pd.tpc_log2;
+  // the low group, contiguous, of a halved state of nq = n - 1 qubits, in pairs of tiles
+  if (nq != n - 1 || pd.c != TB || pd.s != TB || pd.split || tiles_log2 < 1 || tpc < 0 || tpc > tiles_log2 - 1 ||
+      tpc > kMaxTpcLog2)
+    return cudaErrorInvalidValue;
+  const int64_t blocks = (int64_t)nlist << (tiles_log2 - 1 - tpc);
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  uint32_t mm[4] = {0, 0, 0, 0};
+  for (int k = 0; k < kFull; ++k)
+    for (int j = 0; j < R; ++j)
+      if (((round_slots(TB, R, false, k) >> j) & 1u) && lay_off(TB, R, false, k) + j >= pd.mix_lo) mm[k] |= 1u << j;
+  k_layer_mirror<TB, R, kFull><<<(unsigned)blocks, 1 << (TB - R), smem, st>>>(
+      pd, n, tiles_log2, inst, list, subs, planes, tables, states, partials, tabcap, consts, mm[0], mm[1], mm[2],
+      mm[3]);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mirror(int kind, int n, int nq, const PassDesc& pd, const InstDev* inst, const int32_t* list,
+                                 int32_t nlist, const SubDev* subs, const uint32_t* planes, const float2* tables,
+                                 float2* states, double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st) {
+  if (!layer_mirror_supported(kind)) return cudaErrorInvalidValue;
+  if (kTileShapes[kind].tb == 12)
+    return launch_mirror_t<12, 4>(n, nq, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap,
+                                  consts, st);
+  return launch_mirror_t<13, 4>(n, nq, pd, inst, list, nlist, subs, planes, tables, states, partials, tabcap, consts,
+                                st);
 }
 
 // ------------------------------------------------------------ persistent form

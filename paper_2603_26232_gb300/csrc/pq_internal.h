@@ -45,6 +45,7 @@ struct InstDev {
   float2 final_scale;        // lambda_p: scalar the last mixer left out
   float final_scale2;        // |lambda_p|^2
   int32_t cc_slot;           // its part's slot in the layer passes' cut-constant arrays
+  int32_t halved;            // the state holds only z < 2^(n-1) (psi_z = psi_(not z)); <C> counts both halves
 };
 
 // One layer pass over every tile of a group of same-size instances.
@@ -61,6 +62,10 @@ struct PassDesc {
   int32_t last;     // the final pass (stores apply lambda_p)
   int32_t split;    // low-group pass of a split schedule: mix local bits [0, 2R) in two rounds
   int32_t tpc_log2; // each CTA processes 2^tpc_log2 tiles of one instance (strided by the CTAs per instance)
+  // halved states (PARAQAOA_SIM_HALVED): this low-group pass also applies the
+  // mixer of the unstored top qubit, after the layerA mixing and/or after the
+  // layerB mixing (k_layer_mirror)
+  int32_t mirrorA, mirrorB;
 };
 
 // One segment of the persistent layer-pass kernel's work queue: one pass of
@@ -92,10 +97,13 @@ cudaError_t launch_smem_sim(int n, const InstDev* inst, const int32_t* list, int
                             int32_t p, const SubDev* subs, const uint32_t* planes,
                             const float2* tables, float2* states, double* expect, int32_t keep,
                             int32_t want_expect, int32_t tabcap, cudaStream_t st);
-cudaError_t launch_layer_pass(int kind, int n, const PassDesc& pd, const InstDev* inst,
+// n: the parts' vertices; nq: the stored qubits (n, or n - 1 for halved states)
+cudaError_t launch_layer_pass(int kind, int n, int nq, const PassDesc& pd, const InstDev* inst,
                               const int32_t* list, int32_t nlist, const SubDev* subs,
                               const uint32_t* planes, const float2* tables, float2* states,
                               double* partials, int32_t tabcap, int32_t* consts, cudaStream_t st);
+// Whether the tile shape has a halved-state (mirror) low-group pass.
+bool layer_mirror_supported(int kind);
 int64_t cut_consts_elems(int kind, int32_t nlist);
 // Register rounds of a pass and the slots each mixes (as launch_layer_pass uses them).
 int layer_pass_rounds(int kind, const PassDesc& pd);

@@ -385,7 +385,8 @@ __global__ void k_expect_reduce(const InstDev* __restrict__ inst_all, const int3
   double acc = 0.0;
   for (int t = threadIdx.x; t < tiles; t += blockDim.x) acc += partials[I.part_off + t];
   double s = block_sum(acc, red, threadIdx.x, blockDim.x);
-  if (threadIdx.x == 0) expect[ii] = s * (double)I.final_scale2;
+  // a halved state holds one of each pair z, not z of equal |psi|^2 and C
+  if (threadIdx.x == 0) expect[ii] = s * (double)I.final_scale2 * (I.halved ? 2.0 : 1.0);
 }
 
 cudaError_t launch_expect_reduce(const InstDev* inst, const int32_t* list, int32_t nlist,

@@ -731,3 +731,84 @@ def test_merge_exhaustive_600_vertices_two_candidates(api, orc):
             assert cb <= res[0][1]
     finally:
         capi.paraqaoa_part_free(part)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_halved_states_match_oracle(api, orc, p):
+    """Halved states (PARAQAOA_SIM_HALVED: parts of >= 16 qubits keep z <
+    2^(n-1), the top qubit's mixer pairs each z with its complement inside
+    the low-group passes): the whole state read back, <C> and the canonical
+    top-16 against the oracle, on parts of 16..22 qubits beside an on-chip
+    part (simulated in full), with the 2^12 x 16 and 2^13 x 16 tiles."""
+    capi, ctx = api
+    sizes = [12, 16, 17, 19, 20, 21, 22]
+    g = chain_graph(sizes, 0.35, 700 + p, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(len(sizes), dtype=np.int32)
+        gam, bet = synth.random_angles(len(sizes), p, 710 + p)
+        for sched in [(12, 4, 2, 0, 1), (13, 4, 2, 0, 0), (12, 4, 3, 0, 3)]:
+            for n in (15, 16, 18, 19, 20, 21):  # halved parts of n vertices use n - 1's schedule
+                capi.paraqaoa_set_schedule(ctx, n, *sched)
+            flags = capi.SIM_EXPECT | capi.SIM_KEEP_STATE | capi.SIM_HALVED
+            capi.paraqaoa_simulate_batch(ctx, part, ids, p, gam, bet, flags)
+            ex = capi.paraqaoa_expect(ctx, len(ids))
+            z, pr = capi.paraqaoa_topk(ctx, len(ids), 16)
+            for i, s in enumerate(subs):
+                ref = orc.simulate(s, gam[i], bet[i])
+                ours = capi.paraqaoa_state(ctx, i, s.n)
+                assert np.max(np.abs(ours - ref)) <= AMP_TOL, (sched, s.n)
+                assert abs(ex[i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL, (sched, s.n)
+                _check_topk(orc, s, ref, z[i], pr[i], 16)
+            with pytest.raises(capi.ParaQAOAError):
+                capi.paraqaoa_topk(ctx, len(ids), 4, capi.TOPK_RAW)
+            # <C> without kept states (the expect-only last pass) agrees
+            capi.paraqaoa_simulate_batch(ctx, part, ids, p, gam, bet, capi.SIM_EXPECT | capi.SIM_HALVED)
+            ex2 = capi.paraqaoa_expect(ctx, len(ids))
+            assert np.all(np.abs(ex2 - ex) <= 1e-9 * np.abs(ex)), sched
+    finally:
+        for n in (15, 16, 18, 19, 20, 21):
+            capi.paraqaoa_set_schedule(ctx, n, 12, 4, 3, 0)
+        capi.paraqaoa_part_free(part)
+
+
+def test_halved_states_extreme_angles_and_full_size(api, orc):
+    """Halved states at beta = +-pi/4 and pi/2 (both mixer factorisations)
+    and a 24-qubit part (three qubit groups), against the oracle; and a
+    26-qubit part against the full-state path (<C> and 4096 sampled
+    amplitudes)."""
+    capi, ctx = api
+    sizes = [16, 18, 24]
+    g = chain_graph(sizes, 0.3, 720, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
+    try:
+        subs = oracle_parts(orc, g, sizes)
+        ids = np.arange(3, dtype=np.int32)
+        for b in [np.pi / 4, -np.pi / 4, np.pi / 2, 0.3]:
+            gam = np.full((3, 2), 0.45)
+            bet = np.full((3, 2), b)
+            capi.paraqaoa_simulate_batch(ctx, part, ids, 2, gam, bet,
+                                         capi.SIM_EXPECT | capi.SIM_KEEP_STATE | capi.SIM_HALVED)
+            ex = capi.paraqaoa_expect(ctx, 3)
+            for i, s in enumerate(subs):
+                ref = orc.simulate(s, gam[i], bet[i])
+                assert np.max(np.abs(capi.paraqaoa_state(ctx, i, s.n) - ref)) <= AMP_TOL, (b, s.n)
+                assert abs(ex[i] - orc.expect_state(s, ref)) / s.total_weight <= EXP_TOL, (b, s.n)
+    finally:
+        capi.paraqaoa_part_free(part)
+    g26 = synth.erdos_renyi(26, 0.2, 726, wmax=10)
+    p26 = capi.paraqaoa_partition(capi.Graph.of(g26), 1)
+    try:
+        ids = np.zeros(1, np.int32)
+        gam, bet = synth.random_angles(1, 2, 727)
+        out = []
+        for flags in (0, capi.SIM_HALVED):
+            capi.paraqaoa_simulate_batch(ctx, p26, ids, 2, gam, bet, capi.SIM_EXPECT | capi.SIM_KEEP_STATE | flags)
+            out.append((capi.paraqaoa_expect(ctx, 1)[0], capi.paraqaoa_state(ctx, 0, 26)))
+        W = float(capi.paraqaoa_part_info(p26)[3][0])
+        assert abs(out[0][0] - out[1][0]) / W <= EXP_TOL
+        idx = np.random.default_rng(26).integers(0, 1 << 26, 4096)
+        assert np.max(np.abs(out[0][1][idx] - out[1][1][idx])) <= AMP_TOL
+    finally:
+        capi.paraqaoa_part_free(p26)
