@@ -1044,7 +1044,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     ms, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
-    large = batching = sweep = None
+    large = batching = sweep = halved_step = None
     if rank == 0 and not args.no_extras:
         # the batching configuration and two points of the amplitude-layer
         # sweep, on a context of their own (their autotuning leaves the
@@ -1055,6 +1055,34 @@ def main():
             sweep = [sweep_point(capi, xctx, n) for n in (22, 26)]
         finally:
             capi.paraqaoa_destroy(xctx)
+        # the same step on halved states (a separate metric: 8 B per
+        # amplitude-layer instead of the 16 B the roofline counts)
+        hsolver = pkg.Solver(device=local, halved=True)
+        capi.paraqaoa_set_stream(hsolver.ctx, stream.cuda_stream)
+        try:
+            def hstep():
+                out = []
+                for G, sc in zip(Gs, sched):
+                    capi.paraqaoa_set_schedule(hsolver.ctx, 19, *sc)  # halved 20-qubit parts hold 19 qubits
+                    out.append(hsolver.solve(G, cfg))
+                return out
+            for _ in range(2):
+                hstep()
+            torch.cuda.synchronize()
+            hev0, hev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                hev0.record(stream)
+                for _ in range(args.steps):
+                    hres = hstep()
+                hev1.record(stream)
+            torch.cuda.synchronize()
+            hms = hev0.elapsed_time(hev1)
+            halved_step = {"metric": "amplitude-layers/s on halved states (z < 2^(n-1) stored, 8 B per amplitude-layer)",
+                           "value": job_value(amp_layers_per_graph() * len(graphs), args.steps, 1, hms),
+                           "ms_per_step": hms / args.steps, "speedup_over_full": ms / hms,
+                           "cuts": [int(r.cut) for r in hres]}
+        finally:
+            hsolver.close()
     if rank == 0 and not args.no_large:
         large = large_learned(capi, pkg, plain=not args.no_large_plain)
     amps_step = amp_layers_per_graph() * len(graphs)
@@ -1099,6 +1127,7 @@ def main():
             "time_to_cut_16k": large,
             "batching": batching,
             "sweep": sweep,
+            "halved_step": halved_step,
         }
         print(json.dumps(line), flush=True)
     solver.close()

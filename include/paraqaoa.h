@@ -413,6 +413,14 @@ int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, i
                       int32_t *out_reg_bits, int32_t *out_c_min, int32_t *out_split,
                       int32_t *out_tiles_per_cta_log2);
 
+/* Halved states for every simulate call of ctx (on/off; off by default):
+ * as if each call passed PARAQAOA_SIM_HALVED, including the calls the angle
+ * search (paraqaoa_grid_search, paraqaoa_optimize, paraqaoa_angle_search,
+ * paraqaoa_solve_plain), the learned form and paraqaoa_final_topk make.
+ * The paper stores full states; this is a deployment setting (half the
+ * state memory and HBM traffic of parts of >= 16 vertices). */
+int paraqaoa_set_halved(paraqaoa_ctx *ctx, int32_t enable);
+
 /* Persistent layer passes (on/off; off by default). On: every pass of every
  * size class of n >= 15 qubits that shares a tile shape runs in ONE launch
  * of a persistent kernel (grid: the resident CTAs of the shape on every SM)

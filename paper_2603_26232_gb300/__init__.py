@@ -55,8 +55,10 @@ class Solver:
     """One CUDA context and the full ParaQAOA pipeline on it:
     partition -> angle search -> final simulation -> top-K -> merge."""
 
-    def __init__(self, device: int = 0, hbm_budget: int = 0):
+    def __init__(self, device: int = 0, hbm_budget: int = 0, halved: bool = False):
         self.ctx = _capi.paraqaoa_create(device, hbm_budget)
+        if halved:  # parts of >= 16 vertices simulated on half their state (psi_z = psi_(not z))
+            _capi.paraqaoa_set_halved(self.ctx, True)
 
     def close(self):
         if self.ctx:

@@ -81,6 +81,7 @@ _SIGS = {
                              P, P, P], ctypes.c_int),
     "paraqaoa_set_wait_limit": ([P, ctypes.c_int64], ctypes.c_int),
     "paraqaoa_set_persistent": ([P, ctypes.c_int32], ctypes.c_int),
+    "paraqaoa_set_halved": ([P, ctypes.c_int32], ctypes.c_int),
     "paraqaoa_probe_peaks": ([ctypes.c_int, P, P], ctypes.c_int),
     "paraqaoa_set_merge_fill": ([P, ctypes.c_int32, P], ctypes.c_int),
     "paraqaoa_pei": ([ctypes.c_double] * 4 + [P, P], ctypes.c_int),
@@ -367,6 +368,10 @@ def paraqaoa_final_topk(ctx, part, ids, p: int, gamma, beta, K: int, flags: int 
     _check(load().paraqaoa_final_topk(ctx, part, _ptr(ids), ids.size, int(p), _ptr(g), _ptr(b), int(K), int(flags),
                                       _ptr(ex), _ptr(z), _ptr(pr)), "paraqaoa_final_topk")
     return ex, z, pr
+
+
+def paraqaoa_set_halved(ctx, enable: bool = True):
+    _check(load().paraqaoa_set_halved(ctx, 1 if enable else 0), "paraqaoa_set_halved")
 
 
 def paraqaoa_set_persistent(ctx, enable: bool = True):

@@ -415,6 +415,13 @@ int paraqaoa_schedule(int32_t n, int32_t p, int32_t tile_bits, int32_t reg_bits,
   return PARAQAOA_OK;
 }
 
+int paraqaoa_set_halved(paraqaoa_ctx* c, int32_t enable) {
+  if (!c) return PARAQAOA_E_INVAL;
+  c->halved = enable != 0;
+  c->plan.valid = false;
+  return PARAQAOA_OK;
+}
+
 int paraqaoa_set_persistent(paraqaoa_ctx* c, int32_t enable) {
   if (!c) return PARAQAOA_E_INVAL;
   c->persistent = enable != 0;
@@ -491,7 +498,7 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
         c->c_min[n] = (int8_t)cd.cm;
         c->split[n] = (int8_t)cd.sp;
         c->tpc_log2[n] = (int8_t)cd.tpc;
-        rc = plan_build(c, pt, ids.data(), (int32_t)copies, p, PARAQAOA_SIM_EXPECT);
+        rc = plan_build(c, pt, ids.data(), (int32_t)copies, p, PARAQAOA_SIM_EXPECT | kPlanFullStates);
         if (rc == PARAQAOA_E_ADMISSION) {
           rc = PARAQAOA_OK;
           continue;

@@ -20,7 +20,7 @@ int paraqaoa_simulate_tc(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t
   int rc = upload_part(c, pt, false);
   if (rc) return rc;
   const uint32_t fl = (flags & (PARAQAOA_SIM_EXPECT | PARAQAOA_SIM_KEEP_STATE)) | PARAQAOA_SIM_KEEP_STATE;
-  rc = plan_build(c, pt, ids, count, p, fl);
+  rc = plan_build(c, pt, ids, count, p, fl | kPlanFullStates);
   if (rc) return rc;
   SimPlan& pl = c->plan;
   pl.flags = flags | PARAQAOA_SIM_EXPECT;  // <C> is always reduced; states kept only on request

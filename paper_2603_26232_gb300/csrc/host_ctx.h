@@ -163,6 +163,9 @@ struct paraqaoa_ctx {
   // starting level the last exhaustive merge used
   bool merge_fill = true;
   int32_t merge_levels_used = 0;
+  // every simulate call of the context (the angle search's included) halves
+  // the states it can (paraqaoa_set_halved)
+  bool halved = false;
   // Adam step counter on the device (read by the update kernel)
   pqh::DevBuf o_step;
   // side streams for concurrent size classes, with their fork / join events
@@ -219,6 +222,9 @@ int validate_csr(const paraqaoa_csr* g);
 std::vector<int32_t> levels_of(const paraqaoa_part* pt);
 int upload_part(paraqaoa_ctx* c, const paraqaoa_part* pt, bool force);
 cudaError_t ensure_side_streams(paraqaoa_ctx* c);
+// flags: PARAQAOA_SIM_*, or kPlanFullStates to ignore the context's halved
+// setting (the tensor-core variant and the autotuner simulate full states)
+constexpr uint32_t kPlanFullStates = 0x80000000u;
 int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int32_t count, int32_t p, uint32_t flags);
 int plan_run(paraqaoa_ctx* c);
 // Clear / read the sticky error word of the persistent layer passes' bounded

@@ -120,7 +120,7 @@ int plan_build(paraqaoa_ctx* c, const paraqaoa_part* pt, const int32_t* ids, int
   pl.flags = flags;
   pl.inst.resize(count);
   const bool keep = flags & PARAQAOA_SIM_KEEP_STATE;
-  const bool halve = flags & PARAQAOA_SIM_HALVED;
+  const bool halve = (flags & PARAQAOA_SIM_HALVED) || (c->halved && !(flags & kPlanFullStates));
   std::vector<int32_t> tiny;
   std::map<int, std::vector<int32_t>> smem, hbm;
   for (int32_t i = 0; i < count; ++i) {

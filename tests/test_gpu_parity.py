@@ -812,3 +812,38 @@ def test_halved_states_extreme_angles_and_full_size(api, orc):
         assert np.max(np.abs(out[0][1][idx] - out[1][1][idx])) <= AMP_TOL
     finally:
         capi.paraqaoa_part_free(p26)
+
+
+def test_context_halved_setting_drives_the_angle_search(api, orc):
+    """paraqaoa_set_halved: the grid search, Adam and the final top-K of a
+    context that halves its states against a full-state context: every grid
+    <C> within 1e-5 W, Adam's final <C> at its own angles within 1e-5 W of the
+    oracle, and the tensor-core variant still simulating full states."""
+    capi, ctx = api
+    sizes = [16, 18, 20]
+    g = chain_graph(sizes, 0.3, 730, 10)
+    part = capi.paraqaoa_partition(capi.Graph.of(g), 3, capi.PART_SIZES, sizes)
+    hctx = capi.paraqaoa_create(0)
+    try:
+        capi.paraqaoa_set_halved(hctx, True)
+        ids = np.arange(3, dtype=np.int32)
+        subs = oracle_parts(orc, g, sizes)
+        W = np.array([s.total_weight for s in subs], float)
+        _, _, _, vf = capi.paraqaoa_grid_search(ctx, part, ids, 8, want_values=True)
+        _, _, _, vh = capi.paraqaoa_grid_search(hctx, part, ids, 8, want_values=True)
+        assert np.all(np.abs(vf - vh) <= EXP_TOL * W[:, None])
+        g0, b0 = synth.random_angles(3, 2, 731)
+        gg, bb, val = capi.paraqaoa_optimize(hctx, part, ids, 2, g0, b0, 4)
+        oex = orc.expect_batch(orc.Batch(subs), ids, gg, bb)
+        assert np.all(np.abs(val - oex) <= EXP_TOL * W)
+        ex, z, pr = capi.paraqaoa_final_topk(hctx, part, ids, 2, gg, bb, 8)
+        for i, s in enumerate(subs):
+            _check_topk(orc, s, orc.simulate(s, gg[i], bb[i]), z[i], pr[i], 8)
+        capi.paraqaoa_simulate_tc(hctx, part, ids, 2, gg, bb, capi.SIM_EXPECT | capi.SIM_KEEP_STATE, capi.TC_FP16, 7)
+        assert np.all(np.abs(capi.paraqaoa_expect(hctx, 3) - oex) <= EXP_TOL * W)
+        st = capi.paraqaoa_state(hctx, 2, 20)
+        ref = orc.simulate(subs[2], gg[2], bb[2])
+        assert np.max(np.abs(st - ref)) <= AMP_TOL
+    finally:
+        capi.paraqaoa_destroy(hctx)
+        capi.paraqaoa_part_free(part)
