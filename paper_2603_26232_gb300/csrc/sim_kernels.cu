@@ -259,8 +259,18 @@ cudaError_t launch_tiny_sim(const InstDev* inst, const int32_t* list, int32_t nl
 // 10 <= n <= 14: the whole state of one instance lives in one CTA (registers
 // plus a shared-memory transpose buffer); all p layers, <C> and the optional
 // state write happen without touching HBM in between.
+// Resident CTAs per SM the on-chip kernel is compiled for (registers capped
+// at 65536 / (threads x CTAs)): two CTAs of 256 threads at 13 qubits and four
+// of 128 at 12 (both at 128 registers, a few bytes of spills; uncapped they
+// took 162 and 161 registers, one and three CTAs), four of 64 at 11 (a
+// tighter cap spills 256 B), eight of 32 at 10; 14 qubits fill one SM's
+// shared memory.
+__host__ __device__ constexpr int smem_sim_min_blocks(int tb) {
+  return tb >= 14 ? 1 : (tb == 13 ? 2 : (tb == 10 ? 8 : 4));
+}
+
 template <int TB>
-__global__ void __launch_bounds__(1 << (TB - 5))
+__global__ void __launch_bounds__(1 << (TB - 5), smem_sim_min_blocks(TB))
     k_smem_sim(const InstDev* __restrict__ inst_all, const int32_t* __restrict__ list, int32_t p,
                const SubDev* __restrict__ subs, const uint32_t* __restrict__ planes_all,
                const float2* __restrict__ tables, float2* __restrict__ states,
