@@ -186,6 +186,15 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   const uint32_t ntiles = 1u << pd.tpc_log2;
   const bool tile_barrier_covered =
       !SPLIT && NR >= 2 && !warp_local_transpose<TB, R, O0, O1>() && (pd.layerA >= 0 || pd.layerB >= 0);
+  // Transposes leave out the barrier after their reads (each chains from the
+  // layout the one before it read). Across tiles the chain holds when the
+  // pass starts in the layout it ends in (O0 when it mixes first, else the
+  // cut layout OC); otherwise a CTA barrier of the next tile's set-up must
+  // come between, the tile-constant barrier (cut needed) or the first
+  // barrier (not covered), else one is taken at the end of the tile.
+  const bool tr_a = pd.layerA >= 0, tr_b = pd.layerB >= 0, tr_s = pd.store && !tr_b;
+  const bool trail_tile = NR > 1 && (tr_a || tr_b || tr_s) && (tr_a ? O0 : OC) != ((tr_b || tr_s) ? O0 : OC) &&
+                          !need_cut && tile_barrier_covered;
   // this thread's <C> terms over the CTA's tiles, summed in FP32 in two
   // levels (2^R positive terms per tile, then at most 2^kMaxTpcLog2 tile
   // sums: relative error below 48 x 2^-24, about 3e-6), FP64 from the block
@@ -262,15 +271,15 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
     const float muA = Ip->mu[pd.layerA];
     mix_regs_sel<R, kS0>(a, muA, mm0);
     if constexpr (NR > 1) {
-      transposer_o<TB, R, O0, O1>(a, sm, tid);
+      transposer_o<TB, R, O0, O1, false>(a, sm, tid);
       mix_regs_sel<R, kS1>(a, muA, mm1);
     }
     if constexpr (NR > 2) {
-      transposer_o<TB, R, O1, O2>(a, sm, tid);
+      transposer_o<TB, R, O1, O2, false>(a, sm, tid);
       mix_regs_sel<R, kS2>(a, muA, mm2);
     }
     if constexpr (NR > 3) {
-      transposer_o<TB, R, O2, O3>(a, sm, tid);
+      transposer_o<TB, R, O2, O3, false>(a, sm, tid);
       mix_regs_sel<R, kS3>(a, muA, mm3);
     }
   }
@@ -288,15 +297,15 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
     const float muB = Ip->mu[pd.layerB];
     if constexpr (NR > 3) {
       mix_regs_sel<R, kS3>(a, muB, mm3);
-      transposer_o<TB, R, O3, O2>(a, sm, tid);
+      transposer_o<TB, R, O3, O2, false>(a, sm, tid);
     }
     if constexpr (NR > 2) {
       mix_regs_sel<R, kS2>(a, muB, mm2);
-      transposer_o<TB, R, O2, O1>(a, sm, tid);
+      transposer_o<TB, R, O2, O1, false>(a, sm, tid);
     }
     if constexpr (NR > 1) {
       mix_regs_sel<R, kS1>(a, muB, mm1);
-      transposer_o<TB, R, O1, O0>(a, sm, tid);
+      transposer_o<TB, R, O1, O0, false>(a, sm, tid);
     }
     mix_regs_sel<R, kS0>(a, muB, mm0);
   }
@@ -316,7 +325,7 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   }
   if (pd.store) {
     if (pd.layerB < 0) {  // a pass without a second mixer ends in the cut layout
-      if constexpr (NR > 1) transposer_o<TB, R, OC, O0>(a, sm, tid);
+      if constexpr (NR > 1) transposer_o<TB, R, OC, O0, false>(a, sm, tid);
     }
     if (pd.last) {  // back from the gauge, times lambda_p
       const float2 fs = rot_i(Ip->final_scale, -__popc(zbase | zmap(lt)));
@@ -335,6 +344,7 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
       base[off] = a[k];
     }
   }
+  if (trail_tile) __syncthreads();
   }  // tiles of this CTA
   // One block reduction per CTA (the FP64 pipe is narrow and the reduction
   // serialises the CTA): the sum goes to the partial slot of the CTA's first

@@ -152,7 +152,10 @@ __host__ __device__ __forceinline__ int slot_lbr(int TB, int R, int rho, int j) 
   return rho == 0 ? TB - R + j : (rho == 1 ? TB - 2 * R + j : j);
 }
 
-template <int TB, int R, int FROM, int TO>
+// Transpose from layout FROM to TO through shared memory; TRAIL as for
+// transposer_o below (the barrier after the reads, which a caller whose next
+// buffer write is a transpose from TO does not need).
+template <int TB, int R, int FROM, int TO, bool TRAIL = true>
 __device__ __forceinline__ void transposer(float2 (&a)[1 << R], float2* sm, uint32_t tid) {
   float2* pf = sm + padr<R>(lir<TB, R, FROM>(tid, 0));
   float2* pt = sm + padr<R>(lir<TB, R, TO>(tid, 0));
@@ -161,7 +164,7 @@ __device__ __forceinline__ void transposer(float2 (&a)[1 << R], float2* sm, uint
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < (1 << R); ++k) a[k] = pt[padr<R>(lir<TB, R, TO>(0, k))];
-  __syncthreads();
+  if constexpr (TRAIL) __syncthreads();
 }
 
 // True when layouts OF and OT put the same local bits in the warp index
@@ -186,7 +189,14 @@ static_assert(lay_off(13, 4, false, 2) == 1 && lay_off(13, 4, false, 3) == 0 && 
                   round_slots(12, 5, false, 2) == 3u && round_slots(12, 4, false, 2) == 15u,
               "round offsets and slot masks");
 
-template <int TB, int R, int OF, int OT>
+// Transpose from layout OF to OT through shared memory. TRAIL = false leaves
+// out the barrier after the reads. That is safe when the next write to the
+// buffer is a transpose from OT: each thread then writes exactly the slots it
+// has just read (padr is additive, so a thread's slots in a layout are
+// padr(lir_o(tid, k)) whichever transpose addresses them), and the other
+// threads read only their own slots. Any other next write needs a barrier
+// of the caller's in between.
+template <int TB, int R, int OF, int OT, bool TRAIL = true>
 __device__ __forceinline__ void transposer_o(float2 (&a)[1 << R], float2* sm, uint32_t tid) {
   constexpr bool kWarp = warp_local_transpose<TB, R, OF, OT>();
   float2* pf = sm + padr<R>(lir_o<TB, R, OF>(tid, 0));
@@ -196,7 +206,9 @@ __device__ __forceinline__ void transposer_o(float2 (&a)[1 << R], float2* sm, ui
   if constexpr (kWarp) __syncwarp(); else __syncthreads();
 #pragma unroll
   for (int k = 0; k < (1 << R); ++k) a[k] = pt[padr<R>(lir_o<TB, R, OT>(0, k))];
-  if constexpr (kWarp) __syncwarp(); else __syncthreads();
+  if constexpr (TRAIL) {
+    if constexpr (kWarp) __syncwarp(); else __syncthreads();
+  }
 }
 
 template <int R>

@@ -24,9 +24,13 @@ __device__ __forceinline__ uint32_t li0_rt(int rho, uint32_t tid) {
   return li_of<TB, 2>(tid, 0);
 }
 __host__ __device__ __forceinline__ int slot_lb(int TB, int rho, int j) { return slot_lbr(TB, 5, rho, j); }
+// Every transpose of the on-chip kernel starts from the layout the one before
+// it ended in (goto_layout tracks it), and the only other shared-memory
+// writes (the next layer's phase table, the <C> reduction) sit behind
+// barriers of their own, so the barrier after a transpose's reads is left out.
 template <int TB, int FROM, int TO>
 __device__ __forceinline__ void transpose(float2 (&a)[32], float2* sm, uint32_t tid) {
-  transposer<TB, 5, FROM, TO>(a, sm, tid);
+  transposer<TB, 5, FROM, TO, false>(a, sm, tid);
 }
 
 template <int TB>
@@ -322,7 +326,10 @@ __global__ void __launch_bounds__(1 << (TB - 5), smem_sim_min_blocks(TB))
         mix_regs(a, mu, r == 2 ? mask2 : 31u);
       }
     }
-    __syncthreads();  // before the next table load overwrites tab
+    // The next layer's table load may overwrite tab now: every layer takes at
+    // least one transpose after its phase, whose barrier all threads reach
+    // only after their last read of the table.
+    static_assert(NR >= 2, "a transpose per layer orders the table reads before the next load");
   }
   if (want_expect) {
     ThreadCut t = thread_cut(li0_rt<TB>(cur, tid), *lc, cur, pl, n, P);
