@@ -134,7 +134,8 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   float2* tab = reinterpret_cast<float2*>(smraw);
   float2* sm = tab + tabcap;
   int* qk = reinterpret_cast<int*>(sm + padded_r<TB, R>());  // 2^R entries (<= 32)
-  TileConst* tc = reinterpret_cast<TileConst*>(qk + 32);
+  int* qk8 = qk + 32;  // the same in bytes of the phase table (x sizeof(float2))
+  TileConst* tc = reinterpret_cast<TileConst*>(qk + 64);
   uint32_t* pls = reinterpret_cast<uint32_t*>(tc + 1);  // the instance's bit-planes
   double* red = reinterpret_cast<double*>(pls + PARAQAOA_MAX_QUBITS * kMaxPlanes);
   const uint32_t tid = threadIdx.x;
@@ -167,7 +168,11 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   for (int j = 0; j < R; ++j) ccB[j] = 0;
   if (need_cut) {
     for (int q = tid; q < n * P; q += NT) pls[q] = pl[q];
-    if (tid < (uint32_t)KQ) qk[tid] = cc_inst[tid];
+    if (tid < (uint32_t)KQ) {
+      const int q = cc_inst[tid];
+      qk[tid] = q;
+      qk8[tid] = q * (int)sizeof(float2);
+    }
     ccJ = cc_inst[KQ + tid];
 #pragma unroll
     for (int j = 0; j < R; ++j) ccB[j] = cc_inst[KQ + (1 + j) * NT + tid];
@@ -200,6 +205,14 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   // sums: relative error below 48 x 2^-24, about 3e-6), FP64 from the block
   // reduction on
   float acc_cta = 0.f;
+  // the last round of a classic pass overlaps the one before it when R does
+  // not divide TB: only its slots below the previous offset ever mix
+  constexpr uint32_t kS0 = round_slots(TB, R, SPLIT, 0), kS1 = round_slots(TB, R, SPLIT, 1),
+                     kS2 = round_slots(TB, R, SPLIT, 2), kS3 = round_slots(TB, R, SPLIT, 3);
+  // every slot a round may mix does (the pass's qubit group covers them all):
+  // one broadcast multiplier per round instead of a select per slot
+  const bool full_mix = (mm0 & kS0) == kS0 && (NR < 2 || (mm1 & kS1) == kS1) && (NR < 3 || (mm2 & kS2) == kS2) &&
+                        (NR < 4 || (mm3 & kS3) == kS3);
   for (uint32_t tt = 0; tt < ntiles; ++tt) {
   const uint32_t tile = tj | (tt << per);
   const uint32_t zbase = ((tile & ((1u << lowt) - 1u)) << c) | ((tile >> lowt) << (s + g));
@@ -263,64 +276,72 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
 #pragma unroll
     for (int j = 0; j < R; ++j) kap[j] = tc->lam[OC + j] + ccB[j];
   }
-  // the last round of a classic pass overlaps the one before it when R does
-  // not divide TB: only its slots below the previous offset ever mix
-  constexpr uint32_t kS0 = round_slots(TB, R, SPLIT, 0), kS1 = round_slots(TB, R, SPLIT, 1),
-                     kS2 = round_slots(TB, R, SPLIT, 2), kS3 = round_slots(TB, R, SPLIT, 3);
   if (pd.layerA >= 0) {
     const float muA = Ip->mu[pd.layerA];
-    mix_regs_sel<R, kS0>(a, muA, mm0);
+    mix_round<R, kS0>(a, muA, mm0, full_mix);
     if constexpr (NR > 1) {
       transposer_o<TB, R, O0, O1, false>(a, sm, tid);
-      mix_regs_sel<R, kS1>(a, muA, mm1);
+      mix_round<R, kS1>(a, muA, mm1, full_mix);
     }
     if constexpr (NR > 2) {
       transposer_o<TB, R, O1, O2, false>(a, sm, tid);
-      mix_regs_sel<R, kS2>(a, muA, mm2);
+      mix_round<R, kS2>(a, muA, mm2, full_mix);
     }
     if constexpr (NR > 3) {
       transposer_o<TB, R, O2, O3, false>(a, sm, tid);
-      mix_regs_sel<R, kS3>(a, muA, mm3);
+      mix_round<R, kS3>(a, muA, mm3, full_mix);
     }
   }
   if (pd.layerP >= 0) {
-    int S = A;
-    a[0] = cmul(a[0], tab[tix(S + qk[0], W)]);
+    // cut values walked in bytes of the table: index, clamp, load
+    const unsigned char* tb8 = reinterpret_cast<const unsigned char*>(tab);
+    const uint32_t W8 = (uint32_t)W * (uint32_t)sizeof(float2);
+    int S = A * (int)sizeof(float2);
+    a[0] = cmul(a[0], *reinterpret_cast<const float2*>(tb8 + min((uint32_t)(S + qk8[0]), W8)));
 #pragma unroll
     for (int i = 1; i < KQ; ++i) {
       const int k = gray(i), b = gray_bit(i);
-      S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
-      a[k] = cmul(a[k], tab[tix(S + qk[k], W)]);
+      const int k8 = kap[b] * (int)sizeof(float2);
+      S = ((k >> b) & 1) ? S + k8 : S - k8;
+      a[k] = cmul(a[k], *reinterpret_cast<const float2*>(tb8 + min((uint32_t)(S + qk8[k]), W8)));
     }
   }
   if (pd.layerB >= 0) {
     const float muB = Ip->mu[pd.layerB];
     if constexpr (NR > 3) {
-      mix_regs_sel<R, kS3>(a, muB, mm3);
+      mix_round<R, kS3>(a, muB, mm3, full_mix);
       transposer_o<TB, R, O3, O2, false>(a, sm, tid);
     }
     if constexpr (NR > 2) {
-      mix_regs_sel<R, kS2>(a, muB, mm2);
+      mix_round<R, kS2>(a, muB, mm2, full_mix);
       transposer_o<TB, R, O2, O1, false>(a, sm, tid);
     }
     if constexpr (NR > 1) {
-      mix_regs_sel<R, kS1>(a, muB, mm1);
+      mix_round<R, kS1>(a, muB, mm1, full_mix);
       transposer_o<TB, R, O1, O0, false>(a, sm, tid);
     }
-    mix_regs_sel<R, kS0>(a, muB, mm0);
+    mix_round<R, kS0>(a, muB, mm0, full_mix);
   }
   if (pd.expect) {
-    float acc = 0.f;
-    int S = A;
+    // sum_k |a_k|^2 C_k with C_k = A + sum_{j in k} kap_j + qk[k], and qk
+    // (-2 Q_K) a sum over the pairs of set register bits, qk[{j, l}] each:
+    // after superset sums nk[m] = sum over k containing m of |a_k|^2 it is
+    // A nk[0] + sum_j kap_j nk[{j}] + sum_{j<l} qk[{j,l}] nk[{j,l}].
+    float nk[KQ];
 #pragma unroll
-    for (int i = 0; i < KQ; ++i) {
-      const int k = gray(i);
-      if (i > 0) {
-        const int b = gray_bit(i);
-        S = ((k >> b) & 1) ? S + kap[b] : S - kap[b];
-      }
-      acc = fmaf(fmaf(a[k].x, a[k].x, a[k].y * a[k].y), (float)(S + qk[k]), acc);
-    }
+    for (int k = 0; k < KQ; ++k) nk[k] = fmaf(a[k].x, a[k].x, a[k].y * a[k].y);
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+      for (int k = 0; k < KQ; ++k)
+        if (!((k >> j) & 1)) nk[k] += nk[k | (1 << j)];
+    float acc = (float)A * nk[0];
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc = fmaf((float)kap[j], nk[1 << j], acc);
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+      for (int l = j + 1; l < R; ++l) acc = fmaf((float)qk[(1 << j) | (1 << l)], nk[(1 << j) | (1 << l)], acc);
     acc_cta += acc;
   }
   if (pd.store) {
@@ -374,7 +395,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
 size_t layer_pass_smem(int kind, int tabcap) {
   const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
   const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - r));
-  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 32 * 4 + sizeof(TileConst) +
+  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 64 * 4 + sizeof(TileConst) +
          PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * sizeof(double);
 }
 

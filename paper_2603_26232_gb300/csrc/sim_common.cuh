@@ -239,6 +239,23 @@ __device__ __forceinline__ void mix_regs_sel(float2 (&a)[1 << R], float mu, uint
   }
 }
 
+// One mixing round: with FULL every slot in ALLOWED mixes, so one broadcast
+// multiplier serves them all; otherwise mix_regs_sel's per-slot selects.
+template <int R, uint32_t ALLOWED>
+__device__ __forceinline__ void mix_round(float2 (&a)[1 << R], float mu, uint32_t mask, bool full) {
+  if (full) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (!((ALLOWED >> j) & 1u)) continue;
+#pragma unroll
+      for (int k = 0; k < (1 << R); ++k)
+        if (!((k >> j) & 1)) bfly(a[k], a[k | (1 << j)], mu);
+    }
+  } else {
+    mix_regs_sel<R, ALLOWED>(a, mu, mask);
+  }
+}
+
 // Deterministic block sum of one double per thread (fixed reduction order).
 __device__ __forceinline__ double block_sum(double v, double* red, uint32_t tid, uint32_t nt) {
 #pragma unroll
