@@ -109,6 +109,37 @@ __device__ __forceinline__ float2 ld_state(const float2* p) {
   else return *p;
 }
 
+// Tile constants (cf, lam) of each of a CTA's tiles tj + (u << per), one
+// warp per tile: lane v < n adds vertex v's share of C(z_F), lane v < tb
+// the lam of local bit v. Run once per CTA before its tile loop; kept out of
+// line so that its registers do not weigh on the loop's.
+__device__ __noinline__ void tile_consts(TileConst* tcs, const uint32_t* pls, uint32_t tid, uint32_t nt,
+                                         uint32_t ntiles, uint32_t tj, uint32_t per, uint32_t lowt, int c, int s,
+                                         int g, int n, int P, int tb) {
+  const uint32_t lane = tid & 31u;
+  for (uint32_t u = tid >> 5; u < ntiles; u += nt >> 5) {
+    const uint32_t tu = tj | (u << per);
+    const uint32_t zb = ((tu & ((1u << lowt) - 1u)) << c) | ((tu >> lowt) << (s + g));
+    int cfu = 0;
+    if ((int)lane < n && ((zb >> lane) & 1u)) {
+      const uint32_t* row = pls + lane * P;
+      for (int b = 0; b < P; ++b) cfu += __popc(row[b] & ~zb) << b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cfu += __shfl_xor_sync(0xffffffffu, cfu, o);
+    if (lane < (uint32_t)tb) {
+      const uint32_t* row = pls + qubit_of(lane, c, s) * P;
+      int d = 0, aa = 0;
+      for (int b = 0; b < P; ++b) {
+        d += __popc(row[b]) << b;
+        aa += __popc(row[b] & zb) << b;
+      }
+      tcs[u].lam[lane] = d - 2 * aa;
+    }
+    if (lane == 0) tcs[u].cf = cfu;
+  }
+}
+
 // One CTA's share of a layer pass, work unit `bid` of the pass: instance
 // list[bid >> per] and its tiles tj, tj + 2^per, ... with tj = bid mod 2^per
 // (per = tiles_log2 - tpc_log2, 2^tpc_log2 tiles).
@@ -135,8 +166,8 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   float2* sm = tab + tabcap;
   int* qk = reinterpret_cast<int*>(sm + padded_r<TB, R>());  // 2^R entries (<= 32)
   int* qk8 = qk + 32;  // the same in bytes of the phase table (x sizeof(float2))
-  TileConst* tc = reinterpret_cast<TileConst*>(qk + 64);
-  uint32_t* pls = reinterpret_cast<uint32_t*>(tc + 1);  // the instance's bit-planes
+  TileConst* tcs = reinterpret_cast<TileConst*>(qk + 64);  // one per tile of the CTA
+  uint32_t* pls = reinterpret_cast<uint32_t*>(tcs + (1 << kMaxTpcLog2));  // the instance's bit-planes
   double* red = reinterpret_cast<double*>(pls + PARAQAOA_MAX_QUBITS * kMaxPlanes);
   const uint32_t tid = threadIdx.x;
   const int c = CONTIG ? TB : pd.c, s = CONTIG ? TB : pd.s, g = TB - c;
@@ -154,10 +185,11 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   const bool need_cut = pd.layerP >= 0 || pd.expect;
 
   // ---- set-up. One round of global loads, all issued before the first
-  // barrier (the state loads below too): the phase table, the instance's
-  // adjacency bit-planes, the Q_K table and this thread's cut constants.
-  // After the barrier warp 0 derives the tile constants from the planes in
-  // shared memory.
+  // barrier (the first tile's state loads too): the phase table, the
+  // instance's adjacency bit-planes, the Q_K table and this thread's cut
+  // constants. After the barrier each warp derives the constants of one of
+  // the CTA's tiles (more when the tiles outnumber the warps) from the planes
+  // in shared memory, so the tile loop itself needs no barrier for them.
   if (pd.layerP >= 0) {
     const float2* tl = tables + Ip->table_off + (int64_t)pd.layerP * (W + 1);
     for (int cc = tid; cc <= W; cc += NT) tab[cc] = tl[cc];
@@ -184,22 +216,16 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
   auto zmap = [&](uint32_t li) -> uint32_t { return CONTIG ? li : (li & lowm) | ((li & ~lowm) << sh); };
   // load/store layout O0: this thread's amplitude offsets are zmap(lt | register bits)
   const uint32_t lt = lir_o<TB, R, O0>(tid, 0);
-  // Tiles of one CTA share the set-up above. Across iterations the barriers
-  // below order every reuse of shared memory: warp 0 rewrites the tile
-  // constants only after the first barrier of the next tile, which every
-  // thread reaches after its last read of them.
+  // Tiles of one CTA share the set-up above; inside the tile loop shared
+  // memory is written only by the transposes. Those leave out the barrier
+  // after their reads (each chains from the layout the one before it read).
+  // Across tiles the chain holds when the pass starts in the layout it ends
+  // in (O0 when it mixes first, else the cut layout OC); otherwise a barrier
+  // follows the next tile's state loads (issued first, so that they are in
+  // flight while warps wait).
   const uint32_t ntiles = 1u << pd.tpc_log2;
-  const bool tile_barrier_covered =
-      !SPLIT && NR >= 2 && !warp_local_transpose<TB, R, O0, O1>() && (pd.layerA >= 0 || pd.layerB >= 0);
-  // Transposes leave out the barrier after their reads (each chains from the
-  // layout the one before it read). Across tiles the chain holds when the
-  // pass starts in the layout it ends in (O0 when it mixes first, else the
-  // cut layout OC); otherwise a CTA barrier of the next tile's set-up must
-  // come between, the tile-constant barrier (cut needed) or the first
-  // barrier (not covered), else one is taken at the end of the tile.
   const bool tr_a = pd.layerA >= 0, tr_b = pd.layerB >= 0, tr_s = pd.store && !tr_b;
-  const bool trail_tile = NR > 1 && (tr_a || tr_b || tr_s) && (tr_a ? O0 : OC) != ((tr_b || tr_s) ? O0 : OC) &&
-                          !need_cut && tile_barrier_covered;
+  const bool trail_tile = NR > 1 && (tr_a || tr_b || tr_s) && (tr_a ? O0 : OC) != ((tr_b || tr_s) ? O0 : OC);
   // this thread's <C> terms over the CTA's tiles, summed in FP32 in two
   // levels (2^R positive terms per tile, then at most 2^kMaxTpcLog2 tile
   // sums: relative error below 48 x 2^-24, about 3e-6), FP64 from the block
@@ -239,37 +265,20 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
       a[k] = ld_state<CG>(base + off);
     }
   }
-  // Set-up visible (first tile); later, this barrier keeps warp 0 from
-  // rewriting the tile constants while others still read the previous
-  // tile's. A classic pass of two or more rounds that mixes crosses a CTA
-  // barrier (a transpose between warps) after those reads in every tile, so
-  // there it is needed for the first tile only.
-  if (tt == 0 || !tile_barrier_covered) __syncthreads();
+  if (tt == 0) {
+    __syncthreads();  // set-up loads visible
+    if (need_cut) {
+      tile_consts(tcs, pls, tid, NT, ntiles, tj, per, lowt, c, s, g, n, P, TB);
+      __syncthreads();  // tile constants visible
+    }
+  } else if (trail_tile) {
+    __syncthreads();  // the previous tile's last transpose reads, before this tile's first writes
+  }
   int A = 0, kap[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) kap[j] = 0;
   if (need_cut) {
-    if (tid < 32) {
-      // lane u < n: contribution of vertex u to C(z_F); lane u < TB: lam of local bit u
-      int cfu = 0;
-      if ((int)tid < n && ((zbase >> tid) & 1u)) {
-        const uint32_t* row = pls + tid * P;
-        for (int b = 0; b < P; ++b) cfu += __popc(row[b] & ~zbase) << b;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) cfu += __shfl_xor_sync(0xffffffffu, cfu, o);
-      if (tid < (uint32_t)TB) {
-        const uint32_t* row = pls + qubit_of(tid, c, s) * P;
-        int d = 0, aa = 0;
-        for (int b = 0; b < P; ++b) {
-          d += __popc(row[b]) << b;
-          aa += __popc(row[b] & zbase) << b;
-        }
-        tc->lam[tid] = d - 2 * aa;
-      }
-      if (tid == 0) tc->cf = cfu;
-    }
-    __syncthreads();  // tile constants visible
+    const TileConst* tc = tcs + tt;
     A = tc->cf + ccJ;
 #pragma unroll
     for (int b = 0; b < TB - R; ++b) A += ((tid >> b) & 1u) ? tc->lam[thread_bit_local_o<R, OC>(b)] : 0;
@@ -365,7 +374,6 @@ __device__ __forceinline__ void layer_tiles(const PassDesc pd, int32_t n, int32_
       base[off] = a[k];
     }
   }
-  if (trail_tile) __syncthreads();
   }  // tiles of this CTA
   // One block reduction per CTA (the FP64 pipe is narrow and the reduction
   // serialises the CTA): the sum goes to the partial slot of the CTA's first
@@ -395,7 +403,7 @@ __global__ void __launch_bounds__(1 << (TB - R), layer_min_blocks(TB, R))
 size_t layer_pass_smem(int kind, int tabcap) {
   const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
   const size_t padded = (size_t(1) << tb) + (size_t(1) << (tb - r));
-  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 64 * 4 + sizeof(TileConst) +
+  return (size_t)tabcap * sizeof(float2) + padded * sizeof(float2) + 64 * 4 + (sizeof(TileConst) << kMaxTpcLog2) +
          PARAQAOA_MAX_QUBITS * kMaxPlanes * 4 + 32 * sizeof(double);
 }
 
