@@ -397,15 +397,12 @@ int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
  * cycles through the parts of that size, at depth p, and keeps the fastest
  * for ctx: tile shapes (2^12
  * amplitudes per CTA as 32 or 16 registers per thread, or 2^13 as 32),
- * minimum contiguous-qubit runs of the higher groups (2..4), and classic or
- * split schedules (classic: the low group is the tile's 2^12 or 2^13
- * contiguous qubits, mixed in up to three register rounds; split: the low
- * group is the 2R lowest qubits, mixed in two rounds with one transpose),
- * and 1, 2, 4, 8 or 16 tiles per CTA (sharing the per-instance set-up
- * loads and the <C> reduction). Choices that give the same pass schedule are
- * timed once. Optional outputs (31 entries each, indexed by n): chosen tile
- * bits, register bits per thread, minimum run, split flag, log2 tiles per
- * CTA. Without a call the context uses the choices measured on a p = 2
+ * minimum contiguous-qubit runs of the higher groups (2..4), the schedule
+ * form (PARAQAOA_SCHED_*: classic or split, low or high group first) and 1,
+ * 2, 4, 8 or 16 tiles per CTA (sharing the per-instance set-up loads and
+ * the <C> reduction). Choices that give the same pass schedule are timed
+ * once. Optional outputs (31 entries each, indexed by n): chosen tile bits,
+ * register bits per thread, minimum run, form bits, log2 tiles per CTA. Without a call the context uses the choices measured on a p = 2
  * sweep of G(*, 0.3) parts: (12/5, run 2, split, 2 tiles per CTA) up to 18
  * qubits, (12/4, 2, classic, 8) for 19-20, (13/5, 2, classic, 4) for 21-24
  * and (12/5, 2, split, 4) from 25. */
@@ -439,17 +436,30 @@ int paraqaoa_set_halved(paraqaoa_ctx *ctx, int32_t enable);
  * per subgraph (Sec. 3.3). */
 int paraqaoa_set_persistent(paraqaoa_ctx *ctx, int32_t enable);
 
+/* Schedule form bits (the `split` argument of the schedule calls).
+ * SPLIT: the low group is the 2R lowest qubits, mixed in two register rounds
+ * with one transpose (otherwise classic: the low group is the tile's 2^tb
+ * contiguous qubits, mixed in up to four rounds). HIGH_FIRST: every layer
+ * visits the qubit groups in the reverse order, so layer 0 starts on the
+ * highest group; the first pass (write only) and, at even p, the last (read
+ * only) then mix a high group, fewer qubits than the low group. Either order
+ * is the circuit of Sec. 2.2: one layer's mixers commute qubit by qubit. */
+#define PARAQAOA_SCHED_SPLIT 0x1
+#define PARAQAOA_SCHED_HIGH_FIRST 0x2
+
 /* Set the layer-pass schedule of n-qubit parts by hand (the choice the
  * autotuner makes): tile bits and register bits per thread (one of the
- * shapes 12/5, 12/4, 13/5), minimum contiguous run c_min of the higher groups,
- * split (0 classic, 1 split) and log2 of the tiles each CTA walks (0..4).
- * Affects later simulate calls of ctx. */
+ * shapes 12/5, 12/4, 13/5, 13/4, 14/4), minimum contiguous run c_min of the
+ * higher groups, split = PARAQAOA_SCHED_* form bits (0..3) and log2 of the
+ * tiles each CTA walks (0..4). Affects later simulate calls of ctx. States
+ * kept halved (PARAQAOA_SIM_HALVED) use the classic low-group-first form. */
 int paraqaoa_set_schedule(paraqaoa_ctx *ctx, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2);
 
 /* The layer-pass schedule of one n-qubit state at depth p for a tile shape
- * (tile_bits/reg_bits one of 12/5, 12/4, 13/5), minimum contiguous run
- * c_min of the higher groups and split flag, without a context or a GPU
+ * (tile_bits/reg_bits one of 12/5, 12/4, 13/5, 13/4, 14/4), minimum
+ * contiguous run c_min of the higher groups and PARAQAOA_SCHED_* form bits
+ * `split` (0..3), without a context or a GPU
  * (Sec. 2.2: the p layers' mixers commute qubit by qubit, so a layer can be
  * applied in qubit groups that fit a tile, and one pass ends layer l on a
  * group, applies phase l + 1 and starts layer l + 1 on the same group).

@@ -23,6 +23,7 @@ E_SEARCH_TOO_LARGE, E_CUDA, E_TIMEOUT, E_NO_RESULT = -5, -6, -7, -8
 E_SCRATCH_LIMIT = -9
 PART_BALANCED, PART_ALG1_LITERAL, PART_SIZES = 0, 1, 2
 SIM_EXPECT, SIM_KEEP_STATE, SIM_HALVED = 0x1, 0x2, 0x4
+SCHED_SPLIT, SCHED_HIGH_FIRST = 0x1, 0x2
 TOPK_CANONICAL, TOPK_RAW = 0x0, 0x1
 KCLASS_LAYER_PASS, KCLASS_SMEM_SIM, KCLASS_TOPK, KCLASS_MERGE, KCLASS_OTHER, KCLASS_TC_MIXER = range(6)
 TC_BF16, TC_FP16 = 0, 1

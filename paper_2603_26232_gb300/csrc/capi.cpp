@@ -398,13 +398,14 @@ int paraqaoa_state(paraqaoa_ctx* c, int32_t i, float* out_host) {
 int paraqaoa_schedule(int32_t n, int32_t p, int32_t tile_bits, int32_t reg_bits, int32_t c_min, int32_t split,
                       int32_t keep, int32_t expect, int32_t max_passes, int32_t* out, int32_t* out_count) {
   if (!out_count || max_passes < 0 || (max_passes > 0 && !out)) return PARAQAOA_E_INVAL;
-  if (n > PARAQAOA_MAX_QUBITS || p < 1 || p > PARAQAOA_MAX_P || c_min < 0 || c_min > 8 || (split != 0 && split != 1))
+  if (n > PARAQAOA_MAX_QUBITS || p < 1 || p > PARAQAOA_MAX_P || c_min < 0 || c_min > 8 || split < 0 || split > 3)
     return PARAQAOA_E_INVAL;
   int kind = -1;
   for (int k = 0; k < kTileKinds; ++k)
     if (kTileShapes[k].tb == tile_bits && kTileShapes[k].r == reg_bits) kind = k;
-  if (kind < 0 || n < tile_bits || (split && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
-  const auto sched = make_schedule(n, p, tile_bits, c_min, keep != 0, expect != 0, split ? reg_bits : 0);
+  if (kind < 0 || n < tile_bits || ((split & 1) && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
+  const auto sched =
+      make_schedule(n, p, tile_bits, c_min, keep != 0, expect != 0, (split & 1) ? reg_bits : 0, (split & 2) != 0);
   *out_count = (int32_t)sched.size();
   for (int32_t i = 0; i < (int32_t)sched.size() && i < max_passes; ++i) {
     const PassDesc& d = sched[i];
@@ -431,12 +432,12 @@ int paraqaoa_set_persistent(paraqaoa_ctx* c, int32_t enable) {
 
 int paraqaoa_set_schedule(paraqaoa_ctx* c, int32_t n, int32_t tile_bits, int32_t reg_bits, int32_t c_min,
                           int32_t split, int32_t tiles_per_cta_log2) {
-  if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || (split != 0 && split != 1) ||
+  if (!c || n < kSmemMaxQubits + 1 || n > PARAQAOA_MAX_QUBITS || c_min < 0 || c_min > 8 || split < 0 || split > 3 ||
       tiles_per_cta_log2 < 0 || tiles_per_cta_log2 > kMaxTpcLog2)
     return PARAQAOA_E_INVAL;
   for (int kind = 0; kind < kTileKinds; ++kind)
     if (kTileShapes[kind].tb == tile_bits && kTileShapes[kind].r == reg_bits) {
-      if (n < tile_bits || (split && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
+      if (n < tile_bits || ((split & 1) && n <= 2 * reg_bits)) return PARAQAOA_E_INVAL;
       // four-round shapes mix high groups in at most three rounds, which
       // needs at least two contiguous qubits carried
       if (tile_bits > 3 * reg_bits && c_min < 2) return PARAQAOA_E_INVAL;
@@ -478,10 +479,10 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
     for (int kind = 0; kind < kTileKinds; ++kind) {
       const int tb = kTileShapes[kind].tb, r = kTileShapes[kind].r;
       if (n < tb) continue;
-      for (int sp = 0; sp <= 1; ++sp)
+      for (int sp = 0; sp <= 3; ++sp)  // bit 0 split, bit 1 high group first
         for (int cm = 2; cm <= 4; ++cm) {
-          const int G = schedule_groups(n, tb, cm, sp ? r : 0);
-          const auto sched = make_schedule(n, p, tb, cm, false, true, sp ? r : 0);
+          const int G = schedule_groups(n, tb, cm, (sp & 1) ? r : 0);
+          const auto sched = make_schedule(n, p, tb, cm, false, true, (sp & 1) ? r : 0, (sp & 2) != 0);
           const std::pair<int, int> key(G * 1000 + kind * 10 + sp, sched.size() > 1 ? sched[1].c : 0);
           if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
           seen.push_back(key);

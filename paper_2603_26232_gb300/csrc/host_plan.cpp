@@ -271,7 +271,8 @@ int plan_run(paraqaoa_ctx* c) {
           pd.mirrorB = pd.layerB >= 0;
         }
     } else {
-      q.sched = make_schedule(n, p, q.tb, c->c_min[n], keep, want, c->split[n] ? kTileShapes[q.kind].r : 0);
+      q.sched = make_schedule(n, p, q.tb, c->c_min[n], keep, want, (c->split[n] & 1) ? kTileShapes[q.kind].r : 0,
+                              (c->split[n] & 2) != 0);
     }
     std::vector<std::array<int, 4>> keys;
     for (const PassDesc& pd : q.sched) {
@@ -482,7 +483,12 @@ int ctx_part_device(paraqaoa_ctx* c, const paraqaoa_part* pt, const SubDev** sub
 // runs of 2^(tb-g) amplitudes. Layer l visits the groups in increasing order
 // for even l and decreasing for odd l, so the last group of layer l is the
 // first of layer l+1 and one pass can finish layer l, apply the phase of
-// l+1 and start its mixer: 1 + p (G - 1) passes in all.
+// l+1 and start its mixer: 1 + p (G - 1) passes in all. high_first reverses
+// every layer's visiting order (layer 0 runs from the highest group down to
+// group 0): the same number of passes, but the first pass (which only
+// writes) mixes the highest group, and at even p so does the last (which
+// only reads); a high group mixes fewer qubits, in fewer register rounds,
+// than the tile-wide low group.
 // Split schedules (split_r = R > 0) give group 0 only the 2R lowest qubits,
 // which a pass mixes in two register rounds with a single transpose; the
 // tile still loads 2^tb contiguous amplitudes, and qubits [2R, n) form the
@@ -493,7 +499,8 @@ int schedule_groups(int n, int tb, int c_min, int split_r) {
   return 1 + (n - low + gmax - 1) / gmax;
 }
 
-std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect, int split_r) {
+std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect, int split_r,
+                                   bool high_first) {
   const int TB = tb;
   struct Grp {
     int c, s, mix_lo, split;
@@ -521,7 +528,9 @@ std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, 
     return d;
   };
   std::vector<PassDesc> out;
-  PassDesc first = mk(0);
+  // layer l visits the groups upward when l + high_first is even
+  auto order = [&](int l, int i) { return ((l + (high_first ? 1 : 0)) % 2 == 0) ? i : G - 1 - i; };
+  PassDesc first = mk(order(0, 0));
   first.init = 1;
   first.layerP = 0;
   first.layerB = 0;
@@ -529,7 +538,7 @@ std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, 
   out.push_back(first);
   for (int l = 0; l < p; ++l) {
     std::vector<int> ord(G);
-    for (int i = 0; i < G; ++i) ord[i] = (l % 2 == 0) ? i : G - 1 - i;
+    for (int i = 0; i < G; ++i) ord[i] = order(l, i);
     for (int idx = 1; idx < G; ++idx) {
       PassDesc d = mk(ord[idx]);
       d.layerA = l;

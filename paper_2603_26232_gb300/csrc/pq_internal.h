@@ -217,7 +217,8 @@ int ctx_device(paraqaoa_ctx* c);
 int ctx_part_device(paraqaoa_ctx* c, const paraqaoa_part* pt, const SubDev** subs, const uint32_t** planes);
 
 // Pass schedule for an n-qubit instance group (layer_pass.cu host helper).
-std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect, int split_r);
+std::vector<PassDesc> make_schedule(int n, int p, int tb, int c_min, bool keep, bool expect, int split_r,
+                                   bool high_first = false);
 int schedule_groups(int n, int tb, int c_min, int split_r);
 
 }  // namespace pq

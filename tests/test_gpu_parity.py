@@ -425,11 +425,12 @@ def test_autotune_choices_keep_parity(api, orc):
                                              (13, 5, 1, 0), (12, 4, 0, 3), (12, 4, 1, 2), (12, 5, 0, 2),
                                              (12, 5, 1, 3), (13, 5, 0, 1), (13, 5, 1, 2), (13, 4, 0, 0),
                                              (13, 4, 0, 2), (13, 4, 1, 1), (14, 4, 0, 0), (14, 4, 0, 3),
-                                             (14, 4, 1, 0)])
+                                             (14, 4, 1, 0), (12, 4, 2, 3), (12, 5, 3, 0), (13, 5, 2, 2),
+                                             (13, 4, 3, 1), (14, 4, 2, 0)])
 def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
-    """Every tile shape in classic and split schedules, one or several tiles
-    per CTA, on parts of 15..24 qubits (two and three qubit groups), depth 3,
-    states kept."""
+    """Every tile shape in every schedule form (classic or split, low or high
+    group first), one or several tiles per CTA, on parts of 15..24 qubits
+    (two and three qubit groups), depth 3, states kept."""
     capi, ctx = api
     sizes = [15, 16, 19, 20, 21, 23, 24]
     g = chain_graph(sizes, 0.3, 40 + tb + rb + split + tpc, 10)

@@ -41,8 +41,9 @@ def _mixed_qubits(pd, tb, r):
     return set(q[pd["mix_lo"]:])
 
 
-def _replay(n, p, tb, r, c_min, split, keep, expect):
-    passes = capi.paraqaoa_schedule(n, p, tb, r, c_min, split, keep, expect)
+def _replay(n, p, tb, r, c_min, form, keep, expect):
+    passes = capi.paraqaoa_schedule(n, p, tb, r, c_min, form, keep, expect)
+    split, high_first = form & capi.SCHED_SPLIT, form & capi.SCHED_HIGH_FIRST
     full = set(range(n))
     mixed = [set() for _ in range(p)]
     phased = [False] * p
@@ -95,12 +96,30 @@ def _replay(n, p, tb, r, c_min, split, keep, expect):
 
 
 @pytest.mark.parametrize("tb,r", SHAPES)
-@pytest.mark.parametrize("split", [0, 1])
-def test_schedules_replay_the_circuit(tb, r, split):
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
+def test_schedules_replay_the_circuit(tb, r, form):
     for n, p, c_min, keep, expect in itertools.product(range(15, 31), (1, 2, 3, 4), (2, 3, 4), (0, 1), (0, 1)):
         if n < tb:
             continue
-        _replay(n, p, tb, r, c_min, split, keep, expect)
+        _replay(n, p, tb, r, c_min, form, keep, expect)
+
+
+def test_high_group_first_order():
+    # n = 20 on 2^12 x 16: the write-only first pass and, at p = 2, the
+    # read-only last pass mix the 8-qubit high group; the full pass between
+    # them mixes the 12-qubit low group twice around the phase of layer 1
+    passes, G = _replay(20, 2, 12, 4, 2, capi.SCHED_HIGH_FIRST, 0, 1)
+    assert G == 2 and [pd["c"] for pd in passes] == [4, 12, 4]
+    assert (passes[1]["layerA"], passes[1]["layerP"], passes[1]["layerB"]) == (0, 1, 1)
+    # p = 1: the last pass is the low group's
+    passes, _ = _replay(20, 1, 12, 4, 2, capi.SCHED_HIGH_FIRST, 0, 1)
+    assert [pd["c"] for pd in passes] == [4, 12]
+    # three groups: layer 0 runs 2, 1, 0 and layer 1 runs 0, 1, 2
+    passes, G = _replay(26, 2, 12, 5, 2, capi.SCHED_SPLIT | capi.SCHED_HIGH_FIRST, 0, 1)
+    assert G == 3 and [pd["s"] for pd in passes] == [18, 10, 12, 10, 18]
+    # the same pass count as the low-group-first form
+    for n, p in itertools.product((17, 20, 23, 26), (1, 2, 3)):
+        assert len(_replay(n, p, 12, 4, 2, 2, 0, 1)[0]) == len(_replay(n, p, 12, 4, 2, 0, 0, 1)[0])
 
 
 def test_pass_counts_of_the_measured_schedules():
@@ -125,6 +144,7 @@ def test_pass_counts_of_the_measured_schedules():
 
 def test_schedule_rejects_invalid_arguments():
     for args in [(20, 2, 12, 3, 2, 0), (20, 2, 14, 5, 2, 0), (11, 1, 12, 4, 2, 0), (20, 0, 12, 4, 2, 0),
-                 (20, 17, 12, 4, 2, 0), (31, 1, 12, 4, 2, 0), (20, 1, 12, 4, 9, 0), (20, 1, 12, 4, 2, 2)]:
+                 (20, 17, 12, 4, 2, 0), (31, 1, 12, 4, 2, 0), (20, 1, 12, 4, 9, 0), (20, 1, 12, 4, 2, 4),
+                 (20, 1, 12, 4, 2, -1)]:
         with pytest.raises(capi.ParaQAOAError):
             capi.paraqaoa_schedule(*args)
