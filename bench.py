@@ -490,8 +490,9 @@ def run_sweep_case(args):
 
 
 def run_shapes_case(args):
-    """Every distinct layer-pass schedule (tile shape, contiguous run, classic
-    or split, tiles per CTA) at n = sweep-lo..sweep-hi, on the sweep's batch
+    """Every distinct layer-pass schedule (tile shape, contiguous run, form:
+    classic or split, low or high group first; tiles per CTA) at
+    n = sweep-lo..sweep-hi, on the sweep's batch
     (sum 2^n >= 2^28, p = 2, <C> only): the layer passes' summed event time
     per batch, their fraction of the 16 B roofline and their streamed bytes'
     fraction of the measured copy bandwidth; the 12 fastest per n."""
@@ -512,9 +513,9 @@ def run_shapes_case(args):
         gam, bet = synth.random_angles(count, 2, 11)
         rows, seen = [], set()
         for tb, r in shapes:
-            for sp in (0, 1):
+            for sp in (0, 1, 2, 3):  # schedule form bits: split, high group first
                 for cm in (2, 3, 4):
-                    for tpc in range(4):
+                    for tpc in range(5):
                         try:
                             capi.paraqaoa_set_schedule(ctx, n, tb, r, cm, sp, tpc)
                         except capi.ParaQAOAError:

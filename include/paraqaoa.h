@@ -402,10 +402,11 @@ int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
  * 2, 4, 8 or 16 tiles per CTA (sharing the per-instance set-up loads and
  * the <C> reduction). Choices that give the same pass schedule are timed
  * once. Optional outputs (31 entries each, indexed by n): chosen tile bits,
- * register bits per thread, minimum run, form bits, log2 tiles per CTA. Without a call the context uses the choices measured on a p = 2
- * sweep of G(*, 0.3) parts: (12/5, run 2, split, 2 tiles per CTA) up to 18
- * qubits, (12/4, 2, classic, 8) for 19-20, (13/5, 2, classic, 4) for 21-24
- * and (12/5, 2, split, 4) from 25. */
+ * register bits per thread, minimum run, form bits, log2 tiles per CTA.
+ * Without a call the context uses the choices measured on a p = 2 sweep of
+ * G(*, 0.3) parts: (13/5, run 2, split + high first, 8 tiles per CTA),
+ * except (12/4, 2, split + high first, 16) at 16 qubits and (13/5, 2,
+ * classic + high first, 8) for 21-24. */
 int paraqaoa_autotune(paraqaoa_ctx *ctx, const paraqaoa_part *part, int32_t p, int32_t *out_tile_bits,
                       int32_t *out_reg_bits, int32_t *out_c_min, int32_t *out_split,
                       int32_t *out_tiles_per_cta_log2);

@@ -50,28 +50,19 @@ int paraqaoa_create(paraqaoa_ctx** out, int device, size_t hbm_budget) {
   c->budget = hbm_budget;
   for (int n = 0; n <= PARAQAOA_MAX_QUBITS; ++n) {
     // Default schedules: the autotuner's choices on the p = 2 amplitude-layer
-    // sweep (parts of G(*, 0.3), weights 1..10): 2^12 x 32-register split
-    // schedules up to 18 qubits, 2^12 x 16 classic walking 8 tiles per CTA for
-    // 19-20, 2^13 x 32 classic walking 4 tiles for 21-24, and the split
-    // schedule walking 4 tiles from 25 qubits (three qubit groups). Parts of
-    // other graphs may prefer another; paraqaoa_autotune measures.
+    // sweep (parts of G(*, 0.3), 0.2 from 24 qubits, weights 1..10), all with
+    // contiguous runs of >= 2 qubits: 2^13 x 32 registers, split low group,
+    // high group first, walking 8 tiles per CTA (16 qubits: 2^12 x 16 split,
+    // high first, 16 tiles), the same tile classic and high first for 21-24
+    // (two qubit groups), split and high first again from 25 (three groups).
+    // Parts of other graphs may prefer another; paraqaoa_autotune measures.
     c->c_min[n] = 2;
-    if (n <= 18) {
-      c->tile_kind[n] = 0;
-      c->split[n] = 1;
-      c->tpc_log2[n] = 1;
-    } else if (n <= 20) {
+    c->tile_kind[n] = 2;
+    c->tpc_log2[n] = 3;
+    c->split[n] = (n >= 21 && n <= 24) ? 2 : 3;
+    if (n == 16) {
       c->tile_kind[n] = 1;
-      c->split[n] = 0;
-      c->tpc_log2[n] = 3;
-    } else if (n <= 24) {
-      c->tile_kind[n] = 2;
-      c->split[n] = 0;
-      c->tpc_log2[n] = 2;
-    } else {
-      c->tile_kind[n] = 0;
-      c->split[n] = 1;
-      c->tpc_log2[n] = 2;
+      c->tpc_log2[n] = 4;
     }
   }
   *out = c;

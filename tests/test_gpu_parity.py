@@ -406,7 +406,7 @@ def test_autotune_choices_keep_parity(api, orc):
         choice = capi.paraqaoa_autotune(ctx, part, 2)
         for n in sizes:
             tb, rb, cm, sp, tp = choice[n]
-            assert (tb, rb) in ((12, 5), (12, 4), (13, 5), (13, 4), (14, 4)) and cm in (2, 3, 4) and sp in (0, 1)
+            assert (tb, rb) in ((12, 5), (12, 4), (13, 5), (13, 4), (14, 4)) and cm in (2, 3, 4) and sp in (0, 1, 2, 3)
             assert 0 <= tp <= 4
         subs = oracle_parts(orc, g, sizes)
         ids = np.arange(len(sizes), dtype=np.int32)
@@ -459,12 +459,12 @@ def test_every_schedule_matches_oracle(api, orc, tb, rb, split, tpc):
 
 def test_default_schedules_match_oracle(api, orc):
     """A fresh context's built-in schedules (no autotune, no set_schedule):
-    2^12 x 32-register split walking 2 tiles up to 18 qubits, 2^12 x 16
-    classic walking 8 for 19-20, 2^13 x 32 classic walking 4 for 21-24;
-    depth 2, states kept."""
+    2^13 x 32 registers, split and high group first, walking 8 tiles (16
+    qubits: 2^12 x 16 walking 16), classic and high first for 21-24; depth 2,
+    states kept."""
     capi, _ = api
     ctx = capi.paraqaoa_create(0)
-    sizes = [15, 17, 19, 20, 21, 23, 24]
+    sizes = [15, 16, 17, 19, 20, 21, 23, 24]
     g = chain_graph(sizes, 0.3, 91, 10)
     part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
     try:
@@ -497,10 +497,11 @@ def test_set_schedule_rejects_out_of_range(api):
 
 def test_large_parts_full_size(api, orc):
     """Parts of 25 and 26 qubits (the 16,000-vertex workload's sizes, 256 and
-    512 MB complex64 states), p = 2, in the split schedule the autotuner picks
-    there and the context uses by default (three qubit groups, five passes, 4
-    tiles per CTA) and in a classic one: <C>, 4096
-    sampled amplitudes plus the top-32 entries, and the top-32 lists."""
+    512 MB complex64 states), p = 2, in the schedule the context uses by
+    default there (2^13 x 32, split and high group first: three qubit groups,
+    five passes, 8 tiles per CTA), the split 2^12 x 32 one, a classic 2^13
+    one and two groups on the 2^14 x 16 tile: <C>, 4096 sampled amplitudes
+    plus the top-32 entries, and the top-32 lists."""
     capi, ctx = api
     sizes = [25, 26]
     g = chain_graph(sizes, 0.15, 77, 10)
@@ -513,7 +514,7 @@ def test_large_parts_full_size(api, orc):
     try:
         # three groups in the split 2^12 x 32 schedule, a classic 2^13 one, and
         # two groups on the 2^14 x 16 tile (four register rounds in the low group)
-        for sched in [(12, 5, 2, 1, 2), (13, 5, 2, 0), (14, 4, 2, 0, 2)]:
+        for sched in [(13, 5, 2, 3, 3), (12, 5, 2, 1, 2), (13, 5, 2, 0), (14, 4, 2, 0, 2)]:
             for n in sizes:
                 capi.paraqaoa_set_schedule(ctx, n, *sched)
             ids = np.arange(2, dtype=np.int32)
