@@ -587,6 +587,19 @@ def onchip_measure(capi, ctx, peaks):
     return out
 
 
+def run_streams_case(args):
+    """Plain HBM streams (write only, read only, copy) over 2 GiB buffers:
+    the ceilings of the layer passes that only write or only read."""
+    import paper_2603_26232_gb300 as pkg
+    from paper_2603_26232_gb300 import _capi as capi
+
+    pkg.build()
+    peak, kind = read_peaks()
+    w, r, c = capi.paraqaoa_probe_streams(0, 1 << 31)
+    print(json.dumps({"case": "streams", "bytes": 1 << 31, "write_gbs": w, "read_gbs": r, "copy_gbs": c,
+                      "hbm_gbs": peak, "hbm_gbs_source": kind}), flush=True)
+
+
 def run_onchip_case(args):
     import paper_2603_26232_gb300 as pkg
     from paper_2603_26232_gb300 import _capi as capi
@@ -897,7 +910,7 @@ def main():
     ap.add_argument("--sweep-lo", type=int, default=14)
     ap.add_argument("--sweep-hi", type=int, default=26)
     ap.add_argument("--case", default="solve", choices=["solve", "layer_pass", "large", "learned", "sweep",
-                                                        "batching", "tc", "shapes", "onchip", "merge_levels",
+                                                        "batching", "tc", "shapes", "onchip", "streams", "merge_levels",
                                                         "ksweep", "halved"],
                     help="layer_pass: only the p=2 <C> batch of one Adam step (168 x 2^20), "
                          "a small case for profiling the layer-pass kernel")
@@ -943,6 +956,8 @@ def main():
         return run_shapes_case(args)
     if args.case == "onchip":
         return run_onchip_case(args)
+    if args.case == "streams":
+        return run_streams_case(args)
     if args.case == "merge_levels":
         return run_merge_levels_case(args)
     if args.case == "ksweep":

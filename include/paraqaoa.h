@@ -489,6 +489,17 @@ int paraqaoa_schedule(int32_t n, int32_t p, int32_t tile_bits, int32_t reg_bits,
  * No counterpart in the paper. */
 int paraqaoa_probe_peaks(int device, double *fp32_tflops, double *smem_tbs);
 
+/* Measured HBM stream bandwidth of device `device`, the ceilings of the
+ * layer passes that only write (a batch's first pass) or only read (its
+ * <C> pass): grid-stride float4 writes, reads and copies over buffers of
+ * `bytes` each (1 MiB .. 16 GiB, a multiple of 16; use >> L2), 8 resident
+ * CTAs of 256 threads per SM, best of five timed launches after one
+ * warm-up, in GB/s (copy counts read + written bytes). Allocates and frees
+ * two buffers of `bytes`; synchronises. Returns PARAQAOA_E_INVAL for bad
+ * arguments, PARAQAOA_E_NOMEM when the buffers do not fit. No counterpart
+ * in the paper. */
+int paraqaoa_probe_streams(int device, int64_t bytes, double *write_gbs, double *read_gbs, double *copy_gbs);
+
 /* Per-kernel device time recorded with CUDA events on the context stream.
  * enable != 0 starts recording (and clears the counters). While it is on,
  * size classes run in order on the context stream and Adam steps are

@@ -84,6 +84,7 @@ _SIGS = {
     "paraqaoa_set_persistent": ([P, ctypes.c_int32], ctypes.c_int),
     "paraqaoa_set_halved": ([P, ctypes.c_int32], ctypes.c_int),
     "paraqaoa_probe_peaks": ([ctypes.c_int, P, P], ctypes.c_int),
+    "paraqaoa_probe_streams": ([ctypes.c_int, ctypes.c_int64, P, P, P], ctypes.c_int),
     "paraqaoa_set_merge_fill": ([P, ctypes.c_int32, P], ctypes.c_int),
     "paraqaoa_pei": ([ctypes.c_double] * 4 + [P, P], ctypes.c_int),
     "paraqaoa_mlp_param_count": ([ctypes.c_int32], ctypes.c_int64),
@@ -402,6 +403,15 @@ def paraqaoa_probe_peaks(device: int = 0):
     m = ctypes.c_double(0.0)
     _check(load().paraqaoa_probe_peaks(int(device), ctypes.byref(f), ctypes.byref(m)), "paraqaoa_probe_peaks")
     return f.value, m.value
+
+
+def paraqaoa_probe_streams(device: int = 0, nbytes: int = 1 << 31):
+    """(write-only, read-only, copy) HBM GB/s measured on the device over
+    buffers of nbytes each."""
+    w, r, c = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().paraqaoa_probe_streams(int(device), int(nbytes), ctypes.byref(w), ctypes.byref(r), ctypes.byref(c)),
+           "paraqaoa_probe_streams")
+    return w.value, r.value, c.value
 
 
 def paraqaoa_set_wait_limit(ctx, ns: int):

@@ -2,7 +2,9 @@
 // (FFMA2, the butterfly instruction of the simulation kernels) and
 // shared-memory load/store bandwidth (their transposes). The on-chip
 // simulation of states of <= 14 qubits never touches HBM between layers;
-// these two measured rates are its roofline.
+// these two measured rates are its roofline. Plain HBM streams (write only,
+// read only, copy) give the ceilings of the layer passes that only write
+// (the first) or only read (the <C> pass).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,9 +65,88 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_smem(float2* out, int i
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Grid-stride float4 streams over n4 elements.
+__global__ void __launch_bounds__(kProbeThreads) k_stream_write(float4* p, size_t n4, float v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = make_float4(v, v, v, v);
+}
+__global__ void __launch_bounds__(kProbeThreads) k_stream_read(const float4* p, size_t n4, float* out) {
+  float s = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = p[i];
+    s += (a.x + a.y) + (a.z + a.w);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the loads live
+}
+__global__ void __launch_bounds__(kProbeThreads) k_stream_copy(const float4* a, float4* b, size_t n4) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
 }  // namespace
 
 }  // namespace pq
+
+extern "C" int paraqaoa_probe_streams(int device, int64_t bytes, double* write_gbs, double* read_gbs,
+                                      double* copy_gbs) {
+  using namespace pq;
+  if (!write_gbs || !read_gbs || !copy_gbs || bytes < (int64_t(1) << 20) || bytes > (int64_t(1) << 34) ||
+      bytes % 16 != 0)
+    return PARAQAOA_E_INVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return PARAQAOA_E_INVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return PARAQAOA_E_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PARAQAOA_E_CUDA;
+  const int blocks = sms * 8;  // 8 resident CTAs of 256 threads per SM
+  const size_t n4 = (size_t)bytes / 16;
+  float4 *a = nullptr, *b = nullptr;
+  float* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = PARAQAOA_OK;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == PARAQAOA_OK) rc = e == cudaErrorMemoryAllocation ? PARAQAOA_E_NOMEM : PARAQAOA_E_CUDA;
+    return e == cudaSuccess;
+  };
+  ck(cudaMalloc(&a, (size_t)bytes));
+  ck(cudaMalloc(&b, (size_t)bytes));
+  ck(cudaMalloc(&out, sizeof(float) * (size_t)blocks * kProbeThreads));
+  ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  ck(cudaEventCreate(&e0));
+  ck(cudaEventCreate(&e1));
+  if (rc == PARAQAOA_OK) {
+    ck(cudaMemsetAsync(a, 0, (size_t)bytes, st));
+    ck(cudaMemsetAsync(b, 0, (size_t)bytes, st));
+  }
+  float best[3] = {1e30f, 1e30f, 1e30f};
+  for (int rep = 0; rep < 6 && rc == PARAQAOA_OK; ++rep) {  // the first round warms up
+    for (int k = 0; k < 3 && rc == PARAQAOA_OK; ++k) {
+      float ms = 0.f;
+      ck(cudaEventRecord(e0, st));
+      if (k == 0) k_stream_write<<<blocks, kProbeThreads, 0, st>>>(a, n4, 1.f);
+      else if (k == 1) k_stream_read<<<blocks, kProbeThreads, 0, st>>>(b, n4, out);
+      else k_stream_copy<<<blocks, kProbeThreads, 0, st>>>(a, b, n4);
+      ck(cudaGetLastError());
+      ck(cudaEventRecord(e1, st));
+      ck(cudaEventSynchronize(e1));
+      ck(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) best[k] = std::min(best[k], ms);
+    }
+  }
+  if (rc == PARAQAOA_OK) {
+    *write_gbs = (double)bytes / (best[0] * 1e-3) / 1e9;
+    *read_gbs = (double)bytes / (best[1] * 1e-3) / 1e9;
+    *copy_gbs = 2.0 * (double)bytes / (best[2] * 1e-3) / 1e9;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (out) cudaFree(out);
+  if (b) cudaFree(b);
+  if (a) cudaFree(a);
+  return rc;
+}
 
 extern "C" int paraqaoa_probe_peaks(int device, double* fp32_tflops, double* smem_tbs) {
   using namespace pq;
