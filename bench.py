@@ -221,15 +221,15 @@ def run_reference(args, rank, world):
 
 
 def run_layer_case(args):
-    """168 instances (21 parts x 8 angle sets) of 20 qubits at p = --layer-p
-    (default 2: one Adam-step batch of the workload), <C> only; prints the
-    layer passes' timing."""
+    """168 instances (21 parts x 8 angle sets) of 20 qubits of G(400,
+    --layer-density) at p = --layer-p (default 2: one Adam-step batch of the
+    workload), <C> only; prints the layer passes' timing."""
     import torch
     import paper_2603_26232_gb300 as pkg
     from paper_2603_26232_gb300 import _capi as capi
 
     pkg.build()
-    g = synth.erdos_renyi(NV, 0.1, 0, wmax=WMAX)
+    g = synth.erdos_renyi(NV, args.layer_density, 0, wmax=WMAX)
     ctx = capi.paraqaoa_create(0)
     G = capi.Graph.of(g)
     part = capi.paraqaoa_partition(G, M)
@@ -917,6 +917,8 @@ def main():
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--layer-p", type=int, default=2, help="layer_pass case: QAOA depth of the batch (1: the "
                                                              "grid batches' two half passes, 2: the Adam batches)")
+    ap.add_argument("--layer-density", type=float, default=0.1, help="layer_pass case: edge probability of the "
+                                                                     "400-vertex graph (0.1 or 0.5 in the workload)")
     ap.add_argument("--sched", default="", help="fixed schedule of the 20-qubit parts instead of the autotuner: "
                                                 "tile_bits,reg_bits,c_min,split[,tiles_per_cta_log2]")
     ap.add_argument("--no-large", action="store_true", help="skip the 16k-vertex time-to-cut")

@@ -393,8 +393,10 @@ int paraqaoa_simulate_tc(paraqaoa_ctx *ctx, const paraqaoa_part *part, const int
 
 /* Autotuner for the HBM-streaming layer passes (no counterpart in the paper,
  * which runs a fixed solver per subgraph). For every qubit count n >= 15
- * present in `part`, times the candidate schedules on a >= 1 GB batch that
- * cycles through the parts of that size, at depth p, and keeps the fastest
+ * present in `part`, times the candidate schedules at depth p on the batch
+ * one Adam step of the parts of that size runs (4p evaluations per part),
+ * repeated to >= 1 GB (>= 1 GB of the parts cycled when one step holds more
+ * than 4 GB), and keeps the fastest
  * for ctx: tile shapes (2^12
  * amplitudes per CTA as 32 or 16 registers per thread, or 2^13 as 32),
  * minimum contiguous-qubit runs of the higher groups (2..4), the schedule

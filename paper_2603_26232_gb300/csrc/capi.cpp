@@ -456,8 +456,14 @@ int paraqaoa_autotune(paraqaoa_ctx* c, const paraqaoa_part* pt, int32_t p, int32
     for (int32_t i = 0; i < pt->M; ++i)
       if (pt->size[i] == n && pt->weight[i] <= PARAQAOA_MAX_SUBGRAPH_WEIGHT) reps.push_back(i);
     if (reps.empty()) continue;
-    // the parts cycled until the batch streams >= 1 GB (well past L2)
-    const int64_t copies = std::max<int64_t>(1, std::min<int64_t>(256, (int64_t(1) << 30) / (int64_t(8) << n)));
+    // The batch one Adam step of these parts runs (4p shifted evaluations
+    // per part: its CTA count, and so its wave quantisation on the SMs, is
+    // the one the tuned schedule meets), repeated until it streams >= 1 GB
+    // (well past L2); when one such step holds more than 4 GB, >= 1 GB of
+    // the parts cycled.
+    const int64_t state_b = int64_t(8) << n, step = (int64_t)reps.size() * 4 * p, gb = int64_t(1) << 30;
+    int64_t copies = step * std::max<int64_t>(1, (gb + step * state_b - 1) / (step * state_b));
+    if (step * state_b > 4 * gb || copies > 4096) copies = std::max<int64_t>(1, std::min<int64_t>(4096, gb / state_b));
     std::vector<int32_t> ids(copies);
     for (int64_t k = 0; k < copies; ++k) ids[k] = reps[k % reps.size()];
     std::vector<double> ang(copies * p, 0.5);
