@@ -483,10 +483,11 @@ def test_default_schedules_match_oracle(api, orc):
 
 
 def test_set_schedule_rejects_out_of_range(api):
-    """Host-side validation of hand-set schedules: unknown shapes, runs,
-    tiles per CTA above 2^4, split schedules that do not fit the part."""
+    """Host-side validation of hand-set schedules: unknown shapes, runs, form
+    bits, tiles per CTA above 2^4, split schedules that do not fit the part."""
     capi, ctx = api
-    for args in [(20, 12, 3, 2, 0, 0), (20, 12, 4, 9, 0, 0), (20, 12, 4, 2, 2, 0), (20, 12, 4, 2, 0, 5),
+    for args in [(20, 12, 3, 2, 0, 0), (20, 12, 4, 9, 0, 0), (20, 12, 4, 2, 4, 0), (20, 12, 4, 2, -1, 0),
+                 (20, 12, 4, 2, 0, 5),
                  (20, 13, 5, 2, 0, 5), (8, 12, 4, 2, 0, 0), (20, 14, 5, 2, 0, 0), (20, 14, 4, 1, 0, 0),
                  (20, 13, 4, 0, 0, 0)]:
         with pytest.raises(capi.ParaQAOAError):
@@ -619,8 +620,8 @@ def test_persistent_layer_passes_match_per_pass_launches(api, orc):
     g = chain_graph(sizes, 0.3, 303, 10)
     part = capi.paraqaoa_partition(capi.Graph.of(g), len(sizes), capi.PART_SIZES, sizes)
     try:
-        for n, sc in {15: (12, 5, 2, 1, 1), 16: (12, 4, 2, 0, 2), 17: (12, 4, 2, 0, 0), 18: (12, 4, 3, 1, 1),
-                      20: (12, 4, 2, 0, 3), 21: (13, 4, 2, 0, 2), 22: (13, 4, 2, 0, 1), 24: (13, 4, 2, 0, 0)}.items():
+        for n, sc in {15: (12, 5, 2, 1, 1), 16: (12, 4, 2, 2, 2), 17: (12, 4, 2, 0, 0), 18: (12, 4, 3, 3, 1),
+                      20: (12, 4, 2, 2, 3), 21: (13, 4, 2, 0, 2), 22: (13, 4, 2, 2, 1), 24: (13, 4, 2, 0, 0)}.items():
             capi.paraqaoa_set_schedule(ctx, n, *sc)
         ids = np.arange(len(sizes), dtype=np.int32)
         gam, bet = synth.random_angles(len(sizes), 3, 304)
