@@ -102,6 +102,22 @@ cudaError_t ensure_side_streams(paraqaoa_ctx* c) {
 // Tile shape of size class n: the context's choice, except that a halved
 // class uses the choice for its n - 1 stored qubits when that shape has a
 // halved low-group pass and leaves at least two tiles, else 2^12 x 16.
+// Tiles per CTA of a size class's passes (both launch forms, so that their
+// <C> sums group alike): the context's choice for the stored qubit count,
+// capped by the tiles a pass has (a halved class's low-group passes walk
+// tile pairs: one tile bit fewer), and lowered while a launch of `ninst`
+// instances would fill fewer than four waves of the shape's resident CTAs on
+// every SM: the idle slots of a short grid's last wave cost more than the
+// set-up the extra CTAs repeat (an 84-instance Adam batch of 2^20 states on
+// the 2^13 tile walking 16 tiles is 672 CTAs, 2.2 waves of 304).
+static int class_tpc(const paraqaoa_ctx* c, int kind, int tb, int nq, bool halved, int64_t ninst) {
+  const int tiles_log2 = halved ? nq - tb - 1 : nq - tb;
+  int tpc = std::min<int>(c->tpc_log2[nq], tiles_log2);
+  const int64_t slots = (int64_t)c->num_sms * kTileResidentCtas[kind];
+  while (tpc > 0 && (ninst << (tiles_log2 - tpc)) < 4 * slots) --tpc;
+  return tpc;
+}
+
 int class_kind(const paraqaoa_ctx* c, int n, bool halved) {
   if (!halved) return c->tile_kind[n];
   const int k = c->tile_kind[n - 1];
@@ -322,7 +338,7 @@ int plan_run(paraqaoa_ctx* c) {
           PersistSeg sg;
           std::memset(&sg, 0, sizeof(sg));
           sg.pd = q.sched[j];
-          sg.pd.tpc_log2 = std::min<int>(c->tpc_log2[n], n - q.tb);
+          sg.pd.tpc_log2 = class_tpc(c, q.kind, q.tb, q.nq, q.halved, lst.second);
           sg.n = n;
           sg.nr = layer_pass_rounds(q.kind, sg.pd);
           sg.list_off = lst.first;
@@ -420,8 +436,7 @@ int plan_run(paraqaoa_ctx* c) {
     std::vector<char> done(q.nsets, pl.cc_ready ? 1 : 0);
     for (size_t ip = 0; ip < q.sched.size(); ++ip) {
       PassDesc pd = q.sched[ip];
-      // a halved class's low-group passes walk tile pairs: one tile bit fewer
-      pd.tpc_log2 = q.halved ? std::min<int>(c->tpc_log2[q.nq], q.nq - tb - 1) : std::min<int>(c->tpc_log2[n], n - tb);
+      pd.tpc_log2 = class_tpc(c, kind, tb, q.nq, q.halved, kv.second.second);
       const int k = q.set[ip];
       int32_t* consts = c->d_consts.as<int32_t>() + q.off + (int64_t)std::max(k, 0) * q.elems;
       if (k >= 0 && !done[k]) {

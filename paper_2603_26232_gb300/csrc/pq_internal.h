@@ -19,6 +19,11 @@ struct TileShape {
 };
 constexpr int kTileKinds = 5;
 constexpr TileShape kTileShapes[kTileKinds] = {{12, 5}, {12, 4}, {13, 5}, {13, 4}, {14, 4}};
+// Resident CTAs per SM of each shape's layer pass: the occupancy its launch
+// bounds are compiled for (layer_min_blocks in layer_pass.cu: five CTAs of
+// 128 threads, four of 256, two of 256, two of 512, one of 1024). Used only
+// to size grids in whole waves, so a mismatch costs speed, not results.
+constexpr int kTileResidentCtas[kTileKinds] = {5, 4, 2, 2, 1};
 constexpr int kSmemMaxQubits = 14;  // states of <= 14 qubits stay on chip
 constexpr int kTinyMaxQubits = 9;   // n <= 9: one small CTA, plain loops
 constexpr int kMaxPlanes = 16;      // weight bit-planes (weights < 2^16)
