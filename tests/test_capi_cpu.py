@@ -106,3 +106,12 @@ def test_pei_efficiency_factor(capi):
     assert ef == pytest.approx(1 / (1 + math.exp(-1))) and pei == pytest.approx(80 * ef)
     with pytest.raises(capi.ParaQAOAError):
         capi.paraqaoa_pei(0.9, -1.0, 1.0, 1e-3)
+
+
+def test_probe_streams_validates_arguments(capi):
+    """The HBM stream probe rejects buffer sizes outside 1 MiB .. 16 GiB or not
+    a multiple of 16 bytes before it touches a device."""
+    for nbytes in (0, (1 << 20) - 16, (1 << 34) + 16, (1 << 24) + 8, -(1 << 24)):
+        with pytest.raises(capi.ParaQAOAError) as e:
+            capi.paraqaoa_probe_streams(0, nbytes)
+        assert e.value.code == capi.E_INVAL

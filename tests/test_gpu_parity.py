@@ -850,3 +850,15 @@ def test_context_halved_setting_drives_the_angle_search(api, orc):
     finally:
         capi.paraqaoa_destroy(hctx)
         capi.paraqaoa_part_free(part)
+
+
+def test_probe_streams_measures_plausible_bandwidth(api):
+    """paraqaoa_probe_streams on 1 GiB buffers (past the 129 MB L2): write-only,
+    read-only and copy bandwidth positive and finite, below the HBM3e nominal
+    7.9 TB/s with margin for measurement, and not an order of magnitude below
+    it (the half passes' ceilings are read from these)."""
+    capi, _ = api
+    w, r, c = capi.paraqaoa_probe_streams(0, 1 << 30)
+    for v in (w, r, c):
+        assert np.isfinite(v) and 1000.0 < v < 12000.0, (w, r, c)
+
